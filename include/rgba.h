@@ -1,0 +1,195 @@
+/*
+ * rgba.h -- C ABI of the batch-parallel differentiable Gaussian blendshape rasterizer
+ * (RGBAvatar, arXiv 2503.12886), hand-written CUDA for GB300 (sm_103a).
+ *
+ * One call renders B frames in one pass. Frame b draws the Gaussians of one avatar model,
+ * blended with its own weight vector psi_b (Eq. 1, Sec. 3.1), activated after blending
+ * (Supp. Sec. A.3), projected by EWA splatting, binned to screen tiles with a depth key, sorted
+ * and alpha-composited front to back (the 3DGS "preprocess" / "rasterize" stages that the
+ * batch-parallel rasterizer of Sec. 3.2 builds on). The backward pass takes the image-loss
+ * gradient back to every base Gaussian, blendshape and weight. rgba_step does all of it with a
+ * single host synchronisation per training step (Sec. 3.2, Fig. 4c).
+ *
+ * Conventions shared by every entry point
+ *  - Memory: every array argument is caller-owned DEVICE memory unless marked "host". The
+ *    library allocates nothing on the device; scratch lives in a caller-allocated workspace
+ *    sized by rgba_workspace_size. No pointer is retained after a call returns.
+ *  - Streams: every call is asynchronous on the given stream (0 = legacy default stream) and
+ *    enqueues kernels and memsets only, so it can be captured in a CUDA graph, except
+ *    rgba_step, which ends with one device-to-host read and a stream synchronisation.
+ *  - Errors: every call returns an rgba_status. Host-side validation failures return before
+ *    anything is enqueued. rgba_last_error() gives a thread-local message for the last failure.
+ *    No call aborts or exits the process.
+ *  - Types: fp32 for all attributes and images, int32 for counts and indices.
+ *
+ * Layouts
+ *  - Model (avatar), planar: g0[14][n_pad] with channels 0..2 mean (world, metres), 3..6
+ *    rotation quaternion (w, x, y, z) unnormalised, 7..9 log-scale, 10 opacity logit,
+ *    11..13 RGB colour. n_pad is a multiple of 4 and >= n; padding is ignored.
+ *    dg[k][A][n_pad] holds the blendshape deltas of the A channels set in `mask`, in ascending
+ *    channel order. Opacity (channel 10) must not be blended (Supp. A.3: blendshapes act on
+ *    position, rotation and colour; the synthetic workloads also blend log-scale).
+ *  - Frame parameters fparams[B][RGBA_FP_STRIDE]: 3x4 world-to-camera matrix (row-major,
+ *    x right, y down, z forward), fx, fy, cx, cy, near-plane depth, background RGB.
+ *  - Weights psi[B][k_stride]; frame b uses the first k of its model's entries.
+ *  - Images: frames are concatenated in frame order; frame b occupies 3*H_b*W_b floats, planar
+ *    [3][H_b][W_b]; per-pixel arrays (T_final, n_contrib) occupy H_b*W_b entries.
+ *    Pixel (px, py) has its centre at (px + 0.5, py + 0.5).
+ */
+#ifndef RGBA_H
+#define RGBA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RGBA_OK = 0,
+    RGBA_ERR_INVALID_ARG = 1,  /* bad pointer, size, layout or mask; nothing was enqueued */
+    RGBA_ERR_CAPACITY = 2,     /* tile-pair buffer too small; rgba_step_out.pairs_needed set */
+    RGBA_ERR_CUDA = 3,         /* a CUDA runtime call failed; see rgba_last_error() */
+    RGBA_ERR_TIMEOUT = 4,      /* a bounded device loop gave up; the results are invalid */
+    RGBA_ERR_UNSUPPORTED = 5   /* valid request outside what this build supports */
+} rgba_status;
+
+#define RGBA_NCH 14
+#define RGBA_FP_STRIDE 20
+#define RGBA_MAX_FRAMES 4096
+#define RGBA_MAX_MODELS 256
+#define RGBA_MAX_K 64
+#define RGBA_MAX_DIM 4096
+
+/* Loss kinds for rgba_step (Sec. 3.2 "Loss Function" uses L1). Each frame's loss is the mean
+ * over its 3*H*W values; the batch loss is the mean over frames. */
+#define RGBA_LOSS_L1 1
+#define RGBA_LOSS_L2 2 /* 1/2 (I - target)^2 */
+
+typedef struct {
+    int32_t n;          /* Gaussians */
+    int32_t n_pad;      /* row stride of g0/dg, multiple of 4, >= n */
+    int32_t k;          /* blendshapes, 1..RGBA_MAX_K */
+    uint32_t mask;      /* bit c set: channel c is blended; bit 10 must be clear */
+    const float *g0;    /* device [14][n_pad] */
+    const float *dg;    /* device [k][A][n_pad], A = popcount(mask) */
+    float *grad_g0;     /* device [14][n_pad] or NULL: dL/dG0, overwritten by the backward */
+    float *grad_dg;     /* device [k][A][n_pad] or NULL: dL/ddG, overwritten by the backward */
+} rgba_model;
+
+typedef struct {
+    int32_t model;      /* index into rgba_batch.models */
+    int32_t width;      /* pixels, 1..RGBA_MAX_DIM */
+    int32_t height;
+} rgba_frame;
+
+typedef struct {
+    int32_t n_models;
+    const rgba_model *models;   /* host array [n_models] */
+    int32_t n_frames;
+    const rgba_frame *frames;   /* host array [n_frames] */
+    int32_t k_stride;           /* row stride of psi, >= every model's k */
+    const float *psi;           /* device [n_frames][k_stride] */
+    const float *fparams;       /* device [n_frames][RGBA_FP_STRIDE] */
+    float *grad_psi;            /* device [n_frames][k_stride] or NULL, overwritten */
+    int32_t tile_w, tile_h;     /* screen tile shape: 16x16 or 8x32 (tile_w * tile_h == 256) */
+    int32_t smem_batch;         /* Gaussians staged per shared-memory round: 64, 128 or 256 */
+} rgba_batch;
+
+typedef struct {
+    double loss;                /* batch loss (rgba_step only) */
+    int64_t pairs;              /* (Gaussian, tile) pairs the batch needed */
+    int64_t pair_capacity;      /* pairs the workspace could hold */
+    int64_t pairs_needed;       /* == pairs; set on RGBA_ERR_CAPACITY */
+    uint32_t overflow;          /* 1 when pairs > pair_capacity */
+    uint32_t device_error;      /* non-zero when a bounded device loop gave up */
+} rgba_step_out;
+
+/* Byte offsets of the workspace regions, for tests and debugging tools that read the
+ * intermediate results (splat records, tile ranges, sorted lists) directly. */
+typedef struct {
+    size_t counters;     /* rgba_counters */
+    size_t records;      /* float[R][12]: u, v, conic a, b, c, opacity, r, g, b, depth, 0, 0 */
+    size_t rects;        /* uint16[R][4]: tile rectangle x0, y0, x1, y1 (half-open) */
+    size_t tile_start;   /* uint32[T + 1]: start of each (frame, tile) list */
+    size_t sorted;       /* uint32[capacity]: Gaussian index per list entry */
+    size_t grad2d;       /* float[R][12]: dL/d(u, v, conic a, b, c, opacity, r, g, b) */
+    size_t total_bytes;
+    int64_t records_total;   /* R = sum over frames of the model's n_pad; frame b starts at
+                                the sum of n_pad over frames before b */
+    int64_t tiles_total;     /* T = sum over frames of tiles_x * tiles_y, frame-major,
+                                row-major within a frame */
+    int64_t pair_capacity;
+} rgba_ws_layout;
+
+typedef struct {
+    uint32_t pairs;        /* pairs the batch needed (saturates at 2^32 - 1) */
+    uint32_t overflow;     /* 1 if pairs > capacity */
+    uint32_t n_work;       /* non-empty tiles */
+    uint32_t device_error;
+    double loss;
+} rgba_counters;
+
+typedef struct rgba_ctx *rgba_ctx_t;
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char *rgba_last_error(void);
+
+/* Create a context bound to CUDA device `device` (queries its SM count; allocates one small
+ * pinned host block for rgba_step's result). */
+int rgba_create(int device, rgba_ctx_t *out);
+void rgba_destroy(rgba_ctx_t ctx);
+
+/* Workspace bytes for `batch` with room for `pair_capacity` (Gaussian, tile) pairs.
+ * Every entry point below that takes (ws, ws_bytes) derives the same layout from the batch;
+ * the pair capacity it uses is whatever fits in ws_bytes. ws must be 256-byte aligned. */
+int rgba_workspace_size(const rgba_batch *batch, int64_t pair_capacity, size_t *bytes);
+int rgba_workspace_layout(const rgba_batch *batch, size_t ws_bytes, rgba_ws_layout *out);
+
+/* Eq. 1 (Sec. 3.1): out[b] = G0 + sum_k psi_b[k] dG_k on the blended channels, G0 elsewhere.
+ * out: device [B][14][n_pad(model of b)], frames concatenated. No workspace needed. */
+int rgba_blend(rgba_ctx_t ctx, const rgba_batch *batch, float *out, void *stream);
+
+/* Fused blend (Eq. 1) + activations (Supp. A.3) + EWA projection + tile rectangle + depth key
+ * for every (frame, Gaussian); counts the Gaussians of every (frame, tile). */
+int rgba_preprocess(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
+                    void *stream);
+
+/* Builds every (frame, tile) list sorted by (depth bits, Gaussian index). If the pairs exceed
+ * the capacity the device sets the overflow counter and the later stages skip their work. */
+int rgba_bin_sort(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
+                  void *stream);
+
+/* Front-to-back compositing (Sec. 3.2 "rasterize"): img [3][H][W] per frame = C + T bg,
+ * T_final and n_contrib (list position + 1 of the last blended Gaussian) per pixel.
+ * Alpha = min(0.99, o exp(power)), skipped below 1/255, stop when T (1 - alpha) < 1e-4. */
+int rgba_render_fwd(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
+                    float *img, float *T_final, int32_t *n_contrib, void *stream);
+
+/* Back-propagation of dL/dimg (same layout as img) through compositing, projection,
+ * activations and the blend. Uses only T_final and n_contrib from the forward (recomputes the
+ * compositing in reverse). Writes models[m].grad_g0 / grad_dg and batch->grad_psi (those that
+ * are non-NULL); the per-(frame, Gaussian) 2-D gradients stay in the workspace (grad2d). */
+int rgba_render_bwd(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
+                    const float *dL_dimg, const float *T_final, const int32_t *n_contrib,
+                    void *stream);
+
+/* One training step: preprocess, bin/sort, render with the fused loss against `target`
+ * (layout of img), backward, then ONE device-to-host read of the counters and a stream
+ * synchronisation. img may be NULL (the workspace keeps it). out: host. Returns
+ * RGBA_ERR_CAPACITY (gradients invalid, out->pairs_needed set) when the pairs overflowed. */
+int rgba_step(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
+              const float *target, int loss_kind, float *img, rgba_step_out *out, void *stream);
+
+/* rgba_step without the final read and synchronisation: everything it enqueues is kernels and
+ * memsets, so a caller can capture it in a CUDA graph; the loss and counters stay in the
+ * workspace's rgba_counters. */
+int rgba_step_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
+                    const float *target, int loss_kind, float *img, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RGBA_H */

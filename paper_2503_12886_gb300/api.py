@@ -1,0 +1,169 @@
+"""Thin ctypes binding of librgba (include/rgba.h): the same entry points, argument marshalling
+only. Every step of the rasterizer runs in the CUDA library; if the library is missing this
+module raises instead of falling back to anything else."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librgba.so")
+
+RGBA_OK = 0
+RGBA_ERR_INVALID_ARG = 1
+RGBA_ERR_CAPACITY = 2
+RGBA_ERR_CUDA = 3
+RGBA_ERR_TIMEOUT = 4
+RGBA_ERR_UNSUPPORTED = 5
+RGBA_LOSS_L1 = 1
+RGBA_LOSS_L2 = 2
+RGBA_FP_STRIDE = 20
+RGBA_NCH = 14
+
+# every symbol include/rgba.h declares
+EXPORTS = ("rgba_last_error", "rgba_create", "rgba_destroy", "rgba_workspace_size",
+           "rgba_workspace_layout", "rgba_blend", "rgba_preprocess", "rgba_bin_sort",
+           "rgba_render_fwd", "rgba_render_bwd", "rgba_step", "rgba_step_async")
+
+
+class RgbaModel(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_pad", C.c_int32), ("k", C.c_int32), ("mask", C.c_uint32),
+                ("g0", C.c_void_p), ("dg", C.c_void_p), ("grad_g0", C.c_void_p),
+                ("grad_dg", C.c_void_p)]
+
+
+class RgbaFrame(C.Structure):
+    _fields_ = [("model", C.c_int32), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class RgbaBatch(C.Structure):
+    _fields_ = [("n_models", C.c_int32), ("models", C.POINTER(RgbaModel)),
+                ("n_frames", C.c_int32), ("frames", C.POINTER(RgbaFrame)),
+                ("k_stride", C.c_int32), ("psi", C.c_void_p), ("fparams", C.c_void_p),
+                ("grad_psi", C.c_void_p), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
+                ("smem_batch", C.c_int32)]
+
+
+class RgbaStepOut(C.Structure):
+    _fields_ = [("loss", C.c_double), ("pairs", C.c_int64), ("pair_capacity", C.c_int64),
+                ("pairs_needed", C.c_int64), ("overflow", C.c_uint32),
+                ("device_error", C.c_uint32)]
+
+
+class RgbaWsLayout(C.Structure):
+    _fields_ = [("counters", C.c_size_t), ("records", C.c_size_t), ("rects", C.c_size_t),
+                ("tile_start", C.c_size_t), ("sorted", C.c_size_t), ("grad2d", C.c_size_t),
+                ("total_bytes", C.c_size_t), ("records_total", C.c_int64),
+                ("tiles_total", C.c_int64), ("pair_capacity", C.c_int64)]
+
+
+class RgbaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rgba error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load librgba.so from the package directory (built by build.py / __graft_entry__.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"librgba.so not built at {LIB_PATH}; run the package build")
+            L = C.CDLL(LIB_PATH)
+            P, i32, i64, sz = C.c_void_p, C.c_int, C.c_int64, C.c_size_t
+            Bp = C.POINTER(RgbaBatch)
+            L.rgba_last_error.restype = C.c_char_p
+            L.rgba_create.argtypes = [i32, C.POINTER(P)]
+            L.rgba_destroy.argtypes = [P]
+            L.rgba_destroy.restype = None
+            L.rgba_workspace_size.argtypes = [Bp, i64, C.POINTER(sz)]
+            L.rgba_workspace_layout.argtypes = [Bp, sz, C.POINTER(RgbaWsLayout)]
+            L.rgba_blend.argtypes = [P, Bp, P, P]
+            L.rgba_preprocess.argtypes = [P, Bp, P, sz, P]
+            L.rgba_bin_sort.argtypes = [P, Bp, P, sz, P]
+            L.rgba_render_fwd.argtypes = [P, Bp, P, sz, P, P, P, P]
+            L.rgba_render_bwd.argtypes = [P, Bp, P, sz, P, P, P, P]
+            L.rgba_step.argtypes = [P, Bp, P, sz, P, i32, P, C.POINTER(RgbaStepOut), P]
+            L.rgba_step_async.argtypes = [P, Bp, P, sz, P, i32, P, P]
+            for name in ("rgba_create", "rgba_workspace_size", "rgba_workspace_layout",
+                         "rgba_blend", "rgba_preprocess", "rgba_bin_sort", "rgba_render_fwd",
+                         "rgba_render_bwd", "rgba_step", "rgba_step_async"):
+                getattr(L, name).restype = i32
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().rgba_last_error().decode()
+
+
+def check(rc: int) -> int:
+    if rc != RGBA_OK:
+        raise RgbaError(rc, last_error())
+    return rc
+
+
+def rgba_create(device: int = 0) -> int:
+    h = C.c_void_p()
+    check(lib().rgba_create(device, C.byref(h)))
+    return h.value
+
+
+def rgba_destroy(ctx: int) -> None:
+    lib().rgba_destroy(ctx)
+
+
+def rgba_workspace_size(batch: RgbaBatch, pair_capacity: int) -> int:
+    n = C.c_size_t()
+    check(lib().rgba_workspace_size(C.byref(batch), pair_capacity, C.byref(n)))
+    return n.value
+
+
+def rgba_workspace_layout(batch: RgbaBatch, ws_bytes: int) -> RgbaWsLayout:
+    out = RgbaWsLayout()
+    check(lib().rgba_workspace_layout(C.byref(batch), ws_bytes, C.byref(out)))
+    return out
+
+
+def rgba_blend(ctx, batch, out_ptr, stream) -> int:
+    return check(lib().rgba_blend(ctx, C.byref(batch), out_ptr, stream))
+
+
+def rgba_preprocess(ctx, batch, ws, ws_bytes, stream) -> int:
+    return check(lib().rgba_preprocess(ctx, C.byref(batch), ws, ws_bytes, stream))
+
+
+def rgba_bin_sort(ctx, batch, ws, ws_bytes, stream) -> int:
+    return check(lib().rgba_bin_sort(ctx, C.byref(batch), ws, ws_bytes, stream))
+
+
+def rgba_render_fwd(ctx, batch, ws, ws_bytes, img, T_final, n_contrib, stream) -> int:
+    return check(lib().rgba_render_fwd(ctx, C.byref(batch), ws, ws_bytes, img, T_final,
+                                       n_contrib, stream))
+
+
+def rgba_render_bwd(ctx, batch, ws, ws_bytes, dL_dimg, T_final, n_contrib, stream) -> int:
+    return check(lib().rgba_render_bwd(ctx, C.byref(batch), ws, ws_bytes, dL_dimg, T_final,
+                                       n_contrib, stream))
+
+
+def rgba_step(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream) -> tuple[int, RgbaStepOut]:
+    """Returns (status, out); RGBA_ERR_CAPACITY is returned, not raised, so callers can grow
+    the workspace and retry."""
+    out = RgbaStepOut()
+    rc = lib().rgba_step(ctx, C.byref(batch), ws, ws_bytes, target, loss_kind, img,
+                         C.byref(out), stream)
+    if rc not in (RGBA_OK, RGBA_ERR_CAPACITY):
+        check(rc)
+    return rc, out
+
+
+def rgba_step_async(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream) -> int:
+    return check(lib().rgba_step_async(ctx, C.byref(batch), ws, ws_bytes, target, loss_kind,
+                                       img, stream))

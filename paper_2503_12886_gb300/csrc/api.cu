@@ -1,0 +1,483 @@
+// C ABI of librgba: argument validation, workspace layout and the launch sequence of every entry
+// point declared in include/rgba.h.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rgba_internal.cuh"
+
+using namespace rgba;
+
+struct rgba_ctx {
+    int device;
+    int sms;
+    rgba_counters *pinned;  // host-pinned landing spot of rgba_step's single read
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    return fail(RGBA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int popcount14(unsigned m) {
+    int c = 0;
+    for (int i = 0; i < kNch; ++i) c += (m >> i) & 1u;
+    return c;
+}
+
+struct Plan {
+    std::vector<ModelInfo> models;
+    std::vector<FrameInfo> frames;
+    std::vector<int> mframes;
+    Layout L{};
+    int max_n = 0, max_k = 1, max_chunks = 0, max_nb = 0;
+};
+
+// Host-side checks and tables; sizes of everything except the pair buffers.
+int make_plan(const rgba_batch *b, Plan &p) {
+    if (!b) return fail(RGBA_ERR_INVALID_ARG, "batch is NULL");
+    if (b->n_frames < 0 || b->n_frames > RGBA_MAX_FRAMES)
+        return fail(RGBA_ERR_INVALID_ARG, "n_frames out of range");
+    if (b->n_models < 0 || b->n_models > RGBA_MAX_MODELS)
+        return fail(RGBA_ERR_INVALID_ARG, "n_models out of range");
+    if (b->n_frames > 0 && (!b->frames || !b->models || b->n_models == 0))
+        return fail(RGBA_ERR_INVALID_ARG, "frames/models arrays missing");
+    int tw = b->tile_w, th = b->tile_h;
+    if (tw == 0 && th == 0) tw = th = 16;
+    if (!((tw == 16 && th == 16) || (tw == 8 && th == 32)))
+        return fail(RGBA_ERR_INVALID_ARG, "tile shape must be 16x16 or 8x32");
+    int sb = b->smem_batch == 0 ? 256 : b->smem_batch;
+    if (sb != 64 && sb != 128 && sb != 256)
+        return fail(RGBA_ERR_INVALID_ARG, "smem_batch must be 64, 128 or 256");
+    const int M = b->n_frames > 0 ? b->n_models : 0;
+    p.models.assign(M, ModelInfo{});
+    for (int m = 0; m < M; ++m) {
+        const rgba_model &src = b->models[m];
+        ModelInfo &mi = p.models[m];
+        if (src.n < 0 || src.n_pad < src.n || (src.n_pad & 3))
+            return fail(RGBA_ERR_INVALID_ARG, "model " + std::to_string(m) + ": need 0 <= n <= n_pad, n_pad % 4 == 0");
+        if (src.k < 1 || src.k > RGBA_MAX_K)
+            return fail(RGBA_ERR_INVALID_ARG, "model " + std::to_string(m) + ": k out of range");
+        if (src.mask & ~0x3FFFu) return fail(RGBA_ERR_INVALID_ARG, "mask has bits above channel 13");
+        if (src.mask & (1u << 10)) return fail(RGBA_ERR_INVALID_ARG, "opacity (channel 10) cannot be blended");
+        const int A = popcount14(src.mask);
+        if (src.n > 0 && (!src.g0 || (A > 0 && !src.dg)))
+            return fail(RGBA_ERR_INVALID_ARG, "model " + std::to_string(m) + ": g0/dg is NULL");
+        if ((reinterpret_cast<uintptr_t>(src.g0) | reinterpret_cast<uintptr_t>(src.dg) |
+             reinterpret_cast<uintptr_t>(src.grad_g0) | reinterpret_cast<uintptr_t>(src.grad_dg)) & 15)
+            return fail(RGBA_ERR_INVALID_ARG, "model arrays must be 16-byte aligned");
+        mi.g0 = src.g0;
+        mi.dg = src.dg;
+        mi.gg0 = src.grad_g0;
+        mi.gdg = src.grad_dg;
+        mi.n = src.n;
+        mi.n_pad = src.n_pad;
+        mi.k = src.k;
+        mi.A = A;
+        mi.mask = src.mask;
+        int a = 0;
+        for (int ch = 0; ch < kNch; ++ch)
+            if ((src.mask >> ch) & 1u) mi.chans[a++] = ch;
+        mi.n_chunks = (src.n_pad + kBwdChunk - 1) / kBwdChunk;
+        p.max_n = std::max(p.max_n, src.n_pad);
+        p.max_chunks = std::max(p.max_chunks, mi.n_chunks);
+    }
+    const int B = b->n_frames;
+    p.frames.assign(B, FrameInfo{});
+    long long R = 0, T = 0, P = 0;
+    std::vector<std::vector<int>> by_model(M);
+    for (int f = 0; f < B; ++f) {
+        const rgba_frame &fr = b->frames[f];
+        if (fr.model < 0 || fr.model >= M) return fail(RGBA_ERR_INVALID_ARG, "frame " + std::to_string(f) + ": bad model index");
+        if (fr.width < 1 || fr.height < 1 || fr.width > RGBA_MAX_DIM || fr.height > RGBA_MAX_DIM)
+            return fail(RGBA_ERR_INVALID_ARG, "frame " + std::to_string(f) + ": size out of range");
+        const ModelInfo &mi = p.models[fr.model];
+        if (mi.k > b->k_stride) return fail(RGBA_ERR_INVALID_ARG, "k_stride smaller than a model's k");
+        FrameInfo &fi = p.frames[f];
+        fi.model = fr.model;
+        fi.W = fr.width;
+        fi.H = fr.height;
+        fi.tiles_x = (fr.width + tw - 1) / tw;
+        fi.tiles_y = (fr.height + th - 1) / th;
+        fi.tile_base = (int)T;
+        fi.rec_base = (int)R;
+        fi.n = mi.n;
+        fi.n_pad = mi.n_pad;
+        fi.k = mi.k;
+        fi.pix_base = P;
+        R += mi.n_pad;
+        T += (long long)fi.tiles_x * fi.tiles_y;
+        P += (long long)fr.width * fr.height;
+        if (R > 0x7fffffffLL || T > 0x7fffffffLL) return fail(RGBA_ERR_INVALID_ARG, "batch too large");
+        by_model[fr.model].push_back(f);
+        p.max_k = std::max(p.max_k, mi.k);
+    }
+    if (B > 0 && (!b->psi || !b->fparams)) return fail(RGBA_ERR_INVALID_ARG, "psi/fparams is NULL");
+    long long dpsi = 0;
+    for (int m = 0; m < M; ++m) {
+        ModelInfo &mi = p.models[m];
+        mi.nb = (int)by_model[m].size();
+        mi.frame_off = (int)p.mframes.size();
+        for (int f : by_model[m]) p.mframes.push_back(f);
+        mi.dpsi_off = dpsi;
+        dpsi += (long long)mi.nb * mi.k * mi.n_chunks;
+        p.max_nb = std::max(p.max_nb, mi.nb);
+    }
+    Layout &L = p.L;
+    L.R = R;
+    L.T = T;
+    L.P = P;
+    L.B = B;
+    L.M = M;
+    L.k_stride = b->k_stride;
+    L.tw = tw;
+    L.th = th;
+    L.smem_batch = sb;
+    L.dpsi_floats = dpsi;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    L.counters = take(256);
+    L.models = take(sizeof(ModelInfo) * (size_t)M);
+    L.frames = take(sizeof(FrameInfo) * (size_t)B);
+    L.mframes = take(sizeof(int) * (size_t)B);
+    L.tile_count = take(4 * (size_t)T);
+    L.tile_start = take(4 * (size_t)(T + 1));
+    L.cursor = take(4 * (size_t)T);
+    L.work = take(4 * (size_t)T);
+    L.records = take(sizeof(float) * kRecFloats * (size_t)R);
+    L.rects = take(8 * (size_t)R);
+    L.cache = take(sizeof(float) * kCacheFloats * (size_t)R);
+    L.grad2d = take(sizeof(float) * kG2Floats * (size_t)R);
+    L.pix_T = take(4 * (size_t)P);
+    L.pix_n = take(4 * (size_t)P);
+    L.pix_dl = take(12 * (size_t)P);
+    L.pix_img = take(12 * (size_t)P);
+    L.dpsi_part = take(4 * (size_t)dpsi);
+    L.keys = o;  // pair buffers follow: 8 + 4 bytes per pair
+    return RGBA_OK;
+}
+
+void finish_layout(Layout &L, long long cap) {
+    L.cap = cap;
+    size_t o = L.keys;
+    o = align256(o + 8 * (size_t)cap);
+    L.sorted = o;
+    o = align256(o + 4 * (size_t)cap);
+    L.total = o;
+}
+
+long long cap_for_bytes(const Layout &L, size_t bytes) {
+    Layout t = L;
+    finish_layout(t, 0);
+    if (bytes < t.total) return -1;
+    long long c = (long long)((bytes - L.keys) / 12);
+    while (c > 0) {
+        finish_layout(t, c);
+        if (t.total <= bytes) break;
+        c -= (long long)((t.total - bytes + 11) / 12);
+    }
+    return c < 0 ? 0 : c;
+}
+
+Ctx make_ctx(const Layout &L, unsigned char *ws, const rgba_batch *b) {
+    Ctx c{};
+    c.models = reinterpret_cast<const ModelInfo *>(ws + L.models);
+    c.frames = reinterpret_cast<const FrameInfo *>(ws + L.frames);
+    c.mframes = reinterpret_cast<const int *>(ws + L.mframes);
+    c.psi = b->psi;
+    c.fparams = b->fparams;
+    c.grad_psi = b->grad_psi;
+    c.cnt = reinterpret_cast<Counters *>(ws + L.counters);
+    c.tile_count = reinterpret_cast<unsigned *>(ws + L.tile_count);
+    c.tile_start = reinterpret_cast<unsigned *>(ws + L.tile_start);
+    c.cursor = reinterpret_cast<unsigned *>(ws + L.cursor);
+    c.work = reinterpret_cast<unsigned *>(ws + L.work);
+    c.records = reinterpret_cast<float4 *>(ws + L.records);
+    c.rects = reinterpret_cast<ushort4 *>(ws + L.rects);
+    c.cache = reinterpret_cast<float4 *>(ws + L.cache);
+    c.grad2d = reinterpret_cast<float *>(ws + L.grad2d);
+    c.keys = reinterpret_cast<unsigned long long *>(ws + L.keys);
+    c.sorted = reinterpret_cast<unsigned *>(ws + L.sorted);
+    c.dpsi_part = reinterpret_cast<float *>(ws + L.dpsi_part);
+    c.R = L.R;
+    c.T = L.T;
+    c.cap = L.cap;
+    c.B = L.B;
+    c.M = L.M;
+    c.k_stride = L.k_stride;
+    c.tw = L.tw;
+    c.th = L.th;
+    return c;
+}
+
+// Common prologue of the workspace-taking entry points.
+struct Call {
+    Plan p;
+    Ctx c;
+    unsigned char *ws = nullptr;
+    cudaStream_t s = nullptr;
+};
+
+int prologue(rgba_ctx_t ctx, const rgba_batch *b, void *ws, size_t ws_bytes, void *stream, Call &call) {
+    if (!ctx) return fail(RGBA_ERR_INVALID_ARG, "ctx is NULL");
+    int rc = make_plan(b, call.p);
+    if (rc) return rc;
+    if (!ws) return fail(RGBA_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(RGBA_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    long long cap = cap_for_bytes(call.p.L, ws_bytes);
+    if (cap < 0) return fail(RGBA_ERR_INVALID_ARG, "workspace smaller than the fixed part of the layout");
+    finish_layout(call.p.L, cap);
+    call.ws = static_cast<unsigned char *>(ws);
+    call.c = make_ctx(call.p.L, call.ws, b);
+    call.s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return RGBA_OK;
+}
+
+int upload_tables(Call &k) {
+    const Layout &L = k.p.L;
+    cudaError_t e;
+    if (!k.p.models.empty() &&
+        (e = launch_upload(k.ws + L.models, k.p.models.data(), sizeof(ModelInfo) * k.p.models.size(), k.s)) != cudaSuccess)
+        return cuda_fail(e, "upload models");
+    if (!k.p.frames.empty() &&
+        (e = launch_upload(k.ws + L.frames, k.p.frames.data(), sizeof(FrameInfo) * k.p.frames.size(), k.s)) != cudaSuccess)
+        return cuda_fail(e, "upload frames");
+    if (!k.p.mframes.empty() &&
+        (e = launch_upload(k.ws + L.mframes, k.p.mframes.data(), sizeof(int) * k.p.mframes.size(), k.s)) != cudaSuccess)
+        return cuda_fail(e, "upload model frames");
+    return RGBA_OK;
+}
+
+int memset_async(void *p, size_t bytes, cudaStream_t s, const char *what) {
+    if (bytes == 0) return RGBA_OK;
+    cudaError_t e = cudaMemsetAsync(p, 0, bytes, s);
+    return e == cudaSuccess ? RGBA_OK : cuda_fail(e, what);
+}
+
+int do_preprocess(Call &k) {
+    int rc;
+    if ((rc = upload_tables(k))) return rc;
+    if ((rc = memset_async(k.ws + k.p.L.counters, 256, k.s, "memset counters"))) return rc;
+    if ((rc = memset_async(k.ws + k.p.L.tile_count, 4 * (size_t)k.p.L.T, k.s, "memset tile counts"))) return rc;
+    cudaError_t e = launch_preprocess(k.c, k.p.max_n, k.s);
+    return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "preprocess");
+}
+
+int grid_for(rgba_ctx_t ctx, int per_sm) { return ctx->sms * per_sm; }
+
+int do_bin_sort(rgba_ctx_t ctx, Call &k) {
+    cudaError_t e;
+    int rc;
+    if ((e = launch_scan(k.c, k.s)) != cudaSuccess) return cuda_fail(e, "scan");
+    if ((e = launch_scatter(k.c, k.p.max_n, k.s)) != cudaSuccess) return cuda_fail(e, "scatter");
+    if ((rc = memset_async(&k.c.cnt->next_sort, 4, k.s, "memset sort counter"))) return rc;
+    if ((e = launch_tile_sort(k.c, grid_for(ctx, 1), k.s)) != cudaSuccess) return cuda_fail(e, "tile sort");
+    return RGBA_OK;
+}
+
+int do_render_fwd(rgba_ctx_t ctx, Call &k, float *img, float *T, int *n, const float *target, int loss_kind, float *dl) {
+    int rc;
+    if ((rc = memset_async(&k.c.cnt->next_fwd, 4, k.s, "memset fwd counter"))) return rc;
+    cudaError_t e = launch_render_fwd(k.c, grid_for(ctx, 4), k.p.L.smem_batch, img, T, n, target, loss_kind, dl, nullptr, k.s);
+    return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "render fwd");
+}
+
+int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, const int *n) {
+    int rc;
+    const Layout &L = k.p.L;
+    if ((rc = memset_async(&k.c.cnt->next_bwd, 4, k.s, "memset bwd counter"))) return rc;
+    if ((rc = memset_async(k.ws + L.grad2d, sizeof(float) * kG2Floats * (size_t)L.R, k.s, "memset grad2d"))) return rc;
+    cudaError_t e = launch_render_bwd(k.c, grid_for(ctx, 4), L.smem_batch, dl, T, n, k.s);
+    if (e != cudaSuccess) return cuda_fail(e, "render bwd");
+    for (const ModelInfo &m : k.p.models) {
+        if (m.nb) continue;  // no frame renders it: zero gradient
+        if (m.gg0 && (rc = memset_async(m.gg0, sizeof(float) * kNch * (size_t)m.n_pad, k.s, "memset grad_g0"))) return rc;
+        if (m.gdg && (rc = memset_async(m.gdg, sizeof(float) * (size_t)m.k * m.A * m.n_pad, k.s, "memset grad_dg"))) return rc;
+    }
+    if ((e = launch_gauss_bwd(k.c, k.p.max_chunks, k.p.max_nb, k.p.max_k, k.s)) != cudaSuccess) return cuda_fail(e, "gauss bwd");
+    if ((e = launch_dpsi_reduce(k.c, k.p.max_k, k.s)) != cudaSuccess) return cuda_fail(e, "dpsi reduce");
+    return RGBA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rgba_last_error(void) { return g_err.c_str(); }
+
+int rgba_create(int device, rgba_ctx_t *out) {
+    if (!out) return fail(RGBA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(RGBA_ERR_INVALID_ARG, "no such device");
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    if (prop.major < 10) return fail(RGBA_ERR_UNSUPPORTED, "needs a Blackwell-class GPU (sm_100 or newer)");
+    rgba_ctx *c = new rgba_ctx{};
+    c->device = device;
+    c->sms = prop.multiProcessorCount;
+    if ((e = cudaHostAlloc(reinterpret_cast<void **>(&c->pinned), sizeof(rgba_counters), cudaHostAllocDefault)) != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaHostAlloc");
+    }
+    *out = c;
+    return RGBA_OK;
+}
+
+void rgba_destroy(rgba_ctx_t ctx) {
+    if (!ctx) return;
+    cudaFreeHost(ctx->pinned);
+    delete ctx;
+}
+
+int rgba_workspace_size(const rgba_batch *batch, int64_t pair_capacity, size_t *bytes) {
+    if (!bytes) return fail(RGBA_ERR_INVALID_ARG, "bytes is NULL");
+    if (pair_capacity < 0 || pair_capacity > 0xfffffff0LL) return fail(RGBA_ERR_INVALID_ARG, "pair_capacity out of range");
+    Plan p;
+    int rc = make_plan(batch, p);
+    if (rc) return rc;
+    finish_layout(p.L, pair_capacity);
+    *bytes = p.L.total;
+    return RGBA_OK;
+}
+
+int rgba_workspace_layout(const rgba_batch *batch, size_t ws_bytes, rgba_ws_layout *out) {
+    if (!out) return fail(RGBA_ERR_INVALID_ARG, "out is NULL");
+    Plan p;
+    int rc = make_plan(batch, p);
+    if (rc) return rc;
+    long long cap = cap_for_bytes(p.L, ws_bytes);
+    if (cap < 0) return fail(RGBA_ERR_INVALID_ARG, "workspace smaller than the fixed part of the layout");
+    finish_layout(p.L, cap);
+    out->counters = p.L.counters;
+    out->records = p.L.records;
+    out->rects = p.L.rects;
+    out->tile_start = p.L.tile_start;
+    out->sorted = p.L.sorted;
+    out->grad2d = p.L.grad2d;
+    out->total_bytes = p.L.total;
+    out->records_total = p.L.R;
+    out->tiles_total = p.L.T;
+    out->pair_capacity = p.L.cap;
+    return RGBA_OK;
+}
+
+int rgba_blend(rgba_ctx_t ctx, const rgba_batch *batch, float *out, void *stream) {
+    if (!ctx) return fail(RGBA_ERR_INVALID_ARG, "ctx is NULL");
+    Plan p;
+    int rc = make_plan(batch, p);
+    if (rc) return rc;
+    if (p.L.B == 0) return RGBA_OK;
+    if (!out) return fail(RGBA_ERR_INVALID_ARG, "out is NULL");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    Ctx c{};
+    c.models = p.models.data();  // host tables: launch_blend packs them into kernel parameters
+    c.frames = p.frames.data();
+    c.psi = batch->psi;
+    c.k_stride = batch->k_stride;
+    c.B = p.L.B;
+    e = launch_blend(c, p.max_n, out, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "blend");
+}
+
+int rgba_preprocess(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, void *stream) {
+    Call k;
+    int rc = prologue(ctx, batch, ws, ws_bytes, stream, k);
+    if (rc || k.p.L.B == 0) return rc;
+    return do_preprocess(k);
+}
+
+int rgba_bin_sort(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, void *stream) {
+    Call k;
+    int rc = prologue(ctx, batch, ws, ws_bytes, stream, k);
+    if (rc || k.p.L.B == 0) return rc;
+    return do_bin_sort(ctx, k);
+}
+
+int rgba_render_fwd(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, float *img,
+                    float *T_final, int32_t *n_contrib, void *stream) {
+    Call k;
+    int rc = prologue(ctx, batch, ws, ws_bytes, stream, k);
+    if (rc || k.p.L.B == 0) return rc;
+    if (!img || !T_final || !n_contrib) return fail(RGBA_ERR_INVALID_ARG, "img/T_final/n_contrib is NULL");
+    return do_render_fwd(ctx, k, img, T_final, n_contrib, nullptr, 0, nullptr);
+}
+
+int rgba_render_bwd(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *dL_dimg,
+                    const float *T_final, const int32_t *n_contrib, void *stream) {
+    Call k;
+    int rc = prologue(ctx, batch, ws, ws_bytes, stream, k);
+    if (rc || k.p.L.B == 0) return rc;
+    if (!dL_dimg || !T_final || !n_contrib) return fail(RGBA_ERR_INVALID_ARG, "dL_dimg/T_final/n_contrib is NULL");
+    return do_render_bwd(ctx, k, dL_dimg, T_final, n_contrib);
+}
+
+int rgba_step_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *target,
+                    int loss_kind, float *img, void *stream) {
+    Call k;
+    int rc = prologue(ctx, batch, ws, ws_bytes, stream, k);
+    if (rc || k.p.L.B == 0) return rc;
+    if (!target) return fail(RGBA_ERR_INVALID_ARG, "target is NULL");
+    if (loss_kind != RGBA_LOSS_L1 && loss_kind != RGBA_LOSS_L2) return fail(RGBA_ERR_INVALID_ARG, "bad loss kind");
+    const Layout &L = k.p.L;
+    float *im = img ? img : reinterpret_cast<float *>(k.ws + L.pix_img);
+    float *T = reinterpret_cast<float *>(k.ws + L.pix_T);
+    int *n = reinterpret_cast<int *>(k.ws + L.pix_n);
+    float *dl = reinterpret_cast<float *>(k.ws + L.pix_dl);
+    if ((rc = do_preprocess(k))) return rc;
+    if ((rc = do_bin_sort(ctx, k))) return rc;
+    if ((rc = do_render_fwd(ctx, k, im, T, n, target, loss_kind, dl))) return rc;
+    return do_render_bwd(ctx, k, dl, T, n);
+}
+
+int rgba_step(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *target,
+              int loss_kind, float *img, rgba_step_out *out, void *stream) {
+    if (!out) return fail(RGBA_ERR_INVALID_ARG, "out is NULL");
+    memset(out, 0, sizeof(*out));
+    int rc = rgba_step_async(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream);
+    if (rc) return rc;
+    if (batch->n_frames == 0) return RGBA_OK;
+    Plan p;
+    make_plan(batch, p);
+    const long long cap = cap_for_bytes(p.L, ws_bytes);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(ctx->pinned, static_cast<unsigned char *>(ws) + p.L.counters, sizeof(rgba_counters),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "read counters");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    const rgba_counters &h = *ctx->pinned;
+    out->loss = h.loss;
+    out->pairs = h.pairs;
+    out->pair_capacity = cap;
+    out->overflow = h.overflow;
+    out->device_error = h.device_error;
+    if (h.overflow) {
+        out->pairs_needed = h.pairs;
+        return fail(RGBA_ERR_CAPACITY, "pair buffer too small: need " + std::to_string(h.pairs) + " pairs");
+    }
+    if (h.device_error) return fail(RGBA_ERR_TIMEOUT, "device loop gave up");
+    return RGBA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,325 @@
+// Backward through the projection (EWA splatting, activations) and the linear blend (Eq. 1).
+//
+// One CTA owns a chunk of 32 Gaussians of one model and walks the frames that render that model
+// in groups of up to 32:
+//   phase 1  per (frame, Gaussian): the 2-D gradients dL/d(u, v, conic, opacity, colour) from
+//            compositing -> dL/dG_b over the 14 blended channels (chain rule through conic
+//            inversion, J W Sigma W^T J^T, R diag(s^2) R^T, quaternion normalisation, exp and
+//            sigmoid), written to shared memory as [frame][channel][Gaussian];
+//   phase 2  the adjoint of Eq. 1 with lane = Gaussian:
+//            dG0[ch][i]    += sum_b dG_b[ch][i]
+//            ddG[k][a][i]  += sum_b psi_b[k] dG_b[ch_a][i]
+//            dpsi_b[k]     partial = sum_{a, i in chunk} dG_k[a][i] dG_b[ch_a][i]
+// The reduction over frames happens in registers in a fixed order, so dG0 and ddG are
+// deterministic; dpsi partials go to a [frame][k][chunk] buffer that a second kernel sums.
+#include "rgba_internal.cuh"
+
+namespace rgba {
+namespace {
+
+constexpr int kFG = 32;          // frames per group
+constexpr int kBwdThreads = 256;
+
+struct Fwd {
+    float p[3], qn[4], qlen, s[3], R[3][3], M[3][3], J[2][3], rx, ry;
+    bool clx, cly;
+    float A, B, C, det;
+};
+
+__device__ __forceinline__ void recompute(const float v[10], const float *V, int W, int H, Fwd &f) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) f.p[j] = V[4 * j] * v[0] + V[4 * j + 1] * v[1] + V[4 * j + 2] * v[2] + V[4 * j + 3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) f.s[m] = expf(v[7 + m]);
+    f.qlen = sqrtf(v[3] * v[3] + v[4] * v[4] + v[5] * v[5] + v[6] * v[6]);
+    const float il = 1.0f / f.qlen;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) f.qn[m] = v[3 + m] * il;
+    const float w = f.qn[0], x = f.qn[1], y = f.qn[2], z = f.qn[3];
+    f.R[0][0] = 1.f - 2.f * (y * y + z * z);
+    f.R[0][1] = 2.f * (x * y - w * z);
+    f.R[0][2] = 2.f * (x * z + w * y);
+    f.R[1][0] = 2.f * (x * y + w * z);
+    f.R[1][1] = 1.f - 2.f * (x * x + z * z);
+    f.R[1][2] = 2.f * (y * z - w * x);
+    f.R[2][0] = 2.f * (x * z - w * y);
+    f.R[2][1] = 2.f * (y * z + w * x);
+    f.R[2][2] = 1.f - 2.f * (x * x + y * y);
+    float Sg[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float a = 0.f;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) a += f.R[i][m] * f.s[m] * f.s[m] * f.R[j][m];
+            Sg[i][j] = a;
+        }
+    float Tm[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Tm[i][j] = V[4 * i] * Sg[0][j] + V[4 * i + 1] * Sg[1][j] + V[4 * i + 2] * Sg[2][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) f.M[i][j] = Tm[i][0] * V[4 * j] + Tm[i][1] * V[4 * j + 1] + Tm[i][2] * V[4 * j + 2];
+    const float fx = V[12], fy = V[13], pz = f.p[2];
+    const float limx = 1.3f * (0.5f * W / fx), limy = 1.3f * (0.5f * H / fy);
+    const float rx = f.p[0] / pz, ry = f.p[1] / pz;
+    f.clx = rx > limx || rx < -limx;
+    f.cly = ry > limy || ry < -limy;
+    f.rx = fminf(limx, fmaxf(-limx, rx));
+    f.ry = fminf(limy, fmaxf(-limy, ry));
+    f.J[0][0] = fx / pz;
+    f.J[0][1] = 0.f;
+    f.J[0][2] = -fx * f.rx / pz;
+    f.J[1][0] = 0.f;
+    f.J[1][1] = fy / pz;
+    f.J[1][2] = -fy * f.ry / pz;
+    float S2[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float a = 0.f;
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) a += f.J[i][p] * f.M[p][q] * f.J[j][q];
+            S2[i][j] = a;
+        }
+    f.A = S2[0][0] + 0.3f;
+    f.B = S2[0][1];
+    f.C = S2[1][1] + 0.3f;
+    f.det = f.A * f.C - f.B * f.B;
+}
+
+// dG[14]: gradient w.r.t. the blended channels of one (frame, Gaussian).
+__device__ __forceinline__ void chain(const float v[10], float op, const float *V, int W, int H,
+                                      const float g2[9], float dG[kNch]) {
+    Fwd f;
+    recompute(v, V, W, H, f);
+    const float du = g2[0], dv = g2[1], dca = g2[2], dcb = g2[3], dcc = g2[4];
+    dG[10] = g2[5] * op * (1.f - op);
+    dG[11] = g2[6];
+    dG[12] = g2[7];
+    dG[13] = g2[8];
+    const float A = f.A, B = f.B, C = f.C, D = f.det, iD = 1.f / D, iD2 = iD * iD;
+    const float dA = dca * (-C * C * iD2) + dcb * (B * C * iD2) + dcc * (iD - A * C * iD2);
+    const float dC = dca * (iD - A * C * iD2) + dcb * (A * B * iD2) + dcc * (-A * A * iD2);
+    const float dB = dca * (2.f * B * C * iD2) + dcb * (-iD - 2.f * B * B * iD2) + dcc * (2.f * A * B * iD2);
+    const float G2[2][2] = {{dA, 0.5f * dB}, {0.5f * dB, dC}};
+    // dJ = 2 G2 J M ; dM = J^T G2 J
+    float GJ[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) GJ[r][c] = G2[r][0] * f.J[0][c] + G2[r][1] * f.J[1][c];
+    float dJ[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dJ[r][c] = 2.f * (GJ[r][0] * f.M[0][c] + GJ[r][1] * f.M[1][c] + GJ[r][2] * f.M[2][c]);
+    float dM[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dM[r][c] = f.J[0][r] * GJ[0][c] + f.J[1][r] * GJ[1][c];
+    // dSigma = V^T dM V
+    float tmp[3][3], dS[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tmp[r][c] = V[r] * dM[0][c] + V[4 + r] * dM[1][c] + V[8 + r] * dM[2][c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dS[r][c] = tmp[r][0] * V[c] + tmp[r][1] * V[4 + c] + tmp[r][2] * V[8 + c];
+    // Sigma = R diag(s^2) R^T
+    float dSR[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) dSR[r][m] = dS[r][0] * f.R[0][m] + dS[r][1] * f.R[1][m] + dS[r][2] * f.R[2][m];
+    float dR[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) dR[r][m] = 2.f * dSR[r][m] * f.s[m] * f.s[m];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const float q = f.R[0][m] * dSR[0][m] + f.R[1][m] * dSR[1][m] + f.R[2][m] * dSR[2][m];
+        dG[7 + m] = 2.f * f.s[m] * q * f.s[m];  // ds * s (s = exp(log-scale))
+    }
+    const float w = f.qn[0], x = f.qn[1], y = f.qn[2], z = f.qn[3];
+    const float dw = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+    const float dx = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] +
+                            z * dR[2][0] + w * dR[2][1] - 2.f * x * dR[2][2]);
+    const float dy = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] -
+                            w * dR[2][0] + z * dR[2][1] - 2.f * y * dR[2][2]);
+    const float dz = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
+                            y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+    const float dot = w * dw + x * dx + y * dy + z * dz;
+    const float il = 1.f / f.qlen;
+    dG[3] = (dw - w * dot) * il;
+    dG[4] = (dx - x * dot) * il;
+    dG[5] = (dy - y * dot) * il;
+    dG[6] = (dz - z * dot) * il;
+    // mean
+    const float fx = V[12], fy = V[13], pz = f.p[2], ipz = 1.f / pz, ipz2 = ipz * ipz;
+    float dp0 = du * fx * ipz, dp1 = dv * fy * ipz;
+    float dp2 = -du * fx * f.p[0] * ipz2 - dv * fy * f.p[1] * ipz2;
+    dp2 += -(dJ[0][0] * fx + dJ[1][1] * fy) * ipz2;
+    if (!f.clx) {
+        dp0 += -dJ[0][2] * fx * ipz2;
+        dp2 += dJ[0][2] * 2.f * fx * f.p[0] * ipz2 * ipz;
+    } else {
+        dp2 += dJ[0][2] * fx * f.rx * ipz2;
+    }
+    if (!f.cly) {
+        dp1 += -dJ[1][2] * fy * ipz2;
+        dp2 += dJ[1][2] * 2.f * fy * f.p[1] * ipz2 * ipz;
+    } else {
+        dp2 += dJ[1][2] * fy * f.ry * ipz2;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dG[c] = V[c] * dp0 + V[4 + c] * dp1 + V[8 + c] * dp2;
+}
+
+__global__ void __launch_bounds__(kBwdThreads)
+k_gauss_bwd(Ctx c, int max_k) {
+    extern __shared__ float smem[];
+    float *s_dG = smem;                               // [kFG][14][32]
+    float *s_psi = smem + kFG * kNch * kBwdChunk;     // [kFG][max_k]
+    const ModelInfo &m = c.models[blockIdx.y];
+    const int chunk = blockIdx.x;
+    const int i0 = chunk * kBwdChunk;
+    if (i0 >= m.n_pad || m.nb == 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = i0 + lane;
+    const bool valid = i < m.n;      // real Gaussian
+    const bool in_pad = i < m.n_pad; // row slot (padding slots receive zeros)
+    const int K = m.k, A = m.A;
+    for (int g0 = 0; g0 < m.nb; g0 += kFG) {
+        const int ng = min(kFG, m.nb - g0);
+        // phase 1: per (frame, Gaussian) chain rule
+        for (int item = threadIdx.x; item < kFG * kBwdChunk; item += kBwdThreads) {
+            const int fl = item / kBwdChunk, li = item % kBwdChunk;
+            float dG[kNch];
+#pragma unroll
+            for (int q = 0; q < kNch; ++q) dG[q] = 0.f;
+            const int gi = i0 + li;
+            if (fl < ng && gi < m.n) {
+                const int b = c.mframes[m.frame_off + g0 + fl];
+                const FrameInfo &f = c.frames[b];
+                const long long r = f.rec_base + gi;
+                const ushort4 rc = c.rects[r];
+                if (rc.z > rc.x && rc.w > rc.y) {
+                    const float4 c0 = c.cache[r * 3 + 0], c1 = c.cache[r * 3 + 1], c2 = c.cache[r * 3 + 2];
+                    const float v[10] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y};
+                    const float4 *gp = reinterpret_cast<const float4 *>(c.grad2d + r * kG2Floats);
+                    const float4 ga = gp[0], gb = gp[1], gc = gp[2];
+                    const float g2[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
+                    const float op = c.records[r * 3 + 1].y;
+                    chain(v, op, c.fparams + (size_t)b * RGBA_FP_STRIDE, f.W, f.H, g2, dG);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kNch; ++q) s_dG[(fl * kNch + q) * kBwdChunk + li] = dG[q];
+        }
+        for (int e = threadIdx.x; e < kFG * max_k; e += kBwdThreads) {
+            const int fl = e / max_k, kk = e % max_k;
+            s_psi[e] = (fl < ng && kk < K) ? c.psi[(size_t)c.mframes[m.frame_off + g0 + fl] * c.k_stride + kk] : 0.f;
+        }
+        __syncthreads();
+        // phase 2a: dG0
+        if (m.gg0 && in_pad) {
+            for (int ch = warp; ch < kNch; ch += kBwdThreads / 32) {
+                float a = 0.f;
+                for (int fl = 0; fl < ng; ++fl) a += s_dG[(fl * kNch + ch) * kBwdChunk + lane];
+                float *o = m.gg0 + (size_t)ch * m.n_pad + i;
+                *o = (g0 == 0 ? 0.f : *o) + a;
+            }
+        }
+        // phase 2b/2c: ddG and dpsi partials, one k per warp iteration
+        for (int kk = warp; kk < K; kk += kBwdThreads / 32) {
+            float psum[kFG];
+#pragma unroll
+            for (int fl = 0; fl < kFG; ++fl) psum[fl] = 0.f;
+            for (int a = 0; a < A; ++a) {
+                const int ch = m.chans[a];
+                const size_t off = ((size_t)kk * A + a) * m.n_pad + i;
+                const float dgv = valid ? __ldg(m.dg + off) : 0.f;
+                float acc = 0.f;
+#pragma unroll
+                for (int fl = 0; fl < kFG; ++fl) {
+                    if (fl < ng) {
+                        const float d = s_dG[(fl * kNch + ch) * kBwdChunk + lane];
+                        acc = fmaf(s_psi[fl * max_k + kk], d, acc);
+                        psum[fl] = fmaf(dgv, d, psum[fl]);
+                    }
+                }
+                if (m.gdg && in_pad) {
+                    float *o = m.gdg + off;
+                    *o = (g0 == 0 ? 0.f : *o) + acc;
+                }
+            }
+            if (c.grad_psi) {
+#pragma unroll
+                for (int fl = 0; fl < kFG; ++fl) {
+                    if (fl < ng) {
+                        float x = psum[fl];
+                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                        if (lane == 0)
+                            c.dpsi_part[m.dpsi_off + ((long long)(g0 + fl) * K + kk) * m.n_chunks + chunk] = x;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// dpsi[b][k] = sum over chunks of the partials; zero for k >= the model's k.
+__global__ void k_dpsi_reduce(Ctx c) {
+    const int b = blockIdx.x;
+    const FrameInfo &f = c.frames[b];
+    const ModelInfo &m = c.models[f.model];
+    // position of frame b in its model's frame list
+    int j = 0;
+    for (int q = 0; q < m.nb; ++q)
+        if (c.mframes[m.frame_off + q] == b) j = q;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int kk = warp; kk < c.k_stride; kk += nw) {
+        float s = 0.f;
+        if (kk < m.k) {
+            const float *p = c.dpsi_part + m.dpsi_off + ((long long)j * m.k + kk) * m.n_chunks;
+            for (int q = lane; q < m.n_chunks; q += 32) s += p[q];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        }
+        if (lane == 0) c.grad_psi[(size_t)b * c.k_stride + kk] = s;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_nb, int max_k, cudaStream_t s) {
+    (void)max_nb;
+    if (c.M == 0 || max_chunks == 0) return cudaSuccess;
+    const int smem = (kFG * kNch * kBwdChunk + kFG * max_k) * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_gauss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(max_chunks, c.M);
+    k_gauss_bwd<<<grid, kBwdThreads, smem, s>>>(c, max_k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s) {
+    (void)max_k;
+    if (!c.grad_psi || c.B == 0) return cudaSuccess;
+    k_dpsi_reduce<<<c.B, 256, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+}  // namespace rgba

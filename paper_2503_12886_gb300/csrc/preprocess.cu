@@ -1,0 +1,314 @@
+// Fused blend + activation + EWA projection + tile binning count (the "preprocess" stage of
+// the batch-parallel rasterizer, RGBAvatar Sec. 3.2 / Supp. A.3, built on 3DGS), and the
+// standalone Eq. 1 blend.
+//
+// Every value that decides a discrete outcome (cull, tile rectangle, depth key) is computed by
+// a fixed sequence of correctly rounded binary32 operations written with explicit-rounding
+// intrinsics, so the compiler can neither contract nor reorder them: any other IEEE-754
+// implementation of the same sequence reproduces the tile lists bit for bit.
+#include <cstring>
+
+#include "rgba_internal.cuh"
+
+namespace rgba {
+namespace {
+
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+
+// exp for the decision path: Cody & Waite (1980) range reduction with ln 2 split into a short
+// head and a tail, the degree-7 Taylor polynomial of e^r in Horner form (|r| <= ln2 / 2),
+// and an exact scaling by 2^n. x < -87 -> 0, x > 88 -> +inf.
+__device__ float exp_spec(float x) {
+    if (x != x) return x;
+    if (x < -87.0f) return 0.0f;
+    if (x > 88.0f) return __int_as_float(0x7f800000);
+    const float log2e = 1.44269504088896341f;
+    const float ln2_hi = 0.693145751953125f;
+    const float ln2_lo = 1.428606765330187045e-06f;
+    float n = rintf(fmul(x, log2e));
+    float r = ffma(-n, ln2_hi, x);
+    r = ffma(-n, ln2_lo, r);
+    float p = 1.0f / 5040.0f;
+    p = ffma(p, r, 1.0f / 720.0f);
+    p = ffma(p, r, 1.0f / 120.0f);
+    p = ffma(p, r, 1.0f / 24.0f);
+    p = ffma(p, r, 1.0f / 6.0f);
+    p = ffma(p, r, 0.5f);
+    p = ffma(p, r, 1.0f);
+    p = ffma(p, r, 1.0f);
+    int e = (int)n;
+    return fmul(p, __int_as_float((e + 127) << 23));
+}
+
+struct UploadBlob {
+    uint4 data[240];  // 3840 bytes per launch
+};
+
+__global__ void k_upload_param(uint4 *dst, UploadBlob blob, int n16) {
+    int i = threadIdx.x;
+    if (i < n16) dst[i] = blob.data[i];
+}
+
+// Blends the 14 channels of Gaussian i for frame b: v = g0; v = fma(psi_k, dG_k, v), k ascending.
+__device__ __forceinline__ void blend14(const ModelInfo &m, const float *__restrict__ psi, int i,
+                                        float v[kNch]) {
+    int a = 0;
+#pragma unroll
+    for (int ch = 0; ch < kNch; ++ch) {
+        float x = __ldg(m.g0 + (size_t)ch * m.n_pad + i);
+        if ((m.mask >> ch) & 1u) {
+            const float *d = m.dg + (size_t)a * m.n_pad + i;
+            const size_t kstep = (size_t)m.A * m.n_pad;
+            for (int kk = 0; kk < m.k; ++kk) x = ffma(psi[kk], __ldg(d + kk * kstep), x);
+            ++a;
+        }
+        v[ch] = x;
+    }
+}
+
+constexpr int kPreThreads = 128;
+
+__global__ void __launch_bounds__(kPreThreads)
+k_preprocess(Ctx c) {
+    __shared__ float s_psi[RGBA_MAX_K];
+    __shared__ float s_fp[RGBA_FP_STRIDE];
+    const int b = blockIdx.y;
+    const FrameInfo f = c.frames[b];
+    const ModelInfo &m = c.models[f.model];
+    for (int t = threadIdx.x; t < f.k; t += blockDim.x) s_psi[t] = c.psi[(size_t)b * c.k_stride + t];
+    if (threadIdx.x < RGBA_FP_STRIDE) s_fp[threadIdx.x] = c.fparams[(size_t)b * RGBA_FP_STRIDE + threadIdx.x];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= f.n) return;
+    const long long r = f.rec_base + i;
+
+    float v[kNch];
+    blend14(m, s_psi, i, v);
+    // backward cache: blended mean, raw quaternion, log-scale
+    c.cache[r * 3 + 0] = make_float4(v[0], v[1], v[2], v[3]);
+    c.cache[r * 3 + 1] = make_float4(v[4], v[5], v[6], v[7]);
+    c.cache[r * 3 + 2] = make_float4(v[8], v[9], 0.f, 0.f);
+
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+    ushort4 rc = make_ushort4(0, 0, 0, 0);
+    const float *V = s_fp;
+    do {
+        // view transform
+        float p[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            p[j] = ffma(V[4 * j + 2], v[2], ffma(V[4 * j + 1], v[1], ffma(V[4 * j + 0], v[0], V[4 * j + 3])));
+        if (!(p[2] > V[16])) break;
+        // scales
+        float s[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) s[q] = exp_spec(v[7 + q]);
+        // quaternion
+        float qw = v[3], qx = v[4], qy = v[5], qz = v[6];
+        float n2 = ffma(qz, qz, ffma(qy, qy, ffma(qx, qx, fmul(qw, qw))));
+        if (!(n2 > 0.0f)) break;
+        float inv = fdiv(1.0f, fsqrt(n2));
+        float w = fmul(qw, inv), x = fmul(qx, inv), y = fmul(qy, inv), z = fmul(qz, inv);
+        float xx = fmul(x, x), yy = fmul(y, y), zz = fmul(z, z);
+        float xy = fmul(x, y), xz = fmul(x, z), yz = fmul(y, z);
+        float wx = fmul(w, x), wy = fmul(w, y), wz = fmul(w, z);
+        float R[3][3];
+        R[0][0] = fsub(1.0f, fmul(2.0f, fadd(yy, zz)));
+        R[0][1] = fmul(2.0f, fsub(xy, wz));
+        R[0][2] = fmul(2.0f, fadd(xz, wy));
+        R[1][0] = fmul(2.0f, fadd(xy, wz));
+        R[1][1] = fsub(1.0f, fmul(2.0f, fadd(xx, zz)));
+        R[1][2] = fmul(2.0f, fsub(yz, wx));
+        R[2][0] = fmul(2.0f, fsub(xz, wy));
+        R[2][1] = fmul(2.0f, fadd(yz, wx));
+        R[2][2] = fsub(1.0f, fmul(2.0f, fadd(xx, yy)));
+        // world covariance
+        float d[3] = {fmul(s[0], s[0]), fmul(s[1], s[1]), fmul(s[2], s[2])};
+        float Mm[3][3], Sg[3][3];
+#pragma unroll
+        for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Mm[ii][q] = fmul(R[ii][q], d[q]);
+#pragma unroll
+        for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj)
+                Sg[ii][jj] = ffma(Mm[ii][2], R[jj][2], ffma(Mm[ii][1], R[jj][1], fmul(Mm[ii][0], R[jj][0])));
+        // camera covariance W Sigma W^T
+        float Tm[3][3], Cm[3][3];
+#pragma unroll
+        for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj)
+                Tm[ii][jj] = ffma(V[4 * ii + 2], Sg[2][jj], ffma(V[4 * ii + 1], Sg[1][jj], fmul(V[4 * ii + 0], Sg[0][jj])));
+#pragma unroll
+        for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj)
+                Cm[ii][jj] = ffma(Tm[ii][2], V[4 * jj + 2], ffma(Tm[ii][1], V[4 * jj + 1], fmul(Tm[ii][0], V[4 * jj + 0])));
+        // EWA Jacobian with the 1.3 x half-fov ratio clamp
+        const float fx = V[12], fy = V[13];
+        float limx = fmul(1.3f, fdiv(fmul(0.5f, (float)f.W), fx));
+        float limy = fmul(1.3f, fdiv(fmul(0.5f, (float)f.H), fy));
+        float rx = fdiv(p[0], p[2]), ry = fdiv(p[1], p[2]);
+        rx = fminf(limx, fmaxf(-limx, rx));
+        ry = fminf(limy, fmaxf(-limy, ry));
+        float J[2][3];
+        J[0][0] = fdiv(fx, p[2]);
+        J[0][1] = 0.0f;
+        J[0][2] = fdiv(-fmul(fx, rx), p[2]);
+        J[1][0] = 0.0f;
+        J[1][1] = fdiv(fy, p[2]);
+        J[1][2] = fdiv(-fmul(fy, ry), p[2]);
+        float Km[2][3], Sp[2][2];
+#pragma unroll
+        for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj)
+                Km[ii][jj] = ffma(J[ii][2], Cm[2][jj], ffma(J[ii][1], Cm[1][jj], fmul(J[ii][0], Cm[0][jj])));
+#pragma unroll
+        for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj)
+                Sp[ii][jj] = ffma(Km[ii][2], J[jj][2], ffma(Km[ii][1], J[jj][1], fmul(Km[ii][0], J[jj][0])));
+        float cA = fadd(Sp[0][0], 0.3f), cB = Sp[0][1], cC = fadd(Sp[1][1], 0.3f);
+        float det = fsub(fmul(cA, cC), fmul(cB, cB));
+        if (!(det > 0.0f)) break;
+        float ca = fdiv(cC, det), cb = fdiv(-cB, det), cc = fdiv(cA, det);
+        float mid = fmul(0.5f, fadd(cA, cC));
+        float lam = fadd(mid, fsqrt(fmaxf(0.1f, fsub(fmul(mid, mid), det))));
+        float rad = ceilf(fmul(3.0f, fsqrt(lam)));
+        float u = fadd(fmul(fx, fdiv(p[0], p[2])), V[14]);
+        float vv = fadd(fmul(fy, fdiv(p[1], p[2])), V[15]);
+        const float ftw = (float)c.tw, fth = (float)c.th;
+        float x0 = floorf(fdiv(fsub(u, rad), ftw));
+        float x1 = floorf(fdiv(fadd(fadd(u, rad), fsub(ftw, 1.0f)), ftw));
+        float y0 = floorf(fdiv(fsub(vv, rad), fth));
+        float y1 = floorf(fdiv(fadd(fadd(vv, rad), fsub(fth, 1.0f)), fth));
+        x0 = fminf((float)f.tiles_x, fmaxf(0.0f, x0));
+        x1 = fminf((float)f.tiles_x, fmaxf(0.0f, x1));
+        y0 = fminf((float)f.tiles_y, fmaxf(0.0f, y0));
+        y1 = fminf((float)f.tiles_y, fmaxf(0.0f, y1));
+        if (x0 != x0 || y0 != y0 || x1 != x1 || y1 != y1) break;
+        int ix0 = (int)x0, ix1 = (int)x1, iy0 = (int)y0, iy1 = (int)y1;
+        if ((ix1 - ix0) * (iy1 - iy0) <= 0) break;
+        float op = fdiv(1.0f, fadd(1.0f, exp_spec(-v[10])));
+        r0 = make_float4(u, vv, ca, cb);
+        r1 = make_float4(cc, op, v[11], v[12]);
+        r2 = make_float4(v[13], p[2], 0.f, 0.f);
+        rc = make_ushort4((unsigned short)ix0, (unsigned short)iy0, (unsigned short)ix1, (unsigned short)iy1);
+        unsigned *tc = c.tile_count + f.tile_base;
+        for (int ty = iy0; ty < iy1; ++ty)
+            for (int tx = ix0; tx < ix1; ++tx) atomicAdd(tc + ty * f.tiles_x + tx, 1u);
+    } while (0);
+    c.records[r * 3 + 0] = r0;
+    c.records[r * 3 + 1] = r1;
+    c.records[r * 3 + 2] = r2;
+    c.rects[r] = rc;
+}
+
+// Standalone Eq. 1 for up to kBlendFrames frames per launch; the frame table travels as a
+// kernel parameter so this entry point needs no workspace.
+constexpr int kBlendFrames = 64;
+struct BlendFrame {
+    const float *g0;
+    const float *dg;
+    const float *psi;
+    float *out;
+    int n, n_pad, k, A;
+    unsigned mask;
+    int pad_;
+};
+struct BlendChunk {
+    BlendFrame f[kBlendFrames];
+};
+
+__global__ void __launch_bounds__(kPreThreads)
+k_blend(BlendChunk ch) {
+    __shared__ float s_psi[RGBA_MAX_K];
+    const BlendFrame &f = ch.f[blockIdx.y];
+    for (int t = threadIdx.x; t < f.k; t += blockDim.x) s_psi[t] = f.psi[t];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= f.n) return;
+    ModelInfo m;
+    m.g0 = f.g0;
+    m.dg = f.dg;
+    m.n = f.n;
+    m.n_pad = f.n_pad;
+    m.k = f.k;
+    m.A = f.A;
+    m.mask = f.mask;
+    float v[kNch];
+    blend14(m, s_psi, i, v);
+#pragma unroll
+    for (int q = 0; q < kNch; ++q) f.out[(size_t)q * f.n_pad + i] = v[q];
+}
+
+}  // namespace
+
+cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    // src is host memory: it travels as kernel parameters (captured by value in graphs).
+    const unsigned char *p = static_cast<const unsigned char *>(src);
+    unsigned char *d = static_cast<unsigned char *>(dst);
+    size_t off = 0;
+    while (off < bytes) {
+        UploadBlob blob;
+        size_t n = bytes - off;
+        if (n > sizeof(blob.data)) n = sizeof(blob.data);
+        size_t n16 = (n + 15) / 16;
+        memset(&blob, 0, sizeof(blob));
+        memcpy(&blob, p + off, n);
+        k_upload_param<<<1, 256, 0, s>>>(reinterpret_cast<uint4 *>(d + off), blob, (int)n16);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        off += n16 * 16;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_preprocess(const Ctx &c, int max_n, cudaStream_t s) {
+    if (c.B == 0 || max_n == 0) return cudaSuccess;
+    dim3 grid((max_n + kPreThreads - 1) / kPreThreads, c.B);
+    k_preprocess<<<grid, kPreThreads, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend(const Ctx &c, int max_n, float *out, cudaStream_t s) {
+    // c.models / c.frames are HOST tables here (rgba_blend has no workspace)
+    for (int f0 = 0; f0 < c.B; f0 += kBlendFrames) {
+        const int nf = min(kBlendFrames, c.B - f0);
+        BlendChunk ch;
+        memset(&ch, 0, sizeof(ch));
+        int mx = 0;
+        for (int j = 0; j < nf; ++j) {
+            const FrameInfo &fi = c.frames[f0 + j];
+            const ModelInfo &m = c.models[fi.model];
+            BlendFrame &bf = ch.f[j];
+            bf.g0 = m.g0;
+            bf.dg = m.dg;
+            bf.psi = c.psi + (size_t)(f0 + j) * c.k_stride;
+            bf.out = out + (size_t)fi.rec_base * kNch;
+            bf.n = m.n;
+            bf.n_pad = m.n_pad;
+            bf.k = m.k;
+            bf.A = m.A;
+            bf.mask = m.mask;
+            mx = max(mx, m.n);
+        }
+        if (mx == 0) continue;
+        dim3 grid((mx + kPreThreads - 1) / kPreThreads, nf);
+        k_blend<<<grid, kPreThreads, 0, s>>>(ch);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    (void)max_n;
+    return cudaSuccess;
+}
+
+}  // namespace rgba

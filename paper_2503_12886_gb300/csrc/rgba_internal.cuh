@@ -1,0 +1,105 @@
+// Internal declarations shared by the CUDA translation units of librgba.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rgba.h"
+
+namespace rgba {
+
+constexpr int kNch = 14;
+constexpr int kRecFloats = 12;   // render record: u, v, a, b, c, o, r, g, b, depth, -, -
+constexpr int kCacheFloats = 12; // backward cache: mean(3), quat(4), log-scale(3), -, -
+constexpr int kG2Floats = 12;    // 2-D gradient: du, dv, da, db, dc, dopacity, dr, dg, db, -
+constexpr int kTilePix = 256;    // pixels per screen tile (16x16 or 8x32)
+constexpr int kBwdChunk = 32;    // Gaussians per CTA in the fused preprocess/blend backward
+
+// Per-model table (device copy in the workspace).
+struct ModelInfo {
+    const float *g0;
+    const float *dg;
+    float *gg0;
+    float *gdg;
+    int n, n_pad, k, A;
+    unsigned mask;
+    int nb;          // frames that render this model
+    int frame_off;   // into the model-frame list
+    int n_chunks;    // ceil(n / kBwdChunk)
+    long long dpsi_off;  // float offset of this model's [n_chunks][nb][k] dpsi partials
+    int chans[kNch]; // blended channel ids, ascending (first A used)
+    int pad_[2];
+};
+
+// Per-frame table (device copy in the workspace).
+struct FrameInfo {
+    int model, W, H, tiles_x;
+    int tiles_y, tile_base, rec_base, n;
+    long long pix_base;  // first pixel of this frame in the concatenated image arrays
+    int n_pad, k;
+};
+
+struct Counters {
+    unsigned pairs;       // pairs needed (saturating)
+    unsigned overflow;
+    unsigned n_work;      // non-empty tiles
+    unsigned device_error;
+    double loss;
+    unsigned next_sort;   // dynamic work counters of the persistent kernels
+    unsigned next_fwd;
+    unsigned next_bwd;
+    unsigned pad_[9];
+};
+static_assert(sizeof(Counters) <= 256, "counters fit in one 256-byte block");
+
+struct Layout {
+    size_t counters, models, frames, mframes, tile_count, tile_start, cursor, work;
+    size_t records, rects, cache, grad2d, pix_T, pix_n, pix_dl, pix_img, dpsi_part;
+    size_t keys, sorted, total;
+    long long R, T, P;     // records, tiles, pixels
+    long long dpsi_floats;
+    long long cap;
+    int B, M, k_stride, tw, th, smem_batch;
+    int max_n_pad;
+};
+
+// Everything a kernel needs to find its data (passed by value).
+struct Ctx {
+    const ModelInfo *models;
+    const FrameInfo *frames;
+    const int *mframes;
+    const float *psi;
+    const float *fparams;
+    float *grad_psi;
+    Counters *cnt;
+    unsigned *tile_count;
+    unsigned *tile_start;
+    unsigned *cursor;
+    unsigned *work;
+    float4 *records;   // [R][3]
+    ushort4 *rects;    // [R]
+    float4 *cache;     // [R][3]
+    float *grad2d;     // [R][12]
+    unsigned long long *keys;
+    unsigned *sorted;
+    float *dpsi_part;
+    long long R, T, cap;
+    int B, M, k_stride, tw, th;
+};
+
+// Launch wrappers (each returns the cudaError_t of its launch).
+cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t s);
+cudaError_t launch_preprocess(const Ctx &c, int max_n, cudaStream_t s);
+cudaError_t launch_blend(const Ctx &c, int max_n, float *out, cudaStream_t s);
+cudaError_t launch_scan(const Ctx &c, cudaStream_t s);
+cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s);
+cudaError_t launch_tile_sort(const Ctx &c, int grid, cudaStream_t s);
+cudaError_t launch_render_fwd(const Ctx &c, int grid, int smem_batch, float *img, float *T_final,
+                              int *n_contrib, const float *target, int loss_kind,
+                              float *dl_dimg, const long long *pix_base_dummy, cudaStream_t s);
+cudaError_t launch_render_bwd(const Ctx &c, int grid, int smem_batch, const float *dl_dimg,
+                              const float *T_final, const int *n_contrib, cudaStream_t s);
+cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_nb, int max_k,
+                             cudaStream_t s);
+cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s);
+
+}  // namespace rgba

@@ -1,0 +1,198 @@
+"""Device-side batches, workspaces and the training/render calls on top of the C ABI.
+
+PyTorch supplies device memory and streams only; all arithmetic happens in librgba.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import api, synth
+
+
+@dataclass
+class DeviceModel:
+    n: int
+    k: int
+    mask: int
+    g0: torch.Tensor        # [14][n_pad]
+    dg: torch.Tensor        # [k][A][n_pad]
+    grad_g0: torch.Tensor | None = None
+    grad_dg: torch.Tensor | None = None
+
+    @property
+    def n_pad(self) -> int:
+        return self.g0.shape[1]
+
+
+class DeviceBatch:
+    """A synth.Batch resident on one CUDA device, plus the ABI descriptor that points at it."""
+
+    def __init__(self, batch: synth.Batch, device="cuda", tile=(16, 16), smem_batch=256,
+                 grads=True, models: list[DeviceModel] | None = None):
+        self.device = torch.device(device)
+        if models is None:
+            models = [DeviceModel(m.n, m.k, m.mask, torch.from_numpy(m.g0).to(self.device),
+                                  torch.from_numpy(m.dg).to(self.device))
+                      for m in batch.models]
+        self.models = models
+        if grads:
+            for m in self.models:
+                if m.grad_g0 is None:
+                    m.grad_g0 = torch.zeros_like(m.g0)
+                    m.grad_dg = torch.zeros_like(m.dg)
+        self.frames = [(f.model, f.width, f.height) for f in batch.frames]
+        self.k_stride = batch.k_stride
+        self.psi = torch.from_numpy(np.ascontiguousarray(batch.psi)).to(self.device)
+        self.fparams = torch.from_numpy(np.ascontiguousarray(batch.fparams)).to(self.device)
+        self.grad_psi = torch.zeros_like(self.psi) if grads else None
+        self.tile = tile
+        self.smem_batch = smem_batch
+        offs, tot = [], 0
+        for _, w, h in self.frames:
+            offs.append(tot)
+            tot += w * h
+        self.pix_offsets = offs
+        self.total_pix = tot
+        rec, rt = [], 0
+        for mi, _, _ in self.frames:
+            rec.append(rt)
+            rt += self.models[mi].n_pad
+        self.rec_offsets = rec
+        self.total_rec = rt
+        self._struct = None
+
+    @property
+    def n_frames(self) -> int:
+        return len(self.frames)
+
+    def struct(self) -> api.RgbaBatch:
+        """ABI descriptor; host arrays are kept alive on this object."""
+        ms = (api.RgbaModel * max(1, len(self.models)))()
+        for i, m in enumerate(self.models):
+            ms[i] = api.RgbaModel(m.n, m.n_pad, m.k, m.mask, m.g0.data_ptr(), m.dg.data_ptr(),
+                                  m.grad_g0.data_ptr() if m.grad_g0 is not None else None,
+                                  m.grad_dg.data_ptr() if m.grad_dg is not None else None)
+        fs = (api.RgbaFrame * max(1, len(self.frames)))()
+        for i, (mi, w, h) in enumerate(self.frames):
+            fs[i] = api.RgbaFrame(mi, w, h)
+        b = api.RgbaBatch()
+        b.n_models = len(self.models)
+        b.models = C.cast(ms, C.POINTER(api.RgbaModel))
+        b.n_frames = len(self.frames)
+        b.frames = C.cast(fs, C.POINTER(api.RgbaFrame))
+        b.k_stride = self.k_stride
+        b.psi = self.psi.data_ptr()
+        b.fparams = self.fparams.data_ptr()
+        b.grad_psi = self.grad_psi.data_ptr() if self.grad_psi is not None else None
+        b.tile_w, b.tile_h = self.tile
+        b.smem_batch = self.smem_batch
+        self._keep = (ms, fs)
+        self._struct = b
+        return b
+
+    # views into the concatenated per-frame image arrays
+    def image_views(self, flat: torch.Tensor) -> list[torch.Tensor]:
+        return [flat[3 * o: 3 * (o + w * h)].view(3, h, w)
+                for o, (_, w, h) in zip(self.pix_offsets, self.frames)]
+
+    def pix_views(self, flat: torch.Tensor) -> list[torch.Tensor]:
+        return [flat[o: o + w * h].view(h, w) for o, (_, w, h) in zip(self.pix_offsets, self.frames)]
+
+    def pack_images(self, imgs) -> torch.Tensor:
+        parts = [torch.as_tensor(np.ascontiguousarray(i), dtype=torch.float32).reshape(-1)
+                 for i in imgs]
+        if not parts:
+            return torch.zeros(0, dtype=torch.float32, device=self.device)
+        return torch.cat(parts).to(self.device)
+
+
+def stream_ptr() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Renderer:
+    """Owns one librgba context and a growable workspace."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.ctx = api.rgba_create(device)
+        self.ws: torch.Tensor | None = None
+
+    def close(self):
+        if self.ctx:
+            api.rgba_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ensure_workspace(self, db: DeviceBatch, pair_capacity: int | None = None) -> torch.Tensor:
+        if pair_capacity is None:
+            pair_capacity = 4 * db.total_rec + 4096
+        need = api.rgba_workspace_size(db.struct(), int(pair_capacity))
+        if self.ws is None or self.ws.numel() < need:
+            self.ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
+        return self.ws
+
+    def layout(self, db: DeviceBatch) -> api.RgbaWsLayout:
+        return api.rgba_workspace_layout(db.struct(), self.ws.numel())
+
+    def counters(self, db: DeviceBatch) -> dict:
+        lay = self.layout(db)
+        raw = self.ws[lay.counters: lay.counters + 24].cpu().numpy()
+        u = raw[:16].view(np.uint32)
+        return {"pairs": int(u[0]), "overflow": int(u[1]), "n_work": int(u[2]),
+                "device_error": int(u[3]), "loss": float(raw[16:24].view(np.float64)[0])}
+
+    def forward(self, db: DeviceBatch, grow: bool = True):
+        """preprocess -> bin/sort -> render; returns (img, T_final, n_contrib) flat tensors.
+        Reads the counters once (the one host sync of this path) to detect a pair overflow."""
+        dev = f"cuda:{self.device}"
+        img = torch.empty(3 * db.total_pix, dtype=torch.float32, device=dev)
+        T = torch.empty(db.total_pix, dtype=torch.float32, device=dev)
+        n = torch.empty(db.total_pix, dtype=torch.int32, device=dev)
+        for _ in range(3):
+            ws = self.ensure_workspace(db)
+            b = db.struct()
+            s = stream_ptr()
+            api.rgba_preprocess(self.ctx, b, ws.data_ptr(), ws.numel(), s)
+            api.rgba_bin_sort(self.ctx, b, ws.data_ptr(), ws.numel(), s)
+            api.rgba_render_fwd(self.ctx, b, ws.data_ptr(), ws.numel(), img.data_ptr(),
+                                T.data_ptr(), n.data_ptr(), s)
+            cnt = self.counters(db) if db.n_frames else {"overflow": 0}
+            if not cnt["overflow"]:
+                return img, T, n
+            if not grow:
+                raise api.RgbaError(api.RGBA_ERR_CAPACITY, f"need {cnt['pairs']} pairs")
+            self.ensure_workspace(db, int(cnt["pairs"] * 1.25) + 4096)
+        raise api.RgbaError(api.RGBA_ERR_CAPACITY, "workspace growth did not converge")
+
+    def backward(self, db: DeviceBatch, dl_dimg: torch.Tensor, T: torch.Tensor, n: torch.Tensor):
+        b = db.struct()
+        api.rgba_render_bwd(self.ctx, b, self.ws.data_ptr(), self.ws.numel(),
+                            dl_dimg.data_ptr(), T.data_ptr(), n.data_ptr(), stream_ptr())
+
+    def blend(self, db: DeviceBatch) -> torch.Tensor:
+        out = torch.zeros(db.total_rec * 14, dtype=torch.float32, device=f"cuda:{self.device}")
+        api.rgba_blend(self.ctx, db.struct(), out.data_ptr(), stream_ptr())
+        return out
+
+    def step(self, db: DeviceBatch, target: torch.Tensor, loss_kind: int = api.RGBA_LOSS_L1,
+             img: torch.Tensor | None = None) -> api.RgbaStepOut:
+        """One training step with a single host sync; grows the workspace on overflow."""
+        for _ in range(3):
+            ws = self.ensure_workspace(db)
+            rc, out = api.rgba_step(self.ctx, db.struct(), ws.data_ptr(), ws.numel(),
+                                    target.data_ptr(), loss_kind,
+                                    img.data_ptr() if img is not None else None, stream_ptr())
+            if rc == api.RGBA_OK:
+                return out
+            self.ensure_workspace(db, int(out.pairs_needed * 1.25) + 4096)
+        raise api.RgbaError(api.RGBA_ERR_CAPACITY, "workspace growth did not converge")

@@ -1,0 +1,145 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI, read its
+intermediate results out of the workspace, run the oracle on the same seeded inputs, and
+compare."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2503_12886_gb300 import api, synth
+from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
+
+# Pixels: the workload tolerance. Gradients: relative bound plus a floor of 1e-3 of the
+# largest reference entry of the same channel, for entries that cancel to near zero.
+PIX_ATOL = 1e-4
+GRAD_RTOL = 1e-3
+GRAD_FLOOR = 1e-3
+# Compositing decisions (alpha >= 1/255, T (1 - alpha) >= 1e-4) that the fp32 GPU path and the
+# fp64 oracle may take differently are flagged by the oracle within this relative margin.
+AMBIG_EPS = 1e-5
+
+
+def run_gpu_forward(batch: synth.Batch, tile=(16, 16), smem_batch=256, renderer=None):
+    r = renderer or Renderer(0)
+    db = DeviceBatch(batch, "cuda:0", tile=tile, smem_batch=smem_batch)
+    img, T, n = r.forward(db)
+    torch.cuda.synchronize()
+    return r, db, img, T, n
+
+
+def read_intermediates(r: Renderer, db: DeviceBatch) -> dict:
+    lay = r.layout(db)
+    ws = r.ws
+    R, Tt = lay.records_total, lay.tiles_total
+
+    def arr(off, nbytes, dt):
+        return ws[off: off + nbytes].cpu().numpy().view(dt)
+
+    rec = arr(lay.records, R * 48, np.float32).reshape(R, 12)
+    rects = arr(lay.rects, R * 8, np.uint16).reshape(R, 4)
+    ts = arr(lay.tile_start, (Tt + 1) * 4, np.uint32)
+    pairs = int(ts[-1])
+    srt = arr(lay.sorted, pairs * 4, np.uint32)
+    g2 = arr(lay.grad2d, R * 48, np.float32).reshape(R, 12)
+    return {"records": rec, "rects": rects, "tile_start": ts, "sorted": srt, "grad2d": g2,
+            "layout": lay}
+
+
+def frame_tile_bases(batch: synth.Batch, tile=(16, 16)):
+    TW, TH = tile
+    out, t = [], 0
+    for fr in batch.frames:
+        out.append(t)
+        t += ((fr.width + TW - 1) // TW) * ((fr.height + TH - 1) // TH)
+    return out
+
+
+def compare_decisions(batch, ores, inter, db, tile=(16, 16)):
+    """Bit-exact: rectangles, fp32 record values, tile list offsets and every list."""
+    bases = frame_tile_bases(batch, tile)
+    TW, TH = tile
+    stats = {"kept": 0, "pairs": 0}
+    for b, fr in enumerate(batch.frames):
+        m = batch.models[fr.model]
+        o = ores[b]
+        rb = db.rec_offsets[b]
+        g_rect = inter["rects"][rb: rb + m.n].astype(np.int32)
+        np.testing.assert_array_equal(g_rect, o.rect, err_msg=f"frame {b} rects")
+        kept = (o.rect[:, 2] > o.rect[:, 0]) & (o.rect[:, 3] > o.rect[:, 1])
+        stats["kept"] += int(kept.sum())
+        g = inter["records"][rb: rb + m.n]
+        # u, v, conic a, b, c, opacity, depth from the fp32 decision spec
+        pairs_cols = [(0, 0), (1, 1), (2, 2), (3, 3), (4, 4), (5, 7), (9, 6)]
+        for gc, oc in pairs_cols:
+            np.testing.assert_array_equal(g[kept, gc].view(np.uint32), o.f32[kept, oc].view(np.uint32),
+                                          err_msg=f"frame {b} record column {gc}")
+        nt = ((fr.width + TW - 1) // TW) * ((fr.height + TH - 1) // TH)
+        ts = inter["tile_start"][bases[b]: bases[b] + nt + 1].astype(np.int64)
+        np.testing.assert_array_equal(ts - ts[0], o.tile_start.astype(np.int64),
+                                      err_msg=f"frame {b} tile offsets")
+        lst = inter["sorted"][ts[0]: ts[-1]].astype(np.int64)
+        np.testing.assert_array_equal(lst, o.lst.astype(np.int64), err_msg=f"frame {b} lists")
+        stats["pairs"] += len(o.lst)
+    return stats
+
+
+def compare_images(batch, ores, db, img, T, n, tiles_only=None):
+    """Pixels within PIX_ATOL and equal contributor counts, except on pixels the oracle flags
+    as ambiguous (a cutoff decision within AMBIG_EPS relative); flagged pixels are counted and
+    still bounded by the size of one flipped contribution."""
+    imgs = db.image_views(img)
+    Ts = db.pix_views(T)
+    ns = db.pix_views(n)
+    out = {"pixels": 0, "flagged": 0, "max_err": 0.0, "max_err_flagged": 0.0, "n_mismatch": 0}
+    for b, fr in enumerate(batch.frames):
+        o = ores[b]
+        if o.img is None:
+            continue
+        gi = imgs[b].cpu().numpy().astype(np.float64)
+        gT = Ts[b].cpu().numpy().astype(np.float64)
+        gn = ns[b].cpu().numpy()
+        mask = np.ones((fr.height, fr.width), bool) if tiles_only is None else tiles_only[b]
+        fl = (o.flags > 0) & mask
+        ok = (~fl) & mask
+        e = np.abs(gi - o.img).max(0)
+        eT = np.abs(gT - o.T)
+        out["pixels"] += int(mask.sum())
+        out["flagged"] += int(fl.sum())
+        if ok.any():
+            out["max_err"] = max(out["max_err"], float(e[ok].max()), float(eT[ok].max()))
+            out["n_mismatch"] += int((gn[ok] != o.n_contrib[ok]).sum())
+        if fl.any():
+            out["max_err_flagged"] = max(out["max_err_flagged"], float(e[fl].max()))
+    return out
+
+
+def grad_error(g: np.ndarray, ref: np.ndarray, axis_rows=True):
+    """max over entries of |g - ref| / (rtol |ref| + floor * max|ref of its row|) (<= 1 passes)."""
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if ref.size == 0:
+        return 0.0
+    rows = ref.reshape(ref.shape[0], -1) if axis_rows else ref.reshape(1, -1)
+    gr = g.reshape(rows.shape)
+    scale = np.abs(rows).max(1, keepdims=True)
+    tol = GRAD_RTOL * np.abs(rows) + GRAD_FLOOR * scale + 1e-30
+    return float((np.abs(gr - rows) / tol).max())
+
+
+def oracle_fwd_bwd(batch, targets, kind, tile=(16, 16)):
+    ores = oracle.forward(batch, tile=tile, eps=AMBIG_EPS)
+    L, dls = oracle.loss(batch, ores, targets, kind)
+    per_model, dpsi, g2s, dgbs = oracle.backward(batch, ores, dls, tile=tile)
+    return ores, L, dls, per_model, dpsi, g2s
+
+
+def gpu_step(batch, targets, kind, tile=(16, 16), smem_batch=256, renderer=None):
+    r = renderer or Renderer(0)
+    db = DeviceBatch(batch, "cuda:0", tile=tile, smem_batch=smem_batch)
+    tg = db.pack_images(targets)
+    img = torch.empty(3 * db.total_pix, dtype=torch.float32, device="cuda:0")
+    lk = api.RGBA_LOSS_L1 if kind == "l1" else api.RGBA_LOSS_L2
+    out = r.step(db, tg, lk, img)
+    torch.cuda.synchronize()
+    return r, db, img, out

@@ -1,0 +1,94 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol include/rgba.h
+declares, and rejects invalid batches on the host before anything is enqueued."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2503_12886_gb300 import api as a
+    a.lib()
+    return a
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "rgba.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rgba_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(api):
+    names = header_functions()
+    assert set(names) == set(api.EXPORTS), names
+    L = api.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def _batch(api, **kw):
+    m = api.RgbaModel(10, 12, 4, 0x3B87, 0x1000, 0x2000, None, None)
+    ms = (api.RgbaModel * 1)(m)
+    fs = (api.RgbaFrame * 1)(api.RgbaFrame(0, 64, 48))
+    b = api.RgbaBatch(1, C.cast(ms, C.POINTER(api.RgbaModel)), 1,
+                      C.cast(fs, C.POINTER(api.RgbaFrame)), 4, 0x3000, 0x4000, None, 16, 16, 256)
+    for k, v in kw.items():
+        setattr(b, k, v)
+    b._keep = (ms, fs)
+    return b, ms, fs
+
+
+def test_workspace_size_grows_with_capacity(api):
+    b, _, _ = _batch(api)
+    s0 = api.rgba_workspace_size(b, 0)
+    s1 = api.rgba_workspace_size(b, 1000)
+    assert s1 >= s0 + 12 * 1000 and s0 > 0
+    lay = api.rgba_workspace_layout(b, s1)
+    assert lay.pair_capacity >= 1000 and lay.records_total == 12
+    assert lay.tiles_total == 4 * 3
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda b, ms, fs: setattr(b, "tile_w", 32), "tile"),
+    (lambda b, ms, fs: setattr(b, "smem_batch", 100), "smem_batch"),
+    (lambda b, ms, fs: setattr(ms[0], "mask", 0x3B87 | (1 << 10)), "opacity"),
+    (lambda b, ms, fs: setattr(ms[0], "n_pad", 10), "n_pad"),
+    (lambda b, ms, fs: setattr(ms[0], "k", 0), "k out of range"),
+    (lambda b, ms, fs: setattr(fs[0], "model", 3), "model index"),
+    (lambda b, ms, fs: setattr(fs[0], "width", 0), "size"),
+    (lambda b, ms, fs: setattr(b, "k_stride", 2), "k_stride"),
+    (lambda b, ms, fs: setattr(b, "psi", None), "psi"),
+    (lambda b, ms, fs: setattr(ms[0], "g0", None), "g0"),
+    (lambda b, ms, fs: setattr(ms[0], "g0", 0x1004), "aligned"),
+])
+def test_invalid_batches_rejected_on_host(api, mutate, msg):
+    b, ms, fs = _batch(api)
+    mutate(b, ms, fs)
+    with pytest.raises(api.RgbaError) as e:
+        api.rgba_workspace_size(b, 100)
+    assert e.value.code == api.RGBA_ERR_INVALID_ARG
+    assert msg in str(e.value)
+
+
+def test_null_arguments(api):
+    L = api.lib()
+    assert L.rgba_workspace_size(None, 10, None) == api.RGBA_ERR_INVALID_ARG
+    assert L.rgba_create(0, None) == api.RGBA_ERR_INVALID_ARG
+    b, _, _ = _batch(api)
+    n = C.c_size_t()
+    assert L.rgba_workspace_size(C.byref(b), -1, C.byref(n)) == api.RGBA_ERR_INVALID_ARG
+    assert L.rgba_workspace_layout(C.byref(b), 16, C.byref(api.RgbaWsLayout())) == \
+        api.RGBA_ERR_INVALID_ARG
+    assert L.rgba_step(None, C.byref(b), None, 0, None, 1, None, None, None) == \
+        api.RGBA_ERR_INVALID_ARG
+
+
+def test_empty_batch_is_a_noop_size(api):
+    b, _, _ = _batch(api, n_frames=0)
+    assert api.rgba_workspace_size(b, 0) > 0

@@ -1,0 +1,138 @@
+"""CUDA path vs the FP64 oracle on the same seeded inputs, through the C ABI.
+
+Bars: bit-exact tile rectangles, fp32 splat values, tile offsets and per-tile sorted lists;
+pixels within 1e-4 (pixels the oracle flags as ambiguous at a cutoff are counted and bounded
+separately); gradients within 1e-3 relative with a per-channel floor (gpu_helpers.grad_error).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2503_12886_gb300 import api, synth
+from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
+
+from gpu_helpers import (PIX_ATOL, compare_decisions, compare_images, grad_error,
+                         oracle_fwd_bwd, read_intermediates, run_gpu_forward)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def renderer():
+    import __graft_entry__
+    __graft_entry__.build()
+    r = Renderer(0)
+    yield r
+    r.close()
+
+
+def ragged_batch():
+    """Three frames of one avatar at ragged sizes (not multiples of the tile), random bg."""
+    m = synth.make_model(77, 3000, 6, log_scale_mu=math.log(5e-3))
+    fr = [synth.Frame(0, 100, 75), synth.Frame(0, 37, 129), synth.Frame(0, 64, 64)]
+    return synth.make_batch([m], fr, seed=77, jitter_deg=15, random_bg=True)
+
+
+def uneven_batch():
+    """Eight avatars (N 1k..5k, K 16/24/32) over 8 frames at 256/512/1024 pixels."""
+    models = [synth.make_model(400 + a, n, k) for a, (n, k) in
+              enumerate([(1000, 16), (1750, 24), (2500, 32), (3250, 16), (4000, 24), (4500, 32),
+                         (4750, 16), (5000, 24)])]
+    res = [256, 512, 1024, 256, 512, 256, 512, 256]
+    fr = [synth.Frame(f % 8, res[f], res[f]) for f in range(8)]
+    return synth.make_batch(models, fr, seed=4000, jitter_deg=20, random_bg=True)
+
+
+CASES = {
+    "single_128": (lambda: synth.workload_single(), (16, 16), 256),
+    "gradcheck_64": (lambda: synth.workload_gradcheck(), (16, 16), 256),
+    "gradcheck_paper_mask": (lambda: synth.workload_gradcheck(mask=synth.MASK_PAPER), (16, 16), 128),
+    "batched_reduced": (lambda: synth.workload_batched(n=20_000, k=32, frames=4, res=256), (16, 16), 256),
+    "ragged_8x32": (ragged_batch, (8, 32), 64),
+    "uneven": (uneven_batch, (16, 16), 128),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_decisions_and_sort_bit_exact(renderer, case):
+    make, tile, sb = CASES[case]
+    batch = make()
+    r, db, img, T, n = run_gpu_forward(batch, tile, sb, renderer)
+    ores = oracle.forward(batch, tile=tile, do_render=False)
+    st = compare_decisions(batch, ores, read_intermediates(r, db), db, tile)
+    assert st["kept"] > 0 and st["pairs"] > 0
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_forward_pixels(renderer, case):
+    make, tile, sb = CASES[case]
+    batch = make()
+    r, db, img, T, n = run_gpu_forward(batch, tile, sb, renderer)
+    ores = oracle.forward(batch, tile=tile, eps=1e-5)
+    st = compare_images(batch, ores, db, img, T, n)
+    assert st["max_err"] <= PIX_ATOL, st
+    assert st["n_mismatch"] == 0, st
+    assert st["flagged"] <= 0.001 * st["pixels"], st
+    assert st["max_err_flagged"] <= 5e-3, st
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_backward_gradients(renderer, case):
+    """Same dL/dimg (the oracle's, from its own image) into both backward passes."""
+    make, tile, sb = CASES[case]
+    batch = make()
+    kind = "l2" if case.startswith("gradcheck") else "l1"
+    targets = synth.make_targets(batch, 99)
+    ores, L, dls, per_model, dpsi, g2s = oracle_fwd_bwd(batch, targets, kind, tile)
+    r, db, img, T, n = run_gpu_forward(batch, tile, sb, renderer)
+    dl = db.pack_images([d.astype(np.float32) for d in dls])
+    r.backward(db, dl, T, n)
+    torch.cuda.synchronize()
+    errs = {}
+    for mi, m in enumerate(db.models):
+        g0_ref, dg_ref = per_model[mi]
+        errs[f"g0[{mi}]"] = grad_error(m.grad_g0.cpu().numpy()[:, :m.n], g0_ref[:, :m.n])
+        errs[f"dg[{mi}]"] = grad_error(m.grad_dg.cpu().numpy()[..., :m.n].reshape(-1, m.n),
+                                       dg_ref[..., :m.n].reshape(-1, m.n))
+        assert np.all(m.grad_g0.cpu().numpy()[:, m.n:] == 0)
+    errs["psi"] = grad_error(db.grad_psi.cpu().numpy(), dpsi, axis_rows=False)
+    assert max(errs.values()) <= 1.0, errs
+
+
+@pytest.mark.parametrize("case", ["single_128", "gradcheck_64", "uneven"])
+def test_step_loss_and_grads(renderer, case):
+    """rgba_step (fused loss, one sync) against the oracle loss and gradients."""
+    make, tile, sb = CASES[case]
+    batch = make()
+    kind = "l2" if case.startswith("gradcheck") else "l1"
+    targets = synth.make_targets(batch, 98)
+    ores, L, dls, per_model, dpsi, g2s = oracle_fwd_bwd(batch, targets, kind, tile)
+    db = DeviceBatch(batch, "cuda:0", tile=tile, smem_batch=sb)
+    tg = db.pack_images(targets)
+    img = torch.empty(3 * db.total_pix, dtype=torch.float32, device="cuda:0")
+    out = renderer.step(db, tg, api.RGBA_LOSS_L1 if kind == "l1" else api.RGBA_LOSS_L2, img)
+    torch.cuda.synchronize()
+    assert abs(out.loss - L) <= 1e-5 * abs(L) + 1e-7, (out.loss, L)
+    assert out.pairs == sum(len(o.lst) for o in ores) and not out.overflow
+    errs = {}
+    for mi, m in enumerate(db.models):
+        g0_ref, dg_ref = per_model[mi]
+        errs[f"g0[{mi}]"] = grad_error(m.grad_g0.cpu().numpy()[:, :m.n], g0_ref[:, :m.n])
+        errs[f"dg[{mi}]"] = grad_error(m.grad_dg.cpu().numpy()[..., :m.n].reshape(-1, m.n),
+                                       dg_ref[..., :m.n].reshape(-1, m.n))
+    errs["psi"] = grad_error(db.grad_psi.cpu().numpy(), dpsi, axis_rows=False)
+    assert max(errs.values()) <= 1.0, errs
+
+
+def test_blend_matches_oracle(renderer):
+    batch = uneven_batch()
+    db = DeviceBatch(batch, "cuda:0")
+    out = renderer.blend(db).cpu().numpy()
+    for b, fr in enumerate(batch.frames):
+        m = batch.models[fr.model]
+        ref = oracle.blend(m.g0, m.dg, batch.psi[b, :m.k], m.n, m.mask)
+        got = out[db.rec_offsets[b] * 14: (db.rec_offsets[b] + m.n_pad) * 14].reshape(14, m.n_pad)
+        np.testing.assert_allclose(got[:, :m.n], ref[:, :m.n], rtol=0, atol=2e-6)
