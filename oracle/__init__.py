@@ -61,7 +61,7 @@ def lib():
             L.orc_project_bwd.argtypes = [i32, i32, P, P, i32, i32, P, P, P]
             L.orc_bin.argtypes = [i32, P, P, i32, i32, P, P]
             L.orc_bin.restype = C.c_int64
-            L.orc_render.argtypes = [i32, i32, i32, i32, P, P, P, P, P, f64, P, P, P, P, P]
+            L.orc_render.argtypes = [i32, i32, i32, i32, P, P, P, P, P, f64, f64, P, P, P, P, P]
             L.orc_render.restype = C.c_uint64
             L.orc_render_bwd.argtypes = [i32, i32, i32, i32, P, P, P, P, P, P, P]
             _lib = L
@@ -132,7 +132,7 @@ def bin_sort(rect, depth, tiles_x, tiles_y):
     return ts, lst[:total]
 
 
-def render(W, H, TW, TH, rec, tile_start, lst, bg, tile_mask=None, eps=1e-5):
+def render(W, H, TW, TH, rec, tile_start, lst, bg, tile_mask=None, eps=1e-5, eps_t=1e-4):
     img = np.zeros((3, H, W), np.float64)
     T = np.ones((H, W), np.float64)
     nc = np.zeros((H, W), np.int32)
@@ -142,7 +142,7 @@ def render(W, H, TW, TH, rec, tile_start, lst, bg, tile_mask=None, eps=1e-5):
     lst = np.ascontiguousarray(lst if len(lst) else np.zeros(1, np.int32), np.int32)
     tm = None if tile_mask is None else np.ascontiguousarray(tile_mask, np.uint8)
     h = lib().orc_render(W, H, TW, TH, _p(rec), _p(tile_start), _p(lst), _p(bg), _p(tm), eps,
-                         _p(img), _p(T), _p(nc), _p(flags), _p(stats))
+                         eps_t, _p(img), _p(T), _p(nc), _p(flags), _p(stats))
     return img, T, nc, flags, int(h), stats
 
 
@@ -192,11 +192,18 @@ class FrameResult:
 
 
 def forward(batch, tile=(16, 16), render_frames=None, tile_masks=None, eps=1e-5,
-            params=None, do_render=True):
+            params=None, do_render=True, splat="f64", eps_t=1e-4):
     """Run the forward for every frame of a synth.Batch.
 
     params (optional, FP64 overrides for finite differences): {"g0": [per model], "dg": [...],
     "psi": [B][k_stride]}. The FP32 decision spec reads the same values rounded to fp32.
+
+    splat: "f64" composites the FP64 projection of every Gaussian (the pure FP64 function of
+    the parameters, used by the closed-form and finite-difference pins); "spec" composites the
+    mean, conic and opacity that the FP32 decision spec computes (the same values that define
+    the tile rectangles), widened to FP64, with FP64 colours. Parity with the fp32 GPU path
+    uses "spec": at 1024 px the fp32 rounding of a screen mean alone (up to 7e-5 px) moves
+    alpha by more than the ambiguity margin around the 1/255 cutoff.
     """
     TW, TH = tile
     params = params or {}
@@ -212,6 +219,12 @@ def forward(batch, tile=(16, 16), render_frames=None, tile_masks=None, eps=1e-5,
                            fp, m.n, m.mask, W, H, TW, TH)
         bl = blend(g0, dg, psi, m.n, m.mask)
         rec = project(bl, fp, m.n, W, H, rect)
+        if splat == "spec":
+            kept = (rect[:, 2] > rect[:, 0]) & (rect[:, 3] > rect[:, 1])
+            rec[kept, 0:5] = f32[kept, 0:5]
+            rec[kept, 5] = f32[kept, 7]
+        elif splat != "f64":
+            raise ValueError(splat)
         tx, ty = (W + TW - 1) // TW, (H + TH - 1) // TH
         ts, lst = bin_sort(rect, f32[:, 6], tx, ty)
         fr_res = FrameResult(rect, f32, bl, rec, ts, lst)
@@ -219,7 +232,7 @@ def forward(batch, tile=(16, 16), render_frames=None, tile_masks=None, eps=1e-5,
             tm = None if tile_masks is None else tile_masks.get(b)
             bg = fp[17:20].astype(np.float64)
             (fr_res.img, fr_res.T, fr_res.n_contrib, fr_res.flags, fr_res.hash,
-             fr_res.stats) = render(W, H, TW, TH, rec, ts, lst, bg, tm, eps)
+             fr_res.stats) = render(W, H, TW, TH, rec, ts, lst, bg, tm, eps, eps_t)
         out.append(fr_res)
     return out
 

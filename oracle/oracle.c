@@ -571,12 +571,14 @@ static inline uint64_t fnv(uint64_t h, uint64_t v) {
     return h;
 }
 
-/* tile_mask (may be NULL): render only tiles with a non-zero byte.  eps: relative distance to a
- * cutoff below which a pixel is flagged ambiguous.  stats[0] += list entries evaluated,
- * stats[1] += pixels rendered.  Returns the decision hash of the rendered pixels.              */
+/* tile_mask (may be NULL): render only tiles with a non-zero byte.  eps / eps_t: relative
+ * distance to an alpha cutoff / to the transmittance cutoff below which a pixel is flagged
+ * ambiguous.  stats[0] += list entries evaluated, stats[1] += pixels rendered.  Returns the
+ * decision hash of the rendered pixels.                                                        */
 uint64_t orc_render(int W, int H, int TW, int TH, const double *rec, const int32_t *tile_start,
                     const int32_t *list, const double *bg, const uint8_t *tile_mask, double eps,
-                    double *img, double *T_out, int32_t *n_out, uint8_t *flags, double *stats) {
+                    double eps_t, double *img, double *T_out, int32_t *n_out, uint8_t *flags,
+                    double *stats) {
     int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
     uint64_t hash = 0xCBF29CE484222325ull;
     for (int ty = 0; ty < tiles_y; ++ty)
@@ -607,7 +609,7 @@ uint64_t orc_render(int W, int H, int TW, int TH, const double *rec, const int32
                             continue;
                         }
                         double testT = T * (1.0 - alpha);
-                        if (fabs(testT - T_MIN) <= eps * T_MIN) fl |= FLAG_T_MIN;
+                        if (fabs(testT - T_MIN) <= eps_t * T_MIN) fl |= FLAG_T_MIN;
                         if (testT < T_MIN) {
                             hash = fnv(hash, ((uint64_t)j << 4) | 3u);
                             break;

@@ -71,7 +71,7 @@ def test_forward_pixels(renderer, case):
     make, tile, sb = CASES[case]
     batch = make()
     r, db, img, T, n = run_gpu_forward(batch, tile, sb, renderer)
-    ores = oracle.forward(batch, tile=tile, eps=1e-5)
+    ores = oracle.forward(batch, tile=tile, splat="spec")
     st = compare_images(batch, ores, db, img, T, n)
     assert st["max_err"] <= PIX_ATOL, st
     assert st["n_mismatch"] == 0, st
@@ -135,4 +135,10 @@ def test_blend_matches_oracle(renderer):
         m = batch.models[fr.model]
         ref = oracle.blend(m.g0, m.dg, batch.psi[b, :m.k], m.n, m.mask)
         got = out[db.rec_offsets[b] * 14: (db.rec_offsets[b] + m.n_pad) * 14].reshape(14, m.n_pad)
-        np.testing.assert_allclose(got[:, :m.n], ref[:, :m.n], rtol=0, atol=2e-6)
+        # fp32 fused multiply-add chain over k terms: each step rounds once
+        mag = np.abs(m.g0.astype(np.float64)).copy()
+        chans = synth.blended_channels(m.mask)
+        mag[chans] += np.einsum("k,kan->an", np.abs(batch.psi[b, :m.k].astype(np.float64)),
+                                np.abs(m.dg.astype(np.float64)))
+        bound = (m.k + 1) * 2.0 ** -24 * mag
+        assert (np.abs(got[:, :m.n] - ref[:, :m.n]) <= bound[:, :m.n]).all()

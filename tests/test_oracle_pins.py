@@ -416,3 +416,22 @@ def test_fd_gradients_clamps_active():
             checked += 1
             assert abs(fd - an) <= 2e-4 * abs(an) + 1e-9, (i, ch, fd, an)
     assert checked > 60
+
+
+# --------------------------------------------------------------------------------------------
+# The FP32 decision spec tracks the FP64 projection it stands in for.
+
+@pytest.mark.parametrize("res", [128, 1024])
+def test_decision_spec_tracks_fp64_projection(res):
+    m = synth.make_model(13, 4000, 8)
+    batch = synth.make_batch([m], [synth.Frame(0, res, res)], seed=13, jitter_deg=20)
+    r = oracle.forward(batch, do_render=False)[0]
+    kept = (r.rect[:, 2] > r.rect[:, 0]) & (r.rect[:, 3] > r.rect[:, 1])
+    assert kept.sum() > 3000
+    f, d = r.f32[kept].astype(np.float64), r.rec[kept]
+    np.testing.assert_allclose(f[:, 0:2], d[:, 0:2], rtol=0, atol=4 * res * 2.0 ** -24 * 2)
+    for c in range(2, 5):  # conic a, b, c relative to the conic's scale
+        scale = np.abs(d[:, [2, 4]]).max(1)
+        assert (np.abs(f[:, c] - d[:, c]) <= 1e-5 * scale).all(), c
+    np.testing.assert_allclose(f[:, 6], d[:, 9], rtol=1e-6)
+    np.testing.assert_allclose(f[:, 7], d[:, 5], rtol=0, atol=1e-6)
