@@ -1,0 +1,445 @@
+#!/usr/bin/env python3
+"""Benchmark of the batch-parallel differentiable Gaussian blendshape rasterizer on one GB300.
+
+Default workload: one batched training step (fused blend + EWA preprocess, bin/sort,
+compositing with fused L1 loss, full backward to G0, blendshapes and weights) over B=16 frames
+at 512x512 of one N=60,000-Gaussian avatar with K=32 blendshapes, yaw/pitch jitter of +-20 deg
+and a random background per frame, replayed as a CUDA graph with a single host synchronisation
+per step (RGBAvatar Sec. 3.2, Fig. 4c, Table 5). Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The reference arm (--impl reference) times the FP64 CPU oracle on the host cores, one frame of
+the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("train img/s (fwd+bwd, batched) & serve frames/s + p99 ms vs per-frame path, 1 GB300")
+WORKLOAD = ("batched training step: N=60,000 Gaussians, K=32 blendshapes (mean, log-scale, "
+            "colour blended), B=16 frames at 512x512 per launch, per-frame weights N(0,0.3), "
+            "camera yaw/pitch jitter U[-20,20] deg, random background, L1 loss, fused fwd+bwd to "
+            "G0 / blendshapes / weights, CUDA-graph replay, one host sync per step")
+N_GAUSS, K_BASES, FRAMES, RES = 60_000, 32, 16, 512
+# FP32 FLOPs the compositing backward spends per (pixel, list entry up to the pixel's last
+# contributor): alpha recompute 15, transmittance recovery 2, colour/alpha/background terms 23,
+# conic/mean/opacity terms 19 (counted from the kernel's arithmetic; a fused multiply-add is 2).
+BWD_FLOPS_PER_UNIT = 59
+FWD_FLOPS_PER_UNIT = 20
+SMS, FP32_LANES = 152, 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--variants", type=int, default=4, help="distinct resident input batches")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-per-frame", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the GPU works."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel: str, src_file: str):
+    """DRAM bytes per launch from the committed ncu summary, only while the kernel source is
+    unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f).get(kernel)
+    if not d:
+        return None
+    with open(os.path.join(ROOT, "paper_2503_12886_gb300", "csrc", src_file), "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    return d.get("dram_bytes_per_launch") if d.get("src_sha1") == sha else None
+
+
+# ---------------------------------------------------------------------------------------------
+def make_workload(seed_base=3000, variants=4):
+    from paper_2503_12886_gb300 import synth
+    model = synth.make_model(seed_base, N_GAUSS, K_BASES)
+    frames = [synth.Frame(0, RES, RES) for _ in range(FRAMES)]
+    out = []
+    for j in range(variants):
+        b = synth.make_batch([model], frames, seed_base + 101 * (j + 1), jitter_deg=20.0,
+                             random_bg=True)
+        out.append((b, synth.make_targets(b, seed_base + 7 * (j + 1))))
+    return out
+
+
+def cpu_baseline_sample(batch, targets):
+    """The oracle, as it stands (single thread), on frame 0 of the workload: fwd + loss + bwd."""
+    import oracle
+    from paper_2503_12886_gb300 import synth
+    one = synth.Batch(models=batch.models, frames=batch.frames[:1], psi=batch.psi[:1],
+                      fparams=batch.fparams[:1], k_stride=batch.k_stride)
+    t0 = time.perf_counter()
+    res = oracle.forward(one)
+    _, dls = oracle.loss(one, res, targets[:1], "l1")
+    oracle.backward(one, res, dls)
+    return time.perf_counter() - t0
+
+
+_REF = {}
+
+
+def _ref_init():
+    sys.path.insert(0, ROOT)
+    _REF["work"] = make_workload(variants=1)[0]
+
+
+def _ref_frame(f):
+    from paper_2503_12886_gb300 import synth
+    batch, targets = _REF["work"]
+    sub = synth.Batch(batch.models, batch.frames[f:f + 1], batch.psi[f:f + 1],
+                      batch.fparams[f:f + 1], batch.k_stride)
+    return cpu_baseline_sample(sub, targets[f:f + 1])
+
+
+def run_reference(args, rank, world):
+    """The oracle on every host core: each step is one frame of the workload (fwd + loss + bwd)
+    handed to a pool of single-threaded worker processes."""
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores, initializer=_ref_init) as pool:
+        pool.map(_ref_frame, [i % FRAMES for i in range(max(args.warmup, cores))], chunksize=1)
+        t0 = time.perf_counter()
+        per = pool.map(_ref_frame, [i % FRAMES for i in range(args.steps)], chunksize=1)
+        t = time.perf_counter() - t0
+    value = args.steps / t
+    sample = (f"{args.steps} frames (one per step) of the batched workload (512x512, N=60,000, "
+              f"K=32): oracle FP64 fwd + L1 loss + bwd, {cores} single-threaded worker processes")
+    line = {"metric": METRIC, "value": value, "unit": "img/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": None,
+                       "parallelism": f"{cores} host processes"},
+            "cpu_baseline": {"value": value, "unit": "img/s", "cores": cores, "kind": "oracle",
+                             "sample": sample, "seconds_per_frame_one_core": sum(per) / len(per)},
+            "e2e": {"value": value, "unit": "img/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.set_device(local_rank)
+    from paper_2503_12886_gb300 import api
+    from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
+
+    dev = f"cuda:{local_rank}"
+    work = make_workload(variants=args.variants)
+    r = Renderer(local_rank)
+    dbs, tgs = [], []
+    for j, (b, tg) in enumerate(work):
+        db = DeviceBatch(b, dev, models=dbs[0].models if dbs else None)
+        dbs.append(db)
+        tgs.append(db.pack_images(tg))
+    img = torch.empty(3 * dbs[0].total_pix, dtype=torch.float32, device=dev)
+    # size the workspace from eager steps (+10 % headroom), then capture one graph per variant
+    pairs = max(r.step(db, tg, api.RGBA_LOSS_L1, img).pairs for db, tg in zip(dbs, tgs))
+    ws = r.ensure_workspace(dbs[0], int(pairs * 1.1) + 4096)
+    lay = r.layout(dbs[0])
+    host_cnt = [torch.zeros(24, dtype=torch.uint8).pin_memory() for _ in dbs]
+    structs = [db.struct() for db in dbs]
+    s = torch.cuda.Stream(device=dev)
+    graphs = []
+    with torch.cuda.stream(s):
+        for j, db in enumerate(dbs):  # eager once on the capture stream
+            api.rgba_step_async(r.ctx, structs[j], ws.data_ptr(), ws.numel(), tgs[j].data_ptr(),
+                                api.RGBA_LOSS_L1, img.data_ptr(), s.cuda_stream)
+        s.synchronize()
+        for j, db in enumerate(dbs):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                api.rgba_step_async(r.ctx, structs[j], ws.data_ptr(), ws.numel(),
+                                    tgs[j].data_ptr(), api.RGBA_LOSS_L1, img.data_ptr(),
+                                    s.cuda_stream)
+                host_cnt[j].copy_(ws[lay.counters: lay.counters + 24], non_blocking=True)
+            graphs.append(g)
+    torch.cuda.synchronize()
+
+    def step(i):
+        graphs[i % len(graphs)].replay()
+        s.synchronize()  # the one host synchronisation of the step
+        u = host_cnt[i % len(graphs)][:8].numpy().view(np.uint32)
+        if u[1]:
+            raise RuntimeError("pair buffer overflow inside the timed region")
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    with torch.cuda.stream(s):
+        for i in range(args.warmup):
+            step(i)
+        t_end = time.perf_counter() + 1.0  # keep the GPU busy while the sampler starts
+        i = 0
+        while time.perf_counter() < t_end:
+            step(i)
+            i += 1
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for i in range(args.steps):
+            step(i)
+        e1.record(s)
+        torch.cuda.synchronize()
+    ck = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * FRAMES * args.steps / elapsed
+    ms_per_step = 1e3 * elapsed / args.steps
+    last_loss = float(host_cnt[(args.steps - 1) % len(graphs)][8:16].numpy().view(np.float64)[0])
+
+    # per-stage device time (CUDA events on the launching stream), eager steps
+    api.rgba_profile_enable(r.ctx, True)
+    prof = []
+    with torch.cuda.stream(s):
+        for j in range(len(dbs)):
+            api.rgba_step_async(r.ctx, structs[j], ws.data_ptr(), ws.numel(), tgs[j].data_ptr(),
+                                api.RGBA_LOSS_L1, img.data_ptr(), s.cuda_stream)
+            prof.append(api.rgba_profile_read(r.ctx))
+    api.rgba_profile_enable(r.ctx, False)
+    stage_ms = {k: float(np.mean([p[k] for p in prof])) for k in api.STAGES}
+    launches_per_step = prof[-1]["launches"]
+    # units of the compositing backward of the last profiled step: sum over pixels of
+    # n_contrib, which rgba_step keeps in the workspace
+    P = dbs[-1].total_pix
+    units_bwd = int(ws[lay.pix_n: lay.pix_n + 4 * P].view(torch.int32).sum(dtype=torch.int64))
+    peaks, peak_kind = load_peaks()
+    dominant = max(stage_ms, key=lambda k: stage_ms[k])
+    clock_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+    roof = None
+    if dominant == "render_bwd":
+        ach = units_bwd * BWD_FLOPS_PER_UNIT / (stage_ms["render_bwd"] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_render_bwd", "achieved": ach,
+                "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops,
+                "traffic": traffic_for("render_bwd", "render.cu"),
+                "peak_source": f"FP32 lanes x 2 x {clock_mhz:.0f} MHz (recipe unit counts)",
+                "units": units_bwd, "flops_per_unit": BWD_FLOPS_PER_UNIT}
+    else:
+        ach_ms = stage_ms[dominant]
+        roof = {"bound": "alu", "kernel": dominant, "achieved": None, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": None, "traffic": None, "note": f"{ach_ms:.3f} ms"}
+    # HBM-bound stages, algorithmic bytes
+    R = dbs[0].total_rec
+    A, K = 9, K_BASES
+    pre_bytes = 4 * N_GAUSS * (14 + K * A) + R * (48 + 8 + 48)
+    gbwd_bytes = 4 * N_GAUSS * (14 + 2 * K * A) + R * (48 + 48 + 8 + 12) + FRAMES * K * 4
+    stages = {k: {"ms": v} for k, v in stage_ms.items()}
+    stages["preprocess"]["GB/s"] = pre_bytes / (stage_ms["preprocess"] / 1e3) / 1e9
+    stages["preprocess"]["frac_hbm"] = stages["preprocess"]["GB/s"] / peaks["hbm_gbs"]
+    stages["gauss_bwd"]["GB/s"] = gbwd_bytes / (stage_ms["gauss_bwd"] / 1e3) / 1e9
+    stages["gauss_bwd"]["frac_hbm"] = stages["gauss_bwd"]["GB/s"] / peaks["hbm_gbs"]
+
+    # end to end through the C ABI with host buffers: per step the inputs (targets, weights,
+    # cameras) travel from pinned host memory, rgba_step runs and reads its result back
+    host_in = []
+    for db, (b, tg) in zip(dbs, work):
+        host_in.append((tgs[dbs.index(db)].cpu().pin_memory(), db.psi.cpu().pin_memory(),
+                        db.fparams.cpu().pin_memory()))
+    h2d = sum(x.numel() * x.element_size() for x in host_in[0])
+    with torch.cuda.stream(s):
+        for i in range(3):
+            e2e_step(api, r, dbs, tgs, structs, host_in, ws, img, s, i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = max(10, min(args.steps, 100))
+        for i in range(n_e2e):
+            e2e_step(api, r, dbs, tgs, structs, host_in, ws, img, s, i)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+    e2e_value = world * FRAMES * n_e2e / t_e2e
+
+    # the plain per-frame path (Fig. 4a): every frame its own step with its own host sync
+    per_frame = None
+    if not args.no_per_frame:
+        per_frame = per_frame_path(api, work[0], dev, r)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        b0, t0s = work[0]
+        tcpu = cpu_baseline_sample(b0, t0s)
+        cpu = {"value": 1.0 / tcpu, "unit": "img/s", "cores": 1, "kind": "oracle",
+               "sample": "frame 0 of the batched workload (one 512x512 frame of the N=60,000, "
+                         "K=32 avatar): FP64 fwd + L1 loss + bwd, single thread",
+               "seconds": tcpu}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "img/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded generator, random-init avatar)",
+                "config": {"workload": WORKLOAD, "global_batch": FRAMES * world, "seq_len": None,
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "n_gaussians": N_GAUSS, "k": K_BASES, "resolution": RES,
+                           "input_variants": len(dbs),
+                           "l2": "inputs larger than L2 (bases 69 MB + targets 50 MB + "
+                                 "per-step intermediates ~0.4 GB per variant, 4 variants cycled)",
+                           "pairs_per_step": int(pairs), "last_loss": last_loss},
+                "roofline": roof, "stages": stages,
+                "peaks": {"kind": peak_kind, "hbm_gbs": peaks.get("hbm_gbs"),
+                          "fp32_tflops_nominal": fp32_peak_tflops},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": "img/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": 24, "steps": n_e2e,
+                        "path": "rgba_step through the C ABI, inputs copied from pinned host"},
+                "per_frame": per_frame,
+                "speedup_vs_per_frame": (value / per_frame["value"]) if per_frame else None,
+                "gpu_launches": launches_per_step * args.steps,
+                "launches_per_step": launches_per_step,
+                "clocks": ck}
+        print(json.dumps(line), flush=True)
+    r.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e_step(api, r, dbs, tgs, structs, host_in, ws, img, s, i):
+    j = i % len(dbs)
+    tg_h, psi_h, fp_h = host_in[j]
+    tgs[j].copy_(tg_h, non_blocking=True)
+    dbs[j].psi.copy_(psi_h, non_blocking=True)
+    dbs[j].fparams.copy_(fp_h, non_blocking=True)
+    rc, out = api.rgba_step(r.ctx, structs[j], ws.data_ptr(), ws.numel(), tgs[j].data_ptr(),
+                            api.RGBA_LOSS_L1, img.data_ptr(), s.cuda_stream)
+    if rc != api.RGBA_OK:
+        raise RuntimeError("e2e step overflowed")
+    return out
+
+
+def per_frame_path(api, work0, dev, r):
+    import torch
+    from paper_2503_12886_gb300 import synth
+    from paper_2503_12886_gb300.rasterizer import DeviceBatch
+    batch, targets = work0
+    singles = []
+    base = None
+    for f in range(FRAMES):
+        sub = synth.Batch(batch.models, batch.frames[f:f + 1], batch.psi[f:f + 1],
+                          batch.fparams[f:f + 1], batch.k_stride)
+        db = DeviceBatch(sub, dev, models=base)
+        base = db.models
+        singles.append((db, db.pack_images(targets[f:f + 1])))
+    img = torch.empty(3 * RES * RES, dtype=torch.float32, device=dev)
+    for db, tg in singles[:3]:
+        r.step(db, tg, api.RGBA_LOSS_L1, img)
+    torch.cuda.synchronize()
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for db, tg in singles:
+            r.step(db, tg, api.RGBA_LOSS_L1, img)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    return {"value": reps * FRAMES / t, "unit": "img/s",
+            "path": "one frame per rgba_step (B=1), one host sync per frame"}
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -115,6 +115,10 @@ typedef struct {
     size_t tile_start;   /* uint32[T + 1]: start of each (frame, tile) list */
     size_t sorted;       /* uint32[capacity]: Gaussian index per list entry */
     size_t grad2d;       /* float[R][12]: dL/d(u, v, conic a, b, c, opacity, r, g, b) */
+    size_t pix_T;        /* float[P]: T_final of rgba_step (P = total pixels of the batch) */
+    size_t pix_n;        /* int32[P]: n_contrib of rgba_step */
+    size_t pix_dl;       /* float[3P]: dL/dimg of rgba_step's fused loss */
+    size_t pix_img;      /* float[3P]: image of rgba_step when its img argument is NULL */
     size_t total_bytes;
     int64_t records_total;   /* R = sum over frames of the model's n_pad; frame b starts at
                                 the sum of n_pad over frames before b */
@@ -187,6 +191,23 @@ int rgba_step(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes
  * workspace's rgba_counters. */
 int rgba_step_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
                     const float *target, int loss_kind, float *img, void *stream);
+
+/* Per-stage device timing with CUDA events on the call's stream (off by default). Stages, in
+ * launch order: 0 table upload, 1 preprocess (fused blend + projection), 2 tile-count scan,
+ * 3 pair scatter, 4 per-tile depth sort, 5 compositing forward (+ fused loss), 6 compositing
+ * backward, 7 projection + blend backward, 8 weight-gradient reduction. Do not enable it while
+ * capturing a CUDA graph. */
+#define RGBA_N_STAGES 9
+
+typedef struct {
+    float ms[RGBA_N_STAGES];  /* last recorded duration of each stage; -1 if not recorded */
+    int32_t launches;         /* kernel launches enqueued since the previous read */
+    int32_t pad_;
+} rgba_profile;
+
+int rgba_profile_enable(rgba_ctx_t ctx, int on);
+/* Waits for the recorded events, fills `out` (host) and resets the launch count. */
+int rgba_profile_read(rgba_ctx_t ctx, rgba_profile *out);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,11 @@ RGBA_NCH = 14
 # every symbol include/rgba.h declares
 EXPORTS = ("rgba_last_error", "rgba_create", "rgba_destroy", "rgba_workspace_size",
            "rgba_workspace_layout", "rgba_blend", "rgba_preprocess", "rgba_bin_sort",
-           "rgba_render_fwd", "rgba_render_bwd", "rgba_step", "rgba_step_async")
+           "rgba_render_fwd", "rgba_render_bwd", "rgba_step", "rgba_step_async",
+           "rgba_profile_enable", "rgba_profile_read")
+RGBA_N_STAGES = 9
+STAGES = ("upload", "preprocess", "scan", "scatter", "sort", "render_fwd", "render_bwd",
+          "gauss_bwd", "dpsi_reduce")
 
 
 class RgbaModel(C.Structure):
@@ -54,8 +58,13 @@ class RgbaStepOut(C.Structure):
 class RgbaWsLayout(C.Structure):
     _fields_ = [("counters", C.c_size_t), ("records", C.c_size_t), ("rects", C.c_size_t),
                 ("tile_start", C.c_size_t), ("sorted", C.c_size_t), ("grad2d", C.c_size_t),
-                ("total_bytes", C.c_size_t), ("records_total", C.c_int64),
+                ("pix_T", C.c_size_t), ("pix_n", C.c_size_t), ("pix_dl", C.c_size_t),
+                ("pix_img", C.c_size_t), ("total_bytes", C.c_size_t), ("records_total", C.c_int64),
                 ("tiles_total", C.c_int64), ("pair_capacity", C.c_int64)]
+
+
+class RgbaProfile(C.Structure):
+    _fields_ = [("ms", C.c_float * RGBA_N_STAGES), ("launches", C.c_int32), ("pad_", C.c_int32)]
 
 
 class RgbaError(RuntimeError):
@@ -91,7 +100,9 @@ def lib() -> C.CDLL:
             L.rgba_render_bwd.argtypes = [P, Bp, P, sz, P, P, P, P]
             L.rgba_step.argtypes = [P, Bp, P, sz, P, i32, P, C.POINTER(RgbaStepOut), P]
             L.rgba_step_async.argtypes = [P, Bp, P, sz, P, i32, P, P]
-            for name in ("rgba_create", "rgba_workspace_size", "rgba_workspace_layout",
+            L.rgba_profile_enable.argtypes = [P, i32]
+            L.rgba_profile_read.argtypes = [P, C.POINTER(RgbaProfile)]
+            for name in ("rgba_profile_enable", "rgba_profile_read", "rgba_create", "rgba_workspace_size", "rgba_workspace_layout",
                          "rgba_blend", "rgba_preprocess", "rgba_bin_sort", "rgba_render_fwd",
                          "rgba_render_bwd", "rgba_step", "rgba_step_async"):
                 getattr(L, name).restype = i32
@@ -167,3 +178,15 @@ def rgba_step(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream) -> tuple
 def rgba_step_async(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream) -> int:
     return check(lib().rgba_step_async(ctx, C.byref(batch), ws, ws_bytes, target, loss_kind,
                                        img, stream))
+
+
+def rgba_profile_enable(ctx, on: bool) -> int:
+    return check(lib().rgba_profile_enable(ctx, 1 if on else 0))
+
+
+def rgba_profile_read(ctx) -> dict:
+    out = RgbaProfile()
+    check(lib().rgba_profile_read(ctx, C.byref(out)))
+    d = {name: float(out.ms[i]) for i, name in enumerate(STAGES)}
+    d["launches"] = int(out.launches)
+    return d

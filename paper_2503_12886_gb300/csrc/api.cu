@@ -13,6 +13,10 @@ struct rgba_ctx {
     int device;
     int sms;
     rgba_counters *pinned;  // host-pinned landing spot of rgba_step's single read
+    bool prof;
+    bool recorded[RGBA_N_STAGES];
+    cudaEvent_t ev0[RGBA_N_STAGES], ev1[RGBA_N_STAGES];
+    int launches;
 };
 
 namespace {
@@ -250,8 +254,35 @@ int prologue(rgba_ctx_t ctx, const rgba_batch *b, void *ws, size_t ws_bytes, voi
     return RGBA_OK;
 }
 
-int upload_tables(Call &k) {
+int grid_for(rgba_ctx_t ctx, int per_sm) { return ctx->sms * per_sm; }
+
+enum Stage { ST_UPLOAD, ST_PRE, ST_SCAN, ST_SCATTER, ST_SORT, ST_FWD, ST_BWD, ST_GBWD, ST_DPSI };
+
+// Brackets one stage with events when profiling is on; counts the kernels it launches.
+struct StageScope {
+    rgba_ctx_t c;
+    int st;
+    cudaStream_t s;
+    StageScope(rgba_ctx_t c_, int st_, cudaStream_t s_, int kernels) : c(c_), st(st_), s(s_) {
+        c->launches += kernels;
+        if (c->prof) cudaEventRecord(c->ev0[st], s);
+    }
+    ~StageScope() {
+        if (c->prof) {
+            cudaEventRecord(c->ev1[st], s);
+            c->recorded[st] = true;
+        }
+    }
+};
+
+int upload_kernels(size_t bytes) { return (int)((bytes + 3839) / 3840); }
+
+int upload_tables(rgba_ctx_t ctx, Call &k) {
     const Layout &L = k.p.L;
+    StageScope sc(ctx, ST_UPLOAD, k.s,
+                  upload_kernels(sizeof(ModelInfo) * k.p.models.size()) +
+                      upload_kernels(sizeof(FrameInfo) * k.p.frames.size()) +
+                      upload_kernels(sizeof(int) * k.p.mframes.size()));
     cudaError_t e;
     if (!k.p.models.empty() &&
         (e = launch_upload(k.ws + L.models, k.p.models.data(), sizeof(ModelInfo) * k.p.models.size(), k.s)) != cudaSuccess)
@@ -271,23 +302,32 @@ int memset_async(void *p, size_t bytes, cudaStream_t s, const char *what) {
     return e == cudaSuccess ? RGBA_OK : cuda_fail(e, what);
 }
 
-int do_preprocess(Call &k) {
+
+
+
+int do_preprocess(rgba_ctx_t ctx, Call &k) {
     int rc;
-    if ((rc = upload_tables(k))) return rc;
+    if ((rc = upload_tables(ctx, k))) return rc;
     if ((rc = memset_async(k.ws + k.p.L.counters, 256, k.s, "memset counters"))) return rc;
     if ((rc = memset_async(k.ws + k.p.L.tile_count, 4 * (size_t)k.p.L.T, k.s, "memset tile counts"))) return rc;
+    StageScope sc(ctx, ST_PRE, k.s, 1);
     cudaError_t e = launch_preprocess(k.c, k.p.max_n, k.s);
     return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "preprocess");
 }
 
-int grid_for(rgba_ctx_t ctx, int per_sm) { return ctx->sms * per_sm; }
-
 int do_bin_sort(rgba_ctx_t ctx, Call &k) {
     cudaError_t e;
     int rc;
-    if ((e = launch_scan(k.c, k.s)) != cudaSuccess) return cuda_fail(e, "scan");
-    if ((e = launch_scatter(k.c, k.p.max_n, k.s)) != cudaSuccess) return cuda_fail(e, "scatter");
+    {
+        StageScope sc(ctx, ST_SCAN, k.s, 1);
+        if ((e = launch_scan(k.c, k.s)) != cudaSuccess) return cuda_fail(e, "scan");
+    }
+    {
+        StageScope sc(ctx, ST_SCATTER, k.s, 1);
+        if ((e = launch_scatter(k.c, k.p.max_n, k.s)) != cudaSuccess) return cuda_fail(e, "scatter");
+    }
     if ((rc = memset_async(&k.c.cnt->next_sort, 4, k.s, "memset sort counter"))) return rc;
+    StageScope sc(ctx, ST_SORT, k.s, 1);
     if ((e = launch_tile_sort(k.c, grid_for(ctx, 1), k.s)) != cudaSuccess) return cuda_fail(e, "tile sort");
     return RGBA_OK;
 }
@@ -295,6 +335,7 @@ int do_bin_sort(rgba_ctx_t ctx, Call &k) {
 int do_render_fwd(rgba_ctx_t ctx, Call &k, float *img, float *T, int *n, const float *target, int loss_kind, float *dl) {
     int rc;
     if ((rc = memset_async(&k.c.cnt->next_fwd, 4, k.s, "memset fwd counter"))) return rc;
+    StageScope sc(ctx, ST_FWD, k.s, 1);
     cudaError_t e = launch_render_fwd(k.c, grid_for(ctx, 4), k.p.L.smem_batch, img, T, n, target, loss_kind, dl, nullptr, k.s);
     return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "render fwd");
 }
@@ -304,15 +345,26 @@ int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, cons
     const Layout &L = k.p.L;
     if ((rc = memset_async(&k.c.cnt->next_bwd, 4, k.s, "memset bwd counter"))) return rc;
     if ((rc = memset_async(k.ws + L.grad2d, sizeof(float) * kG2Floats * (size_t)L.R, k.s, "memset grad2d"))) return rc;
-    cudaError_t e = launch_render_bwd(k.c, grid_for(ctx, 4), L.smem_batch, dl, T, n, k.s);
-    if (e != cudaSuccess) return cuda_fail(e, "render bwd");
+    cudaError_t e;
+    {
+        StageScope sc(ctx, ST_BWD, k.s, 1);
+        e = launch_render_bwd(k.c, grid_for(ctx, 4), L.smem_batch, dl, T, n, k.s);
+        if (e != cudaSuccess) return cuda_fail(e, "render bwd");
+    }
     for (const ModelInfo &m : k.p.models) {
         if (m.nb) continue;  // no frame renders it: zero gradient
         if (m.gg0 && (rc = memset_async(m.gg0, sizeof(float) * kNch * (size_t)m.n_pad, k.s, "memset grad_g0"))) return rc;
         if (m.gdg && (rc = memset_async(m.gdg, sizeof(float) * (size_t)m.k * m.A * m.n_pad, k.s, "memset grad_dg"))) return rc;
     }
-    if ((e = launch_gauss_bwd(k.c, k.p.max_chunks, k.p.max_nb, k.p.max_k, k.s)) != cudaSuccess) return cuda_fail(e, "gauss bwd");
-    if ((e = launch_dpsi_reduce(k.c, k.p.max_k, k.s)) != cudaSuccess) return cuda_fail(e, "dpsi reduce");
+    {
+        StageScope sc(ctx, ST_GBWD, k.s, 1);
+        if ((e = launch_gauss_bwd(k.c, k.p.max_chunks, k.p.max_nb, k.p.max_k, k.s)) != cudaSuccess)
+            return cuda_fail(e, "gauss bwd");
+    }
+    if (k.c.grad_psi) {
+        StageScope sc(ctx, ST_DPSI, k.s, 1);
+        if ((e = launch_dpsi_reduce(k.c, k.p.max_k, k.s)) != cudaSuccess) return cuda_fail(e, "dpsi reduce");
+    }
     return RGBA_OK;
 }
 
@@ -346,8 +398,48 @@ int rgba_create(int device, rgba_ctx_t *out) {
 
 void rgba_destroy(rgba_ctx_t ctx) {
     if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->ev0[0]) {
+        for (int i = 0; i < RGBA_N_STAGES; ++i) {
+            cudaEventDestroy(ctx->ev0[i]);
+            cudaEventDestroy(ctx->ev1[i]);
+        }
+    }
     cudaFreeHost(ctx->pinned);
     delete ctx;
+}
+
+int rgba_profile_enable(rgba_ctx_t ctx, int on) {
+    if (!ctx) return fail(RGBA_ERR_INVALID_ARG, "ctx is NULL");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if (on && !ctx->ev0[0]) {
+        for (int i = 0; i < RGBA_N_STAGES; ++i) {
+            if ((e = cudaEventCreate(&ctx->ev0[i])) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+            if ((e = cudaEventCreate(&ctx->ev1[i])) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    ctx->prof = on != 0;
+    for (int i = 0; i < RGBA_N_STAGES; ++i) ctx->recorded[i] = false;
+    return RGBA_OK;
+}
+
+int rgba_profile_read(rgba_ctx_t ctx, rgba_profile *out) {
+    if (!ctx || !out) return fail(RGBA_ERR_INVALID_ARG, "ctx/out is NULL");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    for (int i = 0; i < RGBA_N_STAGES; ++i) {
+        out->ms[i] = -1.0f;
+        if (!ctx->recorded[i]) continue;
+        if ((e = cudaEventSynchronize(ctx->ev1[i])) != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, ctx->ev0[i], ctx->ev1[i])) != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        out->ms[i] = ms;
+    }
+    out->launches = ctx->launches;
+    out->pad_ = 0;
+    ctx->launches = 0;
+    return RGBA_OK;
 }
 
 int rgba_workspace_size(const rgba_batch *batch, int64_t pair_capacity, size_t *bytes) {
@@ -375,6 +467,10 @@ int rgba_workspace_layout(const rgba_batch *batch, size_t ws_bytes, rgba_ws_layo
     out->tile_start = p.L.tile_start;
     out->sorted = p.L.sorted;
     out->grad2d = p.L.grad2d;
+    out->pix_T = p.L.pix_T;
+    out->pix_n = p.L.pix_n;
+    out->pix_dl = p.L.pix_dl;
+    out->pix_img = p.L.pix_img;
     out->total_bytes = p.L.total;
     out->records_total = p.L.R;
     out->tiles_total = p.L.T;
@@ -397,6 +493,7 @@ int rgba_blend(rgba_ctx_t ctx, const rgba_batch *batch, float *out, void *stream
     c.psi = batch->psi;
     c.k_stride = batch->k_stride;
     c.B = p.L.B;
+    ctx->launches += (p.L.B + 63) / 64;
     e = launch_blend(c, p.max_n, out, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "blend");
 }
@@ -405,7 +502,7 @@ int rgba_preprocess(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
     Call k;
     int rc = prologue(ctx, batch, ws, ws_bytes, stream, k);
     if (rc || k.p.L.B == 0) return rc;
-    return do_preprocess(k);
+    return do_preprocess(ctx, k);
 }
 
 int rgba_bin_sort(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, void *stream) {
@@ -445,7 +542,7 @@ int rgba_step_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
     float *T = reinterpret_cast<float *>(k.ws + L.pix_T);
     int *n = reinterpret_cast<int *>(k.ws + L.pix_n);
     float *dl = reinterpret_cast<float *>(k.ws + L.pix_dl);
-    if ((rc = do_preprocess(k))) return rc;
+    if ((rc = do_preprocess(ctx, k))) return rc;
     if ((rc = do_bin_sort(ctx, k))) return rc;
     if ((rc = do_render_fwd(ctx, k, im, T, n, target, loss_kind, dl))) return rc;
     return do_render_bwd(ctx, k, dl, T, n);

@@ -308,8 +308,18 @@ cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_nb, int max_k
     (void)max_nb;
     if (c.M == 0 || max_chunks == 0) return cudaSuccess;
     const int smem = (kFG * kNch * kBwdChunk + kFG * max_k) * (int)sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_gauss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // set once, at the largest size any batch can ask for, so no attribute call happens while
+    // a stream is being captured
+    static int attr_device = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (attr_device != dev) {
+        const int most = (kFG * kNch * kBwdChunk + kFG * RGBA_MAX_K) * (int)sizeof(float);
+        e = cudaFuncSetAttribute(k_gauss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        if (e != cudaSuccess) return e;
+        attr_device = dev;
+    }
     dim3 grid(max_chunks, c.M);
     k_gauss_bwd<<<grid, kBwdThreads, smem, s>>>(c, max_k);
     return cudaGetLastError();

@@ -162,12 +162,15 @@ cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s) {
 }
 
 cudaError_t launch_tile_sort(const Ctx &c, int grid, cudaStream_t s) {
-    static bool attr = false;
+    static int attr_device = -1;
     const int smem = kSortSmemKeys * (int)sizeof(unsigned long long);
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (attr_device != dev) {
+        e = cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr_device = dev;
     }
     k_tile_sort<<<grid, kSortThreads, smem, s>>>(c);
     return cudaGetLastError();

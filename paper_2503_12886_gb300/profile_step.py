@@ -1,0 +1,59 @@
+"""Runs eager training steps of a named workload, for profilers (ncu) and quick timing.
+
+    python -m paper_2503_12886_gb300.profile_step [--workload batched|single|uneven]
+        [--steps N] [--tile 16x16|8x32] [--smem-batch 64|128|256]
+
+One sizing step (grows the workspace to the pair count), then N rgba_step calls, each one
+launch sequence of the whole hot path plus its single host synchronisation. Prints per-stage
+device times of the last step (CUDA events) as one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import torch
+
+from . import api, synth
+from .rasterizer import DeviceBatch, Renderer
+
+
+def make(name: str):
+    if name == "batched":
+        return synth.workload_batched()
+    if name == "single":
+        return synth.workload_single()
+    if name == "uneven":
+        return synth.workload_uneven()
+    raise ValueError(name)
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--workload", default="batched")
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--tile", default="16x16")
+    p.add_argument("--smem-batch", type=int, default=256)
+    a = p.parse_args()
+    tw, th = (int(x) for x in a.tile.split("x"))
+    batch = make(a.workload)
+    r = Renderer(0)
+    db = DeviceBatch(batch, "cuda:0", tile=(tw, th), smem_batch=a.smem_batch)
+    tg = db.pack_images(synth.make_targets(batch, 5))
+    img = torch.empty(3 * db.total_pix, dtype=torch.float32, device="cuda:0")
+    out = r.step(db, tg, api.RGBA_LOSS_L1, img)
+    wall = []
+    api.rgba_profile_enable(r.ctx, True)
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        out = r.step(db, tg, api.RGBA_LOSS_L1, img)
+        wall.append(time.perf_counter() - t0)
+    prof = api.rgba_profile_read(r.ctx)
+    r.close()
+    print(json.dumps({"workload": a.workload, "frames": db.n_frames, "pairs": out.pairs,
+                      "loss": out.loss, "step_ms": [1e3 * w for w in wall], "stages_ms": prof}))
+
+
+if __name__ == "__main__":
+    main()
