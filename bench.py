@@ -285,7 +285,7 @@ def run_ours(args, rank, world, local_rank):
         elapsed = float(t.item())
     value = world * FRAMES * args.steps / elapsed
     ms_per_step = 1e3 * elapsed / args.steps
-    last_loss = float(host_cnt[(args.steps - 1) % len(graphs)][8:16].numpy().view(np.float64)[0])
+    last_loss = float(host_cnt[(args.steps - 1) % len(graphs)][16:24].numpy().view(np.float64)[0])
 
     # per-stage device time (CUDA events on the launching stream), eager steps
     api.rgba_profile_enable(r.ctx, True)
