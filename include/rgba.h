@@ -209,6 +209,28 @@ int rgba_profile_enable(rgba_ctx_t ctx, int on);
 /* Waits for the recorded events, fills `out` (host) and resets the launch count. */
 int rgba_profile_read(rgba_ctx_t ctx, rgba_profile *out);
 
+/* Forward render that allocates nothing: for callers that cannot call cudaMalloc (code inside
+ * another framework's memory pool, plugins whose host forbids device allocation, processes that
+ * must not grow their device footprint). The paper has no counterpart; it is a deployment
+ * variant of rgba_preprocess + rgba_bin_sort + rgba_render_fwd.
+ *  - Scratch: one fixed block of RGBA_NOALLOC_SCRATCH_BYTES (64 MiB) of device memory that is
+ *    part of the library image; every GPU that loads the library holds it until the process
+ *    exits. The caller still passes the inputs (batch) and the outputs img, T_final, n_contrib
+ *    in the layouts of rgba_render_fwd; out (host) receives the pair count.
+ *  - Limits: a batch whose workspace (rgba_workspace_size with capacity = the batch's total
+ *    Gaussian records) does not fit the block returns RGBA_ERR_INVALID_ARG before anything is
+ *    enqueued; more pairs than fit return RGBA_ERR_CAPACITY with out->pairs_needed set.
+ *  - The first call on a device looks up the block's device address with that device current;
+ *    make that first call before any stream capture.
+ *  - Every call uses the same block, which keeps the last call's contents; the call clears what
+ *    must start at zero. Calls that overlap on the GPU (other streams, other threads) race on
+ *    the block: serialise them.
+ *  - Synchronous: ends with one device-to-host read of the counters and a stream
+ *    synchronisation. No device memory is allocated or freed. */
+#define RGBA_NOALLOC_SCRATCH_BYTES (64u << 20)
+int rgba_render_fwd_noalloc(rgba_ctx_t ctx, const rgba_batch *batch, float *img, float *T_final,
+                            int32_t *n_contrib, rgba_step_out *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ RGBA_NCH = 14
 EXPORTS = ("rgba_last_error", "rgba_create", "rgba_destroy", "rgba_workspace_size",
            "rgba_workspace_layout", "rgba_blend", "rgba_preprocess", "rgba_bin_sort",
            "rgba_render_fwd", "rgba_render_bwd", "rgba_step", "rgba_step_async",
-           "rgba_profile_enable", "rgba_profile_read")
+           "rgba_profile_enable", "rgba_profile_read", "rgba_render_fwd_noalloc")
 RGBA_N_STAGES = 9
 STAGES = ("upload", "preprocess", "scan", "scatter", "sort", "render_fwd", "render_bwd",
           "gauss_bwd", "dpsi_reduce")
@@ -100,6 +100,8 @@ def lib() -> C.CDLL:
             L.rgba_render_bwd.argtypes = [P, Bp, P, sz, P, P, P, P]
             L.rgba_step.argtypes = [P, Bp, P, sz, P, i32, P, C.POINTER(RgbaStepOut), P]
             L.rgba_step_async.argtypes = [P, Bp, P, sz, P, i32, P, P]
+            L.rgba_render_fwd_noalloc.argtypes = [P, Bp, P, P, P, C.POINTER(RgbaStepOut), P]
+            L.rgba_render_fwd_noalloc.restype = i32
             L.rgba_profile_enable.argtypes = [P, i32]
             L.rgba_profile_read.argtypes = [P, C.POINTER(RgbaProfile)]
             for name in ("rgba_profile_enable", "rgba_profile_read", "rgba_create", "rgba_workspace_size", "rgba_workspace_layout",
@@ -190,3 +192,14 @@ def rgba_profile_read(ctx) -> dict:
     d = {name: float(out.ms[i]) for i, name in enumerate(STAGES)}
     d["launches"] = int(out.launches)
     return d
+
+
+def rgba_render_fwd_noalloc(ctx, batch, img, T_final, n_contrib, stream) -> tuple[int, RgbaStepOut]:
+    """Forward render with the library's fixed scratch block (no device allocation). Returns
+    (status, out); RGBA_ERR_CAPACITY is returned, not raised."""
+    out = RgbaStepOut()
+    rc = lib().rgba_render_fwd_noalloc(ctx, C.byref(batch), img, T_final, n_contrib,
+                                       C.byref(out), stream)
+    if rc not in (RGBA_OK, RGBA_ERR_CAPACITY):
+        check(rc)
+    return rc, out

@@ -9,16 +9,6 @@
 
 using namespace rgba;
 
-struct rgba_ctx {
-    int device;
-    int sms;
-    rgba_counters *pinned;  // host-pinned landing spot of rgba_step's single read
-    bool prof;
-    bool recorded[RGBA_N_STAGES];
-    cudaEvent_t ev0[RGBA_N_STAGES], ev1[RGBA_N_STAGES];
-    int launches;
-};
-
 namespace {
 
 thread_local std::string g_err;

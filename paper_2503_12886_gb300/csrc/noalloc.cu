@@ -1,0 +1,78 @@
+// Forward render for callers that cannot allocate device memory.
+//
+// Some callers have no device allocator they may use: code running inside another framework's
+// memory pool, plugins whose host forbids cudaMalloc, or processes that must never grow their
+// device footprint after start-up. rgba_render_fwd_noalloc gives them the forward render
+// (preprocess, bin/sort, compositing) with all scratch taken from one fixed block of device
+// memory that is part of this library's image: every GPU that loads the library holds the
+// block until the process exits, and no call allocates or frees device memory.
+#include <mutex>
+
+#include "rgba_internal.cuh"
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(RGBA_NOALLOC_SCRATCH_BYTES);
+
+// The scratch block. In host code this name is only a host-side stand-in for the symbol; its
+// device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_scratch_dev[kMaxDevices] = {};
+
+// With the context's device current: the device address of g_scratch on that device.
+int scratch_address(int device, void **out) {
+    if (device < 0 || device >= kMaxDevices) return RGBA_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_dev[device]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return RGBA_ERR_CUDA;
+        g_scratch_dev[device] = p;
+    }
+    *out = g_scratch_dev[device];
+    return RGBA_OK;
+}
+
+}  // namespace
+
+extern "C" int rgba_render_fwd_noalloc(rgba_ctx_t ctx, const rgba_batch *batch, float *img,
+                                       float *T_final, int32_t *n_contrib, rgba_step_out *out,
+                                       void *stream) {
+    if (!ctx || !batch || !out) return RGBA_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return RGBA_ERR_CUDA;
+    // the batch must leave room in the block for at least one pair per Gaussian record
+    size_t fixed = 0;
+    int rc = rgba_workspace_size(batch, 0, &fixed);
+    if (rc) return rc;
+    rgba_ws_layout lay;
+    if (fixed > kScratchBytes || (rc = rgba_workspace_layout(batch, kScratchBytes, &lay)) != RGBA_OK ||
+        lay.pair_capacity < lay.records_total)
+        return RGBA_ERR_INVALID_ARG;
+    if (batch->n_frames == 0) return RGBA_OK;
+    void *ws = nullptr;
+    if ((rc = scratch_address(ctx->device, &ws)) != RGBA_OK) return rc;
+    // rgba_preprocess clears the counters and tile counts that must start at zero; every other
+    // region is written before it is read.
+    if ((rc = rgba_preprocess(ctx, batch, ws, kScratchBytes, stream)) != RGBA_OK) return rc;
+    if ((rc = rgba_bin_sort(ctx, batch, ws, kScratchBytes, stream)) != RGBA_OK) return rc;
+    if ((rc = rgba_render_fwd(ctx, batch, ws, kScratchBytes, img, T_final, n_contrib, stream)) != RGBA_OK)
+        return rc;
+    rgba_counters h;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&h, static_cast<unsigned char *>(ws) + lay.counters, sizeof(h),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return RGBA_ERR_CUDA;
+    out->pairs = h.pairs;
+    out->pair_capacity = lay.pair_capacity;
+    out->overflow = h.overflow;
+    out->device_error = h.device_error;
+    if (h.overflow) {
+        out->pairs_needed = h.pairs;
+        return RGBA_ERR_CAPACITY;
+    }
+    return RGBA_OK;
+}

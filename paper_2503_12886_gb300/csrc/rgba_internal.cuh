@@ -5,6 +5,17 @@
 
 #include "../../include/rgba.h"
 
+// Context behind rgba_ctx_t.
+struct rgba_ctx {
+    int device;
+    int sms;
+    rgba_counters *pinned;  // host-pinned landing spot of rgba_step's single read
+    bool prof;
+    bool recorded[RGBA_N_STAGES];
+    cudaEvent_t ev0[RGBA_N_STAGES], ev1[RGBA_N_STAGES];
+    int launches;
+};
+
 namespace rgba {
 
 constexpr int kNch = 14;
