@@ -301,7 +301,9 @@ int do_preprocess(rgba_ctx_t ctx, Call &k) {
     if ((rc = memset_async(k.ws + k.p.L.counters, 256, k.s, "memset counters"))) return rc;
     if ((rc = memset_async(k.ws + k.p.L.tile_count, 4 * (size_t)k.p.L.T, k.s, "memset tile counts"))) return rc;
     StageScope sc(ctx, ST_PRE, k.s, 1);
-    cudaError_t e = launch_preprocess(k.c, k.p.max_n, k.s);
+    int max_rows = 0;
+    for (const ModelInfo &m : k.p.models) max_rows = std::max(max_rows, kNch + m.k * m.A);
+    cudaError_t e = launch_preprocess(k.c, k.p.max_n, k.p.max_k, max_rows, k.s);
     return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "preprocess");
 }
 
@@ -326,7 +328,7 @@ int do_render_fwd(rgba_ctx_t ctx, Call &k, float *img, float *T, int *n, const f
     int rc;
     if ((rc = memset_async(&k.c.cnt->next_fwd, 4, k.s, "memset fwd counter"))) return rc;
     StageScope sc(ctx, ST_FWD, k.s, 1);
-    cudaError_t e = launch_render_fwd(k.c, grid_for(ctx, 4), k.p.L.smem_batch, img, T, n, target, loss_kind, dl, nullptr, k.s);
+    cudaError_t e = launch_render_fwd(k.c, ctx->sms, k.p.L.smem_batch, img, T, n, target, loss_kind, dl, nullptr, k.s);
     return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "render fwd");
 }
 
@@ -338,7 +340,7 @@ int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, cons
     cudaError_t e;
     {
         StageScope sc(ctx, ST_BWD, k.s, 1);
-        e = launch_render_bwd(k.c, grid_for(ctx, 4), L.smem_batch, dl, T, n, k.s);
+        e = launch_render_bwd(k.c, ctx->sms, L.smem_batch, dl, T, n, k.s);
         if (e != cudaSuccess) return cuda_fail(e, "render bwd");
     }
     for (const ModelInfo &m : k.p.models) {
@@ -359,6 +361,8 @@ int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, cons
 }
 
 }  // namespace
+
+int rgba::set_error(int code, const char *msg) { return fail(code, msg); }
 
 extern "C" {
 

@@ -14,20 +14,26 @@ namespace {
 constexpr int kScanThreads = 1024;
 
 // Exclusive scan of the tile counts (frame-major), pair total and capacity check, and the work
-// list: non-empty tiles first (tile order), then empty tiles (tile order).
+// list: non-empty tiles first, longest lists first (bucketed by floor(log2(length))), then the
+// empty tiles in tile order. The persistent kernels pull items in this order, so the heaviest
+// tiles start first and the tail of the launch is short.
 __global__ void __launch_bounds__(kScanThreads) k_scan(Ctx c) {
     __shared__ unsigned long long s_sum[kScanThreads];
     __shared__ unsigned s_ne[kScanThreads];
+    __shared__ unsigned s_hist[32];
     const long long T = c.T;
     const int tid = threadIdx.x;
     const long long per = (T + kScanThreads - 1) / kScanThreads;
     const long long lo = tid * per, hi = (lo + per < T) ? lo + per : T;
+    if (tid < 32) s_hist[tid] = 0;
+    __syncthreads();
     unsigned long long sum = 0;
     unsigned ne = 0;
     for (long long t = lo; t < hi; ++t) {
         unsigned v = c.tile_count[t];
         sum += v;
         ne += v > 0;
+        if (v > 0) atomicAdd(&s_hist[31 - __clz(v)], 1u);
     }
     s_sum[tid] = sum;
     s_ne[tid] = ne;
@@ -41,6 +47,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Ctx c) {
         s_ne[tid] += b;
         __syncthreads();
     }
+    if (tid == 0) {  // bucket offsets, longest bucket first
+        unsigned off = 0;
+        for (int k = 31; k >= 0; --k) {
+            const unsigned h = s_hist[k];
+            s_hist[k] = off;
+            off += h;
+        }
+    }
+    __syncthreads();
     const unsigned long long total = s_sum[kScanThreads - 1];
     const unsigned n_ne = s_ne[kScanThreads - 1];
     unsigned long long run = s_sum[tid] - sum;
@@ -51,7 +66,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Ctx c) {
         unsigned st = run > 0xffffffffull ? 0xffffffffu : (unsigned)run;
         c.tile_start[t] = st;
         c.cursor[t] = st;
-        if (v > 0) c.work[ne_run++] = (unsigned)t;
+        if (v > 0) c.work[atomicAdd(&s_hist[31 - __clz(v)], 1u)] = (unsigned)t;
         else c.work[n_ne + e_run++] = (unsigned)t;
         run += v;
     }

@@ -40,9 +40,9 @@ int scratch_address(int device, void **out) {
 extern "C" int rgba_render_fwd_noalloc(rgba_ctx_t ctx, const rgba_batch *batch, float *img,
                                        float *T_final, int32_t *n_contrib, rgba_step_out *out,
                                        void *stream) {
-    if (!ctx || !batch || !out) return RGBA_ERR_INVALID_ARG;
+    if (!ctx || !batch || !out) return rgba::set_error(RGBA_ERR_INVALID_ARG, "ctx/batch/out is NULL");
     memset(out, 0, sizeof(*out));
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return RGBA_ERR_CUDA;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return rgba::set_error(RGBA_ERR_CUDA, "cudaSetDevice failed");
     // the batch must leave room in the block for at least one pair per Gaussian record
     size_t fixed = 0;
     int rc = rgba_workspace_size(batch, 0, &fixed);
@@ -50,10 +50,14 @@ extern "C" int rgba_render_fwd_noalloc(rgba_ctx_t ctx, const rgba_batch *batch, 
     rgba_ws_layout lay;
     if (fixed > kScratchBytes || (rc = rgba_workspace_layout(batch, kScratchBytes, &lay)) != RGBA_OK ||
         lay.pair_capacity < lay.records_total)
-        return RGBA_ERR_INVALID_ARG;
+        return rgba::set_error(RGBA_ERR_INVALID_ARG,
+                               "batch too large for the 64 MiB no-alloc scratch block (its workspace "
+                               "with one pair per Gaussian record must fit); use rgba_render_fwd "
+                               "with a caller-allocated workspace");
     if (batch->n_frames == 0) return RGBA_OK;
     void *ws = nullptr;
-    if ((rc = scratch_address(ctx->device, &ws)) != RGBA_OK) return rc;
+    if ((rc = scratch_address(ctx->device, &ws)) != RGBA_OK)
+        return rgba::set_error(rc, "could not resolve the scratch block's device address");
     // rgba_preprocess clears the counters and tile counts that must start at zero; every other
     // region is written before it is read.
     if ((rc = rgba_preprocess(ctx, batch, ws, kScratchBytes, stream)) != RGBA_OK) return rc;
@@ -65,14 +69,14 @@ extern "C" int rgba_render_fwd_noalloc(rgba_ctx_t ctx, const rgba_batch *batch, 
     if (cudaMemcpyAsync(&h, static_cast<unsigned char *>(ws) + lay.counters, sizeof(h),
                         cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
-        return RGBA_ERR_CUDA;
+        return rgba::set_error(RGBA_ERR_CUDA, "reading the no-alloc counters failed");
     out->pairs = h.pairs;
     out->pair_capacity = lay.pair_capacity;
     out->overflow = h.overflow;
     out->device_error = h.device_error;
     if (h.overflow) {
         out->pairs_needed = h.pairs;
-        return RGBA_ERR_CAPACITY;
+        return rgba::set_error(RGBA_ERR_CAPACITY, "pairs exceed the no-alloc scratch block");
     }
     return RGBA_OK;
 }

@@ -2,6 +2,10 @@
 // the batch-parallel rasterizer, RGBAvatar Sec. 3.2 / Supp. A.3, built on 3DGS), and the
 // standalone Eq. 1 blend.
 //
+// The base Gaussians and blendshapes are read from HBM once per step: a CTA stages its chunk's
+// rows in shared memory with bulk asynchronous copies and blends every frame of the model from
+// there.
+//
 // Every value that decides a discrete outcome (cull, tile rectangle, depth key) is computed by
 // a fixed sequence of correctly rounded binary32 operations written with explicit-rounding
 // intrinsics, so the compiler can neither contract nor reorder them: any other IEEE-754
@@ -71,32 +75,16 @@ __device__ __forceinline__ void blend14(const ModelInfo &m, const float *__restr
     }
 }
 
-constexpr int kPreThreads = 128;
-
-__global__ void __launch_bounds__(kPreThreads)
-k_preprocess(Ctx c) {
-    __shared__ float s_psi[RGBA_MAX_K];
-    __shared__ float s_fp[RGBA_FP_STRIDE];
-    const int b = blockIdx.y;
-    const FrameInfo f = c.frames[b];
-    const ModelInfo &m = c.models[f.model];
-    for (int t = threadIdx.x; t < f.k; t += blockDim.x) s_psi[t] = c.psi[(size_t)b * c.k_stride + t];
-    if (threadIdx.x < RGBA_FP_STRIDE) s_fp[threadIdx.x] = c.fparams[(size_t)b * RGBA_FP_STRIDE + threadIdx.x];
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= f.n) return;
-    const long long r = f.rec_base + i;
-
-    float v[kNch];
-    blend14(m, s_psi, i, v);
-    // backward cache: blended mean, raw quaternion, log-scale
+// The FP32 decision spec for one (frame, Gaussian) from its blended channels v: view transform,
+// activations, EWA covariance, conic, radius, tile rectangle, depth. Writes the render record,
+// the rectangle and the backward cache, and counts the Gaussian in every tile it touches.
+__device__ __forceinline__ void decide_and_write(const Ctx &c, const FrameInfo &f, const float *V,
+                                                 const float v[kNch], long long r) {
     c.cache[r * 3 + 0] = make_float4(v[0], v[1], v[2], v[3]);
     c.cache[r * 3 + 1] = make_float4(v[4], v[5], v[6], v[7]);
     c.cache[r * 3 + 2] = make_float4(v[8], v[9], 0.f, 0.f);
-
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     ushort4 rc = make_ushort4(0, 0, 0, 0);
-    const float *V = s_fp;
     do {
         // view transform
         float p[3];
@@ -212,6 +200,126 @@ k_preprocess(Ctx c) {
     c.rects[r] = rc;
 }
 
+constexpr int kPreThreads = 128;  // standalone blend
+constexpr int kPreG = 64;         // Gaussians per CTA
+constexpr int kPreSlots = 4;      // frame slots per Gaussian
+constexpr int kPreFB = 4;         // frames per thread per round (register block)
+constexpr int kPreRound = kPreSlots * kPreFB;
+constexpr int kPreBlock = kPreG * kPreSlots;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// Bulk asynchronous copy global -> shared completing on an mbarrier (16-byte aligned, size a
+// multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for phase `phase` of the mbarrier; false after max_iter polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned phase, int max_iter) {
+    for (int it = 0; it < max_iter; ++it) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// One CTA = 64 Gaussians of one model and every frame that renders it. The model's G0 rows and
+// blendshape rows for the chunk arrive once in shared memory by bulk async copies; each thread
+// then blends its Gaussian for 4 frames at a time from shared memory (each blendshape value read
+// once per 4 frames) and runs the decision spec per frame.
+__global__ void __launch_bounds__(kPreBlock, 2)
+k_preprocess(Ctx c, int max_k) {
+    extern __shared__ float4 smem4[];
+    __shared__ __align__(8) unsigned long long s_bar;
+    const ModelInfo &m = c.models[blockIdx.y];
+    const int i0 = blockIdx.x * kPreG;
+    if (i0 >= m.n || m.nb == 0) return;
+    const int K = m.k, A = m.A, rows = kNch + K * A;
+    float *s_rows = reinterpret_cast<float *>(smem4);      // [rows][64]: G0 then blendshapes
+    float *s_psi = s_rows + (size_t)rows * kPreG;          // [16][max_k]
+    float *s_fp = s_psi + kPreRound * max_k;               // [16][20]
+    const int tid = threadIdx.x;
+    const int cols = min(kPreG, m.n_pad - i0);
+    const unsigned row_bytes = (unsigned)cols * 4u;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid < 32) {
+        if (tid == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         :: "r"(smem_u32(&s_bar)), "r"(row_bytes * (unsigned)rows) : "memory");
+        __syncwarp();
+        for (int rr = tid; rr < rows; rr += 32) {
+            const float *src = rr < kNch ? m.g0 + (size_t)rr * m.n_pad + i0
+                                         : m.dg + (size_t)(rr - kNch) * m.n_pad + i0;
+            bulk_g2s(s_rows + (size_t)rr * kPreG, src, row_bytes, &s_bar);
+        }
+    }
+    if (!mbar_wait(&s_bar, 0, 1 << 22)) {
+        // the copies never landed: report and give them one more bounded wait before leaving
+        if (tid == 0) atomicExch(&c.cnt->device_error, 1u);
+        mbar_wait(&s_bar, 0, 1 << 20);
+        return;
+    }
+    const int g = tid % kPreG, slot = tid / kPreG;
+    const int i = i0 + g;
+    const bool valid = i < m.n;
+    for (int round = 0; round < m.nb; round += kPreRound) {
+        const int nr = min(kPreRound, m.nb - round);
+        for (int e = tid; e < nr * K; e += kPreBlock) {
+            const int fl = e / K, kk = e - fl * K;
+            const int b = c.mframes[m.frame_off + round + fl];
+            s_psi[fl * max_k + kk] = c.psi[(size_t)b * c.k_stride + kk];
+        }
+        for (int e = tid; e < nr * RGBA_FP_STRIDE; e += kPreBlock) {
+            const int fl = e / RGBA_FP_STRIDE, q = e - fl * RGBA_FP_STRIDE;
+            const int b = c.mframes[m.frame_off + round + fl];
+            s_fp[e] = c.fparams[(size_t)b * RGBA_FP_STRIDE + q];
+        }
+        __syncthreads();
+        const int f0 = slot * kPreFB;
+        if (valid && f0 < nr) {
+            float v[kPreFB][kNch];
+            int a = 0;
+#pragma unroll
+            for (int ch = 0; ch < kNch; ++ch) {
+                const float x = s_rows[ch * kPreG + g];
+#pragma unroll
+                for (int q = 0; q < kPreFB; ++q) v[q][ch] = x;
+                if ((m.mask >> ch) & 1u) {
+                    const float *d = s_rows + (size_t)(kNch + a) * kPreG + g;
+                    for (int kk = 0; kk < K; ++kk) {
+                        const float dv = d[(size_t)kk * A * kPreG];
+#pragma unroll
+                        for (int q = 0; q < kPreFB; ++q)
+                            v[q][ch] = __fmaf_rn(s_psi[(f0 + q) * max_k + kk], dv, v[q][ch]);
+                    }
+                    ++a;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kPreFB; ++q) {
+                if (f0 + q < nr) {
+                    const int b = c.mframes[m.frame_off + round + f0 + q];
+                    const FrameInfo &f = c.frames[b];
+                    decide_and_write(c, f, s_fp + (f0 + q) * RGBA_FP_STRIDE, v[q], f.rec_base + i);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Standalone Eq. 1 for up to kBlendFrames frames per launch; the frame table travels as a
 // kernel parameter so this entry point needs no workspace.
 constexpr int kBlendFrames = 64;
@@ -272,10 +380,24 @@ cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t
     return cudaSuccess;
 }
 
-cudaError_t launch_preprocess(const Ctx &c, int max_n, cudaStream_t s) {
+int preprocess_smem(int max_k, int max_rows) {
+    return (max_rows * kPreG + kPreRound * max_k + kPreRound * RGBA_FP_STRIDE) * (int)sizeof(float);
+}
+
+cudaError_t launch_preprocess(const Ctx &c, int max_n, int max_k, int max_rows, cudaStream_t s) {
     if (c.B == 0 || max_n == 0) return cudaSuccess;
-    dim3 grid((max_n + kPreThreads - 1) / kPreThreads, c.B);
-    k_preprocess<<<grid, kPreThreads, 0, s>>>(c);
+    static int attr_device = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (attr_device != dev) {  // once, at the largest size (K = 64, 13 blended channels)
+        e = cudaFuncSetAttribute(k_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 preprocess_smem(RGBA_MAX_K, kNch + RGBA_MAX_K * 13));
+        if (e != cudaSuccess) return e;
+        attr_device = dev;
+    }
+    dim3 grid((max_n + kPreG - 1) / kPreG, c.M);
+    k_preprocess<<<grid, kPreBlock, preprocess_smem(max_k, max_rows), s>>>(c, max_k);
     return cudaGetLastError();
 }
 

@@ -1,8 +1,10 @@
 // Front-to-back alpha compositing ("rasterize", RGBAvatar Sec. 3.2 on the 3DGS renderer) and
 // its exact reverse. One 256-thread CTA owns one screen tile (16x16 or 8x32 pixels) at a time;
 // persistent CTAs pull (frame, tile) items from the device work list, so every frame of every
-// avatar in the batch shares one launch. Gaussians are staged in shared memory in rounds of
-// BATCH entries; a CTA stops as soon as every pixel of its tile is saturated.
+// avatar in the batch shares one launch. Each of the 128 threads owns two pixels of the tile
+// (rows y and y + TH/2), so every shared-memory read of a Gaussian and every warp reduction of
+// its gradient serves two pixels. Gaussians are staged in shared memory in rounds of BATCH
+// entries; a CTA stops as soon as every pixel of its tile is saturated.
 //
 // Per pixel, with d = pixel centre - mean:
 //   power = -(a dx^2 + c dy^2) / 2 - b dx dy  (skip if > 0)
@@ -10,8 +12,9 @@
 //   stop, without blending, once T (1 - alpha) < 1e-4
 // The backward recomputes each alpha with the same instruction sequence as the forward, walks
 // the list backwards from the stored contributor count, and recovers T by division by
-// (1 - alpha). Per-Gaussian gradients are reduced across the warp, then across the CTA in
-// shared memory, and reach global memory as one atomic per Gaussian, tile and component.
+// (1 - alpha). Per-Gaussian gradients are reduced across the warp (reduce-scatter), then
+// across the CTA in shared memory, and reach global memory as one atomic per Gaussian, tile
+// and component.
 #include "rgba_internal.cuh"
 
 namespace rgba {
@@ -34,6 +37,36 @@ __device__ __forceinline__ int find_frame(const Ctx &c, long long t) {
 __device__ __forceinline__ float eval_power(float dx, float dy, float a, float b, float cc) {
     float q = __fmaf_rn(cc, __fmul_rn(dy, dy), __fmul_rn(__fmul_rn(a, dx), dx));
     return __fmaf_rn(-0.5f, q, -__fmul_rn(__fmul_rn(b, dx), dy));
+}
+
+constexpr int kThreads = kTilePix / 2;  // backward: two pixels per thread, rows y and y + TH/2
+
+struct PixF {
+    float pxc, pyc, T, C0, C1, C2;
+    int last;
+    bool inside, done;
+};
+
+// One list entry for one pixel (forward); marks the pixel done when it saturates.
+__device__ __forceinline__ void composite(PixF &p, const float4 &A, const float4 &Bv, float cb,
+                                          int pos) {
+    if (p.done) return;
+    const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
+    const float power = eval_power(dx, dy, A.z, A.w, Bv.x);
+    if (power > 0.0f) return;
+    const float alpha = fminf(kAlphaMax, __fmul_rn(Bv.y, __expf(power)));
+    if (alpha < kAlphaMin) return;
+    const float testT = p.T * (1.0f - alpha);
+    if (testT < kTMin) {
+        p.done = true;
+        return;
+    }
+    const float wgt = alpha * p.T;
+    p.C0 = fmaf(Bv.z, wgt, p.C0);
+    p.C1 = fmaf(Bv.w, wgt, p.C1);
+    p.C2 = fmaf(cb, wgt, p.C2);
+    p.T = testT;
+    p.last = pos;
 }
 
 template <int TW, int BATCH>
@@ -61,15 +94,12 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
         const int lt = (int)(t - f.tile_base);
         const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
         const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
-        const bool inside = px < f.W && py < f.H;
-        const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+        PixF p{(float)px + 0.5f, (float)py + 0.5f, 1.f, 0.f, 0.f, 0.f, 0, px < f.W && py < f.H, false};
+        p.done = !p.inside;
         const unsigned st = c.tile_start[t], en = c.tile_start[t + 1];
         const float4 *rec = c.records + (size_t)f.rec_base * 3;
-        float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-        int last = 0;
-        bool done = !inside;
         for (unsigned base = st; base < en; base += BATCH) {
-            if (__syncthreads_count(done) == kTilePix) break;
+            if (__syncthreads_count(p.done) == kTilePix) break;
             if (tid < BATCH && base + tid < en) {
                 const unsigned idx = c.sorted[base + tid];
                 s_a[tid] = rec[(size_t)idx * 3 + 0];
@@ -78,40 +108,20 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
             }
             __syncthreads();
             const int cnt = min(BATCH, (int)(en - base));
-            if (!done) {
-                for (int j = 0; j < cnt; ++j) {
-                    const float4 A = s_a[j];
-                    const float dx = __fsub_rn(pxc, A.x), dy = __fsub_rn(pyc, A.y);
-                    const float4 Bv = s_b[j];
-                    const float power = eval_power(dx, dy, A.z, A.w, Bv.x);
-                    if (power > 0.0f) continue;
-                    const float alpha = fminf(kAlphaMax, __fmul_rn(Bv.y, __expf(power)));
-                    if (alpha < kAlphaMin) continue;
-                    const float testT = T * (1.0f - alpha);
-                    if (testT < kTMin) {
-                        done = true;
-                        break;
-                    }
-                    const float wgt = alpha * T;
-                    C0 = fmaf(Bv.z, wgt, C0);
-                    C1 = fmaf(Bv.w, wgt, C1);
-                    C2 = fmaf(s_c[j], wgt, C2);
-                    T = testT;
-                    last = (int)(base - st) + j + 1;
-                }
-            }
+            const int pos0 = (int)(base - st) + 1;
+            for (int j = 0; j < cnt && !p.done; ++j) composite(p, s_a[j], s_b[j], s_c[j], pos0 + j);
         }
-        if (inside) {
+        if (p.inside) {
             const float *bg = c.fparams + (size_t)b * RGBA_FP_STRIDE + 17;
             const long long hw = (long long)f.W * f.H;
             const long long pix = (long long)py * f.W + px;
             float *im = img + f.pix_base * 3 + pix;
-            const float o0 = fmaf(T, bg[0], C0), o1 = fmaf(T, bg[1], C1), o2 = fmaf(T, bg[2], C2);
+            const float o0 = fmaf(p.T, bg[0], p.C0), o1 = fmaf(p.T, bg[1], p.C1), o2 = fmaf(p.T, bg[2], p.C2);
             im[0] = o0;
             im[hw] = o1;
             im[2 * hw] = o2;
-            T_final[f.pix_base + pix] = T;
-            n_contrib[f.pix_base + pix] = last;
+            T_final[f.pix_base + pix] = p.T;
+            n_contrib[f.pix_base + pix] = p.last;
             if (target) {
                 const float *tg = target + f.pix_base * 3 + pix;
                 const float scale = 1.0f / (3.0f * (float)hw * (float)c.B);
@@ -136,15 +146,86 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
         if ((tid & 31) == 0) s_red[tid >> 5] = loss_acc;
         __syncthreads();
         if (tid == 0) {
-            float s = 0.f;
-            for (int i = 0; i < kTilePix / 32; ++i) s += s_red[i];
-            atomicAdd(&c.cnt->loss, (double)s);
+            float sum = 0.f;
+            for (int i = 0; i < kTilePix / 32; ++i) sum += s_red[i];
+            atomicAdd(&c.cnt->loss, (double)sum);
         }
     }
 }
 
+struct PixB {
+    float pxc, pyc, T, Tfin, g0, g1, g2, bgdot, S0, S1, S2;
+    int last;
+};
+
+// One list entry for one pixel, in reverse; adds this pixel's share of the entry's gradient
+// dL/d(u, v, conic a, b, c, opacity, r, g, b) into v. Returns whether the pixel blended it.
+__device__ __forceinline__ bool accumulate(PixB &p, int pos, const float4 &A, const float4 &Bv,
+                                           float cb, float v[9]) {
+    if (pos > p.last) return false;
+    const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
+    const float power = eval_power(dx, dy, A.z, A.w, Bv.x);
+    if (power > 0.0f) return false;
+    const float G = __expf(power);
+    const float araw = __fmul_rn(Bv.y, G);
+    const float alpha = fminf(kAlphaMax, araw);
+    if (alpha < kAlphaMin) return false;
+    const float oma = 1.0f - alpha;
+    const float inv = __fdividef(1.0f, oma);  // 1 - alpha >= 0.01
+    p.T = p.T * inv;  // transmittance in front of this Gaussian
+    const float wgt = alpha * p.T;
+    v[6] = fmaf(wgt, p.g0, v[6]);
+    v[7] = fmaf(wgt, p.g1, v[7]);
+    v[8] = fmaf(wgt, p.g2, v[8]);
+    float dalpha = p.T * (p.g0 * (Bv.z - p.S0) + p.g1 * (Bv.w - p.S1) + p.g2 * (cb - p.S2));
+    dalpha -= p.Tfin * inv * p.bgdot;
+    p.S0 = fmaf(alpha, Bv.z, oma * p.S0);
+    p.S1 = fmaf(alpha, Bv.w, oma * p.S1);
+    p.S2 = fmaf(alpha, cb, oma * p.S2);
+    if (!(araw > kAlphaMax)) {
+        v[5] = fmaf(dalpha, G, v[5]);
+        const float dpow = dalpha * Bv.y * G;
+        v[2] = fmaf(-0.5f * dx * dx, dpow, v[2]);
+        v[3] = fmaf(-dx * dy, dpow, v[3]);
+        v[4] = fmaf(-0.5f * dy * dy, dpow, v[4]);
+        v[0] = fmaf(dpow, A.z * dx + A.w * dy, v[0]);
+        v[1] = fmaf(dpow, Bv.x * dy + A.w * dx, v[1]);
+    }
+    return true;
+}
+
+// Warp sum of v[0..8] as a reduce-scatter: three halving exchanges leave lane l with the partial
+// sum of value (l >> 2) over the 8 lanes that share l & 3, two more butterflies finish it;
+// v[8] takes a plain butterfly. 14 shuffles instead of 45.
+__device__ __forceinline__ void warp_reduce9(const float v[9], int lane, float &mine, float &v8) {
+    const unsigned F = 0xffffffffu;
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    float a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = h16 ? v[i] : v[i + 4];
+        const float keep = h16 ? v[i + 4] : v[i];
+        a[i] = keep + __shfl_xor_sync(F, send, 16);
+    }
+    float b2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = h8 ? a[i] : a[i + 2];
+        const float keep = h8 ? a[i + 2] : a[i];
+        b2[i] = keep + __shfl_xor_sync(F, send, 8);
+    }
+    float m = (h4 ? b2[1] : b2[0]) + __shfl_xor_sync(F, h4 ? b2[0] : b2[1], 4);
+    m += __shfl_xor_sync(F, m, 2);
+    m += __shfl_xor_sync(F, m, 1);
+    mine = m;
+    float x = v[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(F, x, o);
+    v8 = x;
+}
+
 template <int TW, int BATCH>
-__global__ void __launch_bounds__(kTilePix)
+__global__ void __launch_bounds__(kThreads)
 k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__ T_final,
              const int *__restrict__ n_contrib) {
     constexpr int TH = kTilePix / TW;
@@ -152,7 +233,7 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
     __shared__ float4 s_b[BATCH];
     __shared__ float s_c[BATCH];
     __shared__ unsigned s_idx[BATCH];
-    __shared__ float s_g[9][BATCH];
+    __shared__ float s_g[BATCH][9];  // per entry: stride 9 keeps lanes on distinct banks
     __shared__ unsigned s_w;
     __shared__ int s_max;
     if (c.cnt->overflow) return;
@@ -171,105 +252,70 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
         const FrameInfo &f = c.frames[b];
         const int lt = (int)(t - f.tile_base);
         const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
-        const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
-        const bool inside = px < f.W && py < f.H;
-        const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+        const int px = tx * TW + (tid % TW), py0 = ty * TH + (tid / TW);
         const unsigned st = c.tile_start[t], list_len = c.tile_start[t + 1] - st;
         const float4 *rec = c.records + (size_t)f.rec_base * 3;
         float *g2 = c.grad2d + (size_t)f.rec_base * kG2Floats;
         const float *bgp = c.fparams + (size_t)b * RGBA_FP_STRIDE + 17;
-        float T = 0.f, Tfin = 0.f, g0 = 0.f, g1 = 0.f, gb2 = 0.f, bgdot = 0.f;
-        int last = 0;
-        if (inside) {
-            const long long hw = (long long)f.W * f.H;
-            const long long pix = (long long)py * f.W + px;
-            Tfin = T_final[f.pix_base + pix];
-            T = Tfin;
-            last = n_contrib[f.pix_base + pix];
-            const float *dl = dl_dimg + f.pix_base * 3 + pix;
-            g0 = dl[0];
-            g1 = dl[hw];
-            gb2 = dl[2 * hw];
-            bgdot = g0 * bgp[0] + g1 * bgp[1] + gb2 * bgp[2];
+        const long long hw = (long long)f.W * f.H;
+        PixB p[2];
+        int m = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int py = py0 + h * (TH / 2);
+            p[h] = PixB{(float)px + 0.5f, (float)py + 0.5f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+            if (px < f.W && py < f.H) {
+                const long long pix = (long long)py * f.W + px;
+                p[h].Tfin = T_final[f.pix_base + pix];
+                p[h].T = p[h].Tfin;
+                p[h].last = n_contrib[f.pix_base + pix];
+                const float *dl = dl_dimg + f.pix_base * 3 + pix;
+                p[h].g0 = dl[0];
+                p[h].g1 = dl[hw];
+                p[h].g2 = dl[2 * hw];
+                p[h].bgdot = p[h].g0 * bgp[0] + p[h].g1 * bgp[1] + p[h].g2 * bgp[2];
+                m = max(m, p[h].last);
+            }
         }
-        int m = last;
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) atomicMax(&s_max, m);
         __syncthreads();
         const int max_last = min(s_max, (int)list_len);  // n_contrib comes from the caller
-        float S0 = 0.f, S1 = 0.f, S2 = 0.f;  // normalised colour behind the current entry
+        const int warp_last = m;  // entries past it are skipped by the whole warp
         for (int end = max_last; end > 0; end -= BATCH) {
             const int begin = max(0, end - BATCH);
             const int cnt = end - begin;
-            if (tid < cnt) {
-                const unsigned idx = c.sorted[st + begin + tid];
-                s_idx[tid] = idx;
-                s_a[tid] = rec[(size_t)idx * 3 + 0];
-                s_b[tid] = rec[(size_t)idx * 3 + 1];
-                s_c[tid] = rec[(size_t)idx * 3 + 2].x;
+            for (int e = tid; e < cnt; e += kThreads) {
+                const unsigned idx = c.sorted[st + begin + e];
+                s_idx[e] = idx;
+                s_a[e] = rec[(size_t)idx * 3 + 0];
+                s_b[e] = rec[(size_t)idx * 3 + 1];
+                s_c[e] = rec[(size_t)idx * 3 + 2].x;
             }
-            for (int e = tid; e < 9 * BATCH; e += kTilePix) (&s_g[0][0])[e] = 0.f;
+            for (int e = tid; e < 9 * BATCH; e += kThreads) (&s_g[0][0])[e] = 0.f;
             __syncthreads();
-            for (int j = cnt - 1; j >= 0; --j) {
+            for (int j = min(cnt, warp_last - begin) - 1; j >= 0; --j) {
                 const int pos = begin + j + 1;
+                const float4 A = s_a[j], Bv = s_b[j];
+                const float cb = s_c[j];
                 float v[9];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) v[q] = 0.f;
-                bool contrib = false;
-                if (pos <= last) {
-                    const float4 A = s_a[j];
-                    const float dx = __fsub_rn(pxc, A.x), dy = __fsub_rn(pyc, A.y);
-                    const float4 Bv = s_b[j];
-                    const float power = eval_power(dx, dy, A.z, A.w, Bv.x);
-                    if (power <= 0.0f) {
-                        const float G = __expf(power);
-                        const float araw = __fmul_rn(Bv.y, G);
-                        const float alpha = fminf(kAlphaMax, araw);
-                        if (alpha >= kAlphaMin) {
-                            contrib = true;
-                            const float oma = 1.0f - alpha;
-                            T = T / oma;  // transmittance in front of this Gaussian
-                            const float wgt = alpha * T;
-                            const float cb = s_c[j];
-                            v[6] = wgt * g0;
-                            v[7] = wgt * g1;
-                            v[8] = wgt * gb2;
-                            float dalpha = T * (g0 * (Bv.z - S0) + g1 * (Bv.w - S1) + gb2 * (cb - S2));
-                            dalpha -= Tfin / oma * bgdot;
-                            S0 = fmaf(alpha, Bv.z, oma * S0);
-                            S1 = fmaf(alpha, Bv.w, oma * S1);
-                            S2 = fmaf(alpha, cb, oma * S2);
-                            if (!(araw > kAlphaMax)) {
-                                v[5] = dalpha * G;
-                                const float dpow = dalpha * Bv.y * G;
-                                v[2] = -0.5f * dx * dx * dpow;
-                                v[3] = -dx * dy * dpow;
-                                v[4] = -0.5f * dy * dy * dpow;
-                                v[0] = dpow * (A.z * dx + A.w * dy);
-                                v[1] = dpow * (Bv.x * dy + A.w * dx);
-                            }
-                        }
-                    }
-                }
-                if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) {
-                        float x = v[q];
-                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                        v[q] = x;
-                    }
-                    if (lane == 0) {
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) atomicAdd(&s_g[q][j], v[q]);
-                    }
+                bool any = accumulate(p[0], pos, A, Bv, cb, v);
+                any |= accumulate(p[1], pos, A, Bv, cb, v);
+                if (__any_sync(0xffffffffu, any)) {
+                    float mine, v8;
+                    warp_reduce9(v, lane, mine, v8);
+                    if ((lane & 3) == 0) atomicAdd(&s_g[j][lane >> 2], mine);
+                    if (lane == 0) atomicAdd(&s_g[j][8], v8);
                 }
             }
             __syncthreads();
-            if (tid < cnt) {
-                float *dst = g2 + (size_t)s_idx[tid] * kG2Floats;
+            for (int e = tid; e < cnt; e += kThreads) {
+                float *dst = g2 + (size_t)s_idx[e] * kG2Floats;
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
-                    const float x = s_g[q][tid];
+                    const float x = s_g[e][q];
                     if (x != 0.f) atomicAdd(dst + q, x);
                 }
             }
@@ -278,17 +324,35 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
     }
 }
 
+// Persistent grid: every CTA the SMs can hold at once (occupancy query, cached per kernel).
+template <typename K>
+int persistent_grid(K kernel, int sms_hint, int threads) {
+    static int cached = 0;
+    if (!cached) {
+        int per_sm = 0, dev = 0, sms = sms_hint;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 4;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached = per_sm * sms;
+    }
+    return cached;
+}
+
 template <int TW, int BATCH>
 cudaError_t fwd_inst(const Ctx &c, int grid, float *img, float *T, int *n, const float *tg, int lk,
                      float *dl, cudaStream_t s) {
-    k_render_fwd<TW, BATCH><<<grid, kTilePix, 0, s>>>(c, img, T, n, tg, lk, dl);
+    const int g = persistent_grid(k_render_fwd<TW, BATCH>, grid, kTilePix);
+    k_render_fwd<TW, BATCH><<<g, kTilePix, 0, s>>>(c, img, T, n, tg, lk, dl);
     return cudaGetLastError();
 }
 
 template <int TW, int BATCH>
 cudaError_t bwd_inst(const Ctx &c, int grid, const float *dl, const float *T, const int *n,
                      cudaStream_t s) {
-    k_render_bwd<TW, BATCH><<<grid, kTilePix, 0, s>>>(c, dl, T, n);
+    const int g = persistent_grid(k_render_bwd<TW, BATCH>, grid, kThreads);
+    k_render_bwd<TW, BATCH><<<g, kThreads, 0, s>>>(c, dl, T, n);
     return cudaGetLastError();
 }
 

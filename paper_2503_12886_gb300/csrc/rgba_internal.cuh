@@ -97,9 +97,12 @@ struct Ctx {
     int B, M, k_stride, tw, th;
 };
 
+// Records msg as the calling thread's rgba_last_error() text and returns code.
+int set_error(int code, const char *msg);
+
 // Launch wrappers (each returns the cudaError_t of its launch).
 cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t s);
-cudaError_t launch_preprocess(const Ctx &c, int max_n, cudaStream_t s);
+cudaError_t launch_preprocess(const Ctx &c, int max_n, int max_k, int max_rows, cudaStream_t s);
 cudaError_t launch_blend(const Ctx &c, int max_n, float *out, cudaStream_t s);
 cudaError_t launch_scan(const Ctx &c, cudaStream_t s);
 cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s);

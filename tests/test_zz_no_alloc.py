@@ -58,3 +58,4 @@ def test_noalloc_rejects_batches_beyond_its_block(renderer):
         api.rgba_render_fwd_noalloc(renderer.ctx, db.struct(), 0, 0, 0,
                                     torch.cuda.current_stream().cuda_stream)
     assert e.value.code == api.RGBA_ERR_INVALID_ARG
+    assert "no-alloc scratch block" in str(e.value)
