@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--variants", type=int, default=4, help="distinct resident input batches")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-per-frame", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-uneven", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=10.0)
     return p.parse_args()
 
 
@@ -353,6 +356,10 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_per_frame:
         per_frame = per_frame_path(api, work[0], dev, r)
 
+    r.close()
+    uneven = None if args.no_uneven else run_uneven(local_rank)
+    serve = None if args.no_serve else run_serve(local_rank, args.serve_seconds)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         b0, t0s = work[0]
@@ -384,9 +391,9 @@ def run_ours(args, rank, world, local_rank):
                 "speedup_vs_per_frame": (value / per_frame["value"]) if per_frame else None,
                 "gpu_launches": launches_per_step * args.steps,
                 "launches_per_step": launches_per_step,
+                "serve": serve, "uneven": uneven,
                 "clocks": ck}
         print(json.dumps(line), flush=True)
-    r.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -430,6 +437,56 @@ def per_frame_path(api, work0, dev, r):
     t = time.perf_counter() - t0
     return {"value": reps * FRAMES / t, "unit": "img/s",
             "path": "one frame per rgba_step (B=1), one host sync per frame"}
+
+
+def run_uneven(local_rank, steps=20):
+    """8 avatars (N 20k..100k, K 16/24/32), 64 frames at 256/512/1024 px in one batch: the
+    autotuner picks tile shape and staging size, then the graph-replayed step is timed."""
+    import torch
+    from paper_2503_12886_gb300 import synth
+    from paper_2503_12886_gb300.batching import GraphStep, autotune
+    from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
+    batch = synth.workload_uneven()
+    targets = synth.make_targets(batch, 4001)
+    r = Renderer(local_rank)
+    tune = autotune(r, batch, targets, steps=3)
+    db = DeviceBatch(batch, f"cuda:{local_rank}", tile=tune.tile, smem_batch=tune.smem_batch)
+    gs = GraphStep(r, db, db.pack_images(targets))
+    for _ in range(3):
+        gs.replay()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        loss, pairs = gs.replay()
+    t = time.perf_counter() - t0
+    r.close()
+    return {"workload": "8 avatars N 20k..100k, K 16/24/32, 64 frames at 256/512/1024 px, one "
+                        "batch per step (fwd+bwd, L1), CUDA-graph replay",
+            "img_per_s": len(batch.frames) * steps / t, "ms_per_step": 1e3 * t / steps,
+            "pairs": pairs, "tuned": {"tile": list(tune.tile), "smem_batch": tune.smem_batch},
+            "autotune_ms": tune.table}
+
+
+def run_serve(local_rank, seconds):
+    """32 resident avatars (N U[30k,100k], K=32), Poisson arrivals at 2000 req/s of forward-only
+    renders at 512x512 (80 %) or 1024x1024 (20 %), 40 GB admission budget, continuous batching;
+    the per-frame serve loop on the same arrivals for comparison."""
+    from paper_2503_12886_gb300 import synth
+    from paper_2503_12886_gb300.serving import Server, requests_from_trace
+    avatars = synth.serving_avatars()
+    trace = synth.serving_requests(duration_s=seconds)
+    srv = Server(avatars, local_rank, hbm_budget=40e9, max_frames=32, slots=3, max_res=1024)
+    warm = requests_from_trace(synth.serving_requests(seed=77, duration_s=0.2), avatars, 77)
+    srv.run(warm, realtime=True)
+    st = srv.run(requests_from_trace(trace, avatars), realtime=True)
+    pf = srv.run_per_frame(requests_from_trace(trace, avatars), realtime=True)
+    srv.close()
+    return {"workload": "32 avatars N U[30k,100k] K=32; Poisson 2000 req/s for "
+                        f"{seconds:g} s; 80 % 512x512 / 20 % 1024x1024; 40 GB budget",
+            "frames_per_s": st["frames_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "requests": st["requests"], "batches": st["batches"],
+            "per_frame": {"frames_per_s": pf["frames_per_s"], "p50_ms": pf["p50_ms"],
+                          "p99_ms": pf["p99_ms"]}}
 
 
 def main():
