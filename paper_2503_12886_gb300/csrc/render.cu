@@ -20,7 +20,6 @@
 namespace rgba {
 namespace {
 
-constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
@@ -33,11 +32,28 @@ __device__ __forceinline__ int find_frame(const Ctx &c, long long t) {
     return lo;
 }
 
-// power and raw alpha; both kernels call this so their decisions agree bit for bit
-__device__ __forceinline__ float eval_power(float dx, float dy, float a, float b, float cc) {
-    float q = __fmaf_rn(cc, __fmul_rn(dy, dy), __fmul_rn(__fmul_rn(a, dx), dx));
-    return __fmaf_rn(-0.5f, q, -__fmul_rn(__fmul_rn(b, dx), dy));
+// A Gaussian as the compositing loops read it from shared memory:
+//   a = (u, v, -a/2, -b)   b = (-c/2, opacity, r, g)   c = (b, tau)
+// tau = -ln(255 o): alpha = o e^power < 1/255 exactly when power < tau, so most pairs (the far
+// tail of a splat, 90 % of all evaluations) are rejected before the exponential. Both kernels
+// stage and evaluate through these two functions, so their decisions agree bit for bit.
+__device__ __forceinline__ void stage_splat(const float4 *rec, unsigned idx, float4 &sa, float4 &sb,
+                                            float2 &sc) {
+    const float4 r0 = rec[(size_t)idx * 3 + 0], r1 = rec[(size_t)idx * 3 + 1];
+    const float r2 = rec[(size_t)idx * 3 + 2].x;
+    sa = make_float4(r0.x, r0.y, -0.5f * r0.z, -r0.w);
+    sb = make_float4(-0.5f * r1.x, r1.y, r1.z, r1.w);
+    sc = make_float2(r2, -__logf(255.0f * r1.y));
 }
+
+// power = -(a dx^2 + c dy^2)/2 - b dx dy = dx ((-a/2) dx + (-b) dy) + (-c/2) dy dy
+__device__ __forceinline__ float power_of(float dx, float dy, const float4 &A, const float4 &B) {
+    return __fmaf_rn(dx, __fmaf_rn(A.z, dx, __fmul_rn(A.w, dy)), __fmul_rn(__fmul_rn(B.x, dy), dy));
+}
+
+// the skip decision: a positive power (never, for a positive definite conic, but kept as the
+// definition) or alpha below 1/255
+__device__ __forceinline__ bool skip(float power, float tau) { return power > 0.0f || power < tau; }
 
 constexpr int kThreads = kTilePix / 2;  // backward: two pixels per thread, rows y and y + TH/2
 
@@ -48,14 +64,12 @@ struct PixF {
 };
 
 // One list entry for one pixel (forward); marks the pixel done when it saturates.
-__device__ __forceinline__ void composite(PixF &p, const float4 &A, const float4 &Bv, float cb,
+__device__ __forceinline__ void composite(PixF &p, const float4 &A, const float4 &Bv, const float2 &Cc,
                                           int pos) {
-    if (p.done) return;
     const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
-    const float power = eval_power(dx, dy, A.z, A.w, Bv.x);
-    if (power > 0.0f) return;
+    const float power = power_of(dx, dy, A, Bv);
+    if (skip(power, Cc.y)) return;
     const float alpha = fminf(kAlphaMax, __fmul_rn(Bv.y, __expf(power)));
-    if (alpha < kAlphaMin) return;
     const float testT = p.T * (1.0f - alpha);
     if (testT < kTMin) {
         p.done = true;
@@ -64,7 +78,7 @@ __device__ __forceinline__ void composite(PixF &p, const float4 &A, const float4
     const float wgt = alpha * p.T;
     p.C0 = fmaf(Bv.z, wgt, p.C0);
     p.C1 = fmaf(Bv.w, wgt, p.C1);
-    p.C2 = fmaf(cb, wgt, p.C2);
+    p.C2 = fmaf(Cc.x, wgt, p.C2);
     p.T = testT;
     p.last = pos;
 }
@@ -74,9 +88,9 @@ __global__ void __launch_bounds__(kTilePix)
 k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *__restrict__ n_contrib,
              const float *__restrict__ target, int loss_kind, float *__restrict__ dl_dimg) {
     constexpr int TH = kTilePix / TW;
-    __shared__ float4 s_a[BATCH];  // u, v, conic a, conic b
-    __shared__ float4 s_b[BATCH];  // conic c, opacity, r, g
-    __shared__ float s_c[BATCH];   // b
+    __shared__ float4 s_a[BATCH];
+    __shared__ float4 s_b[BATCH];
+    __shared__ float2 s_c[BATCH];
     __shared__ unsigned s_w;
     __shared__ float s_red[kTilePix / 32];
     if (c.cnt->overflow) return;
@@ -100,12 +114,7 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
         const float4 *rec = c.records + (size_t)f.rec_base * 3;
         for (unsigned base = st; base < en; base += BATCH) {
             if (__syncthreads_count(p.done) == kTilePix) break;
-            if (tid < BATCH && base + tid < en) {
-                const unsigned idx = c.sorted[base + tid];
-                s_a[tid] = rec[(size_t)idx * 3 + 0];
-                s_b[tid] = rec[(size_t)idx * 3 + 1];
-                s_c[tid] = rec[(size_t)idx * 3 + 2].x;
-            }
+            if (tid < BATCH && base + tid < en) stage_splat(rec, c.sorted[base + tid], s_a[tid], s_b[tid], s_c[tid]);
             __syncthreads();
             const int cnt = min(BATCH, (int)(en - base));
             const int pos0 = (int)(base - st) + 1;
@@ -161,15 +170,15 @@ struct PixB {
 // One list entry for one pixel, in reverse; adds this pixel's share of the entry's gradient
 // dL/d(u, v, conic a, b, c, opacity, r, g, b) into v. Returns whether the pixel blended it.
 __device__ __forceinline__ bool accumulate(PixB &p, int pos, const float4 &A, const float4 &Bv,
-                                           float cb, float v[9]) {
+                                           const float2 &Cc, float v[9]) {
     if (pos > p.last) return false;
     const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
-    const float power = eval_power(dx, dy, A.z, A.w, Bv.x);
-    if (power > 0.0f) return false;
+    const float power = power_of(dx, dy, A, Bv);
+    if (skip(power, Cc.y)) return false;
+    const float cb = Cc.x;
     const float G = __expf(power);
     const float araw = __fmul_rn(Bv.y, G);
     const float alpha = fminf(kAlphaMax, araw);
-    if (alpha < kAlphaMin) return false;
     const float oma = 1.0f - alpha;
     const float inv = __fdividef(1.0f, oma);  // 1 - alpha >= 0.01
     p.T = p.T * inv;  // transmittance in front of this Gaussian
@@ -188,8 +197,9 @@ __device__ __forceinline__ bool accumulate(PixB &p, int pos, const float4 &A, co
         v[2] = fmaf(-0.5f * dx * dx, dpow, v[2]);
         v[3] = fmaf(-dx * dy, dpow, v[3]);
         v[4] = fmaf(-0.5f * dy * dy, dpow, v[4]);
-        v[0] = fmaf(dpow, A.z * dx + A.w * dy, v[0]);
-        v[1] = fmaf(dpow, Bv.x * dy + A.w * dx, v[1]);
+        // conic a = -2 A.z, b = -A.w, c = -2 B.x
+        v[0] = fmaf(-dpow, 2.0f * A.z * dx + A.w * dy, v[0]);
+        v[1] = fmaf(-dpow, 2.0f * Bv.x * dy + A.w * dx, v[1]);
     }
     return true;
 }
@@ -231,7 +241,7 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
     constexpr int TH = kTilePix / TW;
     __shared__ float4 s_a[BATCH];
     __shared__ float4 s_b[BATCH];
-    __shared__ float s_c[BATCH];
+    __shared__ float2 s_c[BATCH];
     __shared__ unsigned s_idx[BATCH];
     __shared__ float s_g[BATCH][9];  // per entry: stride 9 keeps lanes on distinct banks
     __shared__ unsigned s_w;
@@ -288,21 +298,19 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
             for (int e = tid; e < cnt; e += kThreads) {
                 const unsigned idx = c.sorted[st + begin + e];
                 s_idx[e] = idx;
-                s_a[e] = rec[(size_t)idx * 3 + 0];
-                s_b[e] = rec[(size_t)idx * 3 + 1];
-                s_c[e] = rec[(size_t)idx * 3 + 2].x;
+                stage_splat(rec, idx, s_a[e], s_b[e], s_c[e]);
             }
             for (int e = tid; e < 9 * BATCH; e += kThreads) (&s_g[0][0])[e] = 0.f;
             __syncthreads();
             for (int j = min(cnt, warp_last - begin) - 1; j >= 0; --j) {
                 const int pos = begin + j + 1;
                 const float4 A = s_a[j], Bv = s_b[j];
-                const float cb = s_c[j];
+                const float2 Cc = s_c[j];
                 float v[9];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) v[q] = 0.f;
-                bool any = accumulate(p[0], pos, A, Bv, cb, v);
-                any |= accumulate(p[1], pos, A, Bv, cb, v);
+                bool any = accumulate(p[0], pos, A, Bv, Cc, v);
+                any |= accumulate(p[1], pos, A, Bv, Cc, v);
                 if (__any_sync(0xffffffffu, any)) {
                     float mine, v8;
                     warp_reduce9(v, lane, mine, v8);
