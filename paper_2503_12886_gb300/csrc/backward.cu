@@ -1,23 +1,20 @@
 // Backward through the projection (EWA splatting, activations) and the linear blend (Eq. 1).
 //
-// One CTA owns a chunk of 32 Gaussians of one model and walks the frames that render that model
-// in groups of up to 32:
-//   phase 1  per (frame, Gaussian): the 2-D gradients dL/d(u, v, conic, opacity, colour) from
-//            compositing -> dL/dG_b over the 14 blended channels (chain rule through conic
-//            inversion, J W Sigma W^T J^T, R diag(s^2) R^T, quaternion normalisation, exp and
-//            sigmoid), written to shared memory as [frame][channel][Gaussian];
-//   phase 2  the adjoint of Eq. 1 with lane = Gaussian:
-//            dG0[ch][i]    += sum_b dG_b[ch][i]
-//            ddG[k][a][i]  += sum_b psi_b[k] dG_b[ch_a][i]
-//            dpsi_b[k]     partial = sum_{a, i in chunk} dG_k[a][i] dG_b[ch_a][i]
+//   k_chain      one thread per (frame, Gaussian): the 2-D gradients dL/d(u, v, conic,
+//                opacity, colour) from compositing -> dL/dG_b over the 14 blended channels
+//                (chain rule through conic inversion, J W Sigma W^T J^T, R diag(s^2) R^T,
+//                quaternion normalisation, exp and sigmoid), streamed to the workspace;
+//   k_blend_bwd  one CTA per 32 Gaussians of one model, lane = Gaussian, the adjoint of Eq. 1:
+//                dG0[ch][i]    += sum_b dG_b[ch][i]
+//                ddG[k][a][i]  += sum_b psi_b[k] dG_b[ch_a][i]
+//                dpsi_b[k]     partial = sum_{a, i in chunk} dG_k[a][i] dG_b[ch_a][i]
 // The reduction over frames happens in registers in a fixed order, so dG0 and ddG are
-// deterministic; dpsi partials go to a [frame][k][chunk] buffer that a second kernel sums.
+// deterministic; dpsi partials go to a [frame][k][chunk] buffer that a third kernel sums.
 #include "rgba_internal.cuh"
 
 namespace rgba {
 namespace {
 
-constexpr int kFG = 32;          // frames per group
 constexpr int kBwdThreads = 256;
 
 struct Fwd {
@@ -187,11 +184,51 @@ __device__ __forceinline__ void chain(const float v[10], float op, const float *
     for (int c = 0; c < 3; ++c) dG[c] = V[c] * dp0 + V[4 + c] * dp1 + V[8 + c] * dp2;
 }
 
+// Phase 1, streaming: one thread per (frame, Gaussian); dL/dG_b over the 14 channels into the
+// workspace ([R][16] floats, channels 14 and 15 zero).
+constexpr int kChainThreads = 256;
+
+__global__ void __launch_bounds__(kChainThreads)
+k_chain(Ctx c) {
+    __shared__ float s_fp[RGBA_FP_STRIDE];
+    const int b = blockIdx.y;
+    const FrameInfo f = c.frames[b];
+    if (threadIdx.x < RGBA_FP_STRIDE) s_fp[threadIdx.x] = c.fparams[(size_t)b * RGBA_FP_STRIDE + threadIdx.x];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= f.n) return;
+    const long long r = f.rec_base + i;
+    float dG[kNch];
+#pragma unroll
+    for (int q = 0; q < kNch; ++q) dG[q] = 0.f;
+    const ushort4 rc = c.rects[r];
+    if (rc.z > rc.x && rc.w > rc.y) {
+        const float4 c0 = c.cache[r * 3 + 0], c1 = c.cache[r * 3 + 1], c2 = c.cache[r * 3 + 2];
+        const float v[10] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y};
+        const float4 *gp = reinterpret_cast<const float4 *>(c.grad2d + r * kG2Floats);
+        const float4 ga = gp[0], gb = gp[1], gc = gp[2];
+        const float g2[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
+        const float op = c.records[r * 3 + 1].y;
+        chain(v, op, s_fp, f.W, f.H, g2, dG);
+    }
+    float4 *o = reinterpret_cast<float4 *>(c.dgb + r * 16);
+    o[0] = make_float4(dG[0], dG[1], dG[2], dG[3]);
+    o[1] = make_float4(dG[4], dG[5], dG[6], dG[7]);
+    o[2] = make_float4(dG[8], dG[9], dG[10], dG[11]);
+    o[3] = make_float4(dG[12], dG[13], 0.f, 0.f);
+}
+
+// Phase 2: the adjoint of Eq. 1. One CTA = 32 Gaussians (lane = Gaussian) of one model; the
+// frames that render it go through shared memory 16 at a time.
+constexpr int kFG2 = 16;
+constexpr int kWarps = kBwdThreads / 32;
+
 __global__ void __launch_bounds__(kBwdThreads)
-k_gauss_bwd(Ctx c, int max_k) {
+k_blend_bwd(Ctx c, int max_k) {
     extern __shared__ float smem[];
-    float *s_dG = smem;                               // [kFG][14][32]
-    float *s_psi = smem + kFG * kNch * kBwdChunk;     // [kFG][max_k]
+    float *s_dG = smem;                                   // [16][14][32]
+    float *s_psi = s_dG + kFG2 * kNch * kBwdChunk;        // [16][max_k]
+    float *s_red = s_psi + kFG2 * max_k;                  // [warps][32][17]
     const ModelInfo &m = c.models[blockIdx.y];
     const int chunk = blockIdx.x;
     const int i0 = chunk * kBwdChunk;
@@ -201,64 +238,59 @@ k_gauss_bwd(Ctx c, int max_k) {
     const bool valid = i < m.n;      // real Gaussian
     const bool in_pad = i < m.n_pad; // row slot (padding slots receive zeros)
     const int K = m.k, A = m.A;
-    for (int g0 = 0; g0 < m.nb; g0 += kFG) {
-        const int ng = min(kFG, m.nb - g0);
-        // phase 1: per (frame, Gaussian) chain rule
-        for (int item = threadIdx.x; item < kFG * kBwdChunk; item += kBwdThreads) {
-            const int fl = item / kBwdChunk, li = item % kBwdChunk;
-            float dG[kNch];
-#pragma unroll
-            for (int q = 0; q < kNch; ++q) dG[q] = 0.f;
+    float *red = s_red + warp * 32 * (kFG2 + 1);
+    for (int g0 = 0; g0 < m.nb; g0 += kFG2) {
+        const int ng = min(kFG2, m.nb - g0);
+        // dL/dG_b of the chunk: 4 float4 per (frame, Gaussian), coalesced
+        for (int e = threadIdx.x; e < ng * kBwdChunk * 4; e += kBwdThreads) {
+            const int fl = e / (kBwdChunk * 4), rem = e - fl * kBwdChunk * 4;
+            const int li = rem >> 2, q4 = rem & 3;
             const int gi = i0 + li;
-            if (fl < ng && gi < m.n) {
-                const int b = c.mframes[m.frame_off + g0 + fl];
-                const FrameInfo &f = c.frames[b];
-                const long long r = f.rec_base + gi;
-                const ushort4 rc = c.rects[r];
-                if (rc.z > rc.x && rc.w > rc.y) {
-                    const float4 c0 = c.cache[r * 3 + 0], c1 = c.cache[r * 3 + 1], c2 = c.cache[r * 3 + 2];
-                    const float v[10] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y};
-                    const float4 *gp = reinterpret_cast<const float4 *>(c.grad2d + r * kG2Floats);
-                    const float4 ga = gp[0], gb = gp[1], gc = gp[2];
-                    const float g2[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
-                    const float op = c.records[r * 3 + 1].y;
-                    chain(v, op, c.fparams + (size_t)b * RGBA_FP_STRIDE, f.W, f.H, g2, dG);
-                }
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gi < m.n) {
+                const FrameInfo &f = c.frames[c.mframes[m.frame_off + g0 + fl]];
+                v = reinterpret_cast<const float4 *>(c.dgb + (f.rec_base + (long long)gi) * 16)[q4];
             }
-#pragma unroll
-            for (int q = 0; q < kNch; ++q) s_dG[(fl * kNch + q) * kBwdChunk + li] = dG[q];
+            float *d = s_dG + (fl * kNch + q4 * 4) * kBwdChunk + li;
+            d[0] = v.x;
+            d[kBwdChunk] = v.y;
+            if (q4 < 3) {
+                d[2 * kBwdChunk] = v.z;
+                d[3 * kBwdChunk] = v.w;
+            }
         }
-        for (int e = threadIdx.x; e < kFG * max_k; e += kBwdThreads) {
+        // frames past the group's end read as zero (the loops below run over all 16 slots)
+        for (int e = ng * kNch * kBwdChunk + threadIdx.x; e < kFG2 * kNch * kBwdChunk; e += kBwdThreads)
+            s_dG[e] = 0.f;
+        for (int e = threadIdx.x; e < kFG2 * max_k; e += kBwdThreads) {
             const int fl = e / max_k, kk = e % max_k;
             s_psi[e] = (fl < ng && kk < K) ? c.psi[(size_t)c.mframes[m.frame_off + g0 + fl] * c.k_stride + kk] : 0.f;
         }
         __syncthreads();
-        // phase 2a: dG0
+        // dG0[ch][i] = sum_b dG_b[ch][i]
         if (m.gg0 && in_pad) {
-            for (int ch = warp; ch < kNch; ch += kBwdThreads / 32) {
+            for (int ch = warp; ch < kNch; ch += kWarps) {
                 float a = 0.f;
                 for (int fl = 0; fl < ng; ++fl) a += s_dG[(fl * kNch + ch) * kBwdChunk + lane];
                 float *o = m.gg0 + (size_t)ch * m.n_pad + i;
                 *o = (g0 == 0 ? 0.f : *o) + a;
             }
         }
-        // phase 2b/2c: ddG and dpsi partials, one k per warp iteration
-        for (int kk = warp; kk < K; kk += kBwdThreads / 32) {
-            float psum[kFG];
+        // ddG[k][a][i] = sum_b psi_b[k] dG_b[ch_a][i];  dpsi_b[k] partial = sum_a,i dG_k[a][i] dG_b[ch_a][i]
+        for (int kk = warp; kk < K; kk += kWarps) {
+            float psum[kFG2];
 #pragma unroll
-            for (int fl = 0; fl < kFG; ++fl) psum[fl] = 0.f;
+            for (int fl = 0; fl < kFG2; ++fl) psum[fl] = 0.f;
             for (int a = 0; a < A; ++a) {
                 const int ch = m.chans[a];
                 const size_t off = ((size_t)kk * A + a) * m.n_pad + i;
                 const float dgv = valid ? __ldg(m.dg + off) : 0.f;
                 float acc = 0.f;
 #pragma unroll
-                for (int fl = 0; fl < kFG; ++fl) {
-                    if (fl < ng) {
-                        const float d = s_dG[(fl * kNch + ch) * kBwdChunk + lane];
-                        acc = fmaf(s_psi[fl * max_k + kk], d, acc);
-                        psum[fl] = fmaf(dgv, d, psum[fl]);
-                    }
+                for (int fl = 0; fl < kFG2; ++fl) {
+                    const float d = s_dG[(fl * kNch + ch) * kBwdChunk + lane];
+                    acc = fmaf(s_psi[fl * max_k + kk], d, acc);
+                    psum[fl] = fmaf(dgv, d, psum[fl]);
                 }
                 if (m.gdg && in_pad) {
                     float *o = m.gdg + off;
@@ -266,15 +298,17 @@ k_gauss_bwd(Ctx c, int max_k) {
                 }
             }
             if (c.grad_psi) {
+                // warp sum of psum[fl] for every fl: transpose through shared memory
 #pragma unroll
-                for (int fl = 0; fl < kFG; ++fl) {
-                    if (fl < ng) {
-                        float x = psum[fl];
-                        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                        if (lane == 0)
-                            c.dpsi_part[m.dpsi_off + ((long long)(g0 + fl) * K + kk) * m.n_chunks + chunk] = x;
-                    }
+                for (int fl = 0; fl < kFG2; ++fl) red[lane * (kFG2 + 1) + fl] = psum[fl];
+                __syncwarp();
+                if (lane < ng) {
+                    float x = 0.f;
+#pragma unroll 8
+                    for (int l = 0; l < 32; ++l) x += red[l * (kFG2 + 1) + lane];
+                    c.dpsi_part[m.dpsi_off + ((long long)(g0 + lane) * K + kk) * m.n_chunks + chunk] = x;
                 }
+                __syncwarp();
             }
         }
         __syncthreads();
@@ -304,24 +338,27 @@ __global__ void k_dpsi_reduce(Ctx c) {
 
 }  // namespace
 
-cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_nb, int max_k, cudaStream_t s) {
-    (void)max_nb;
+cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_n, int max_k, cudaStream_t s) {
     if (c.M == 0 || max_chunks == 0) return cudaSuccess;
-    const int smem = (kFG * kNch * kBwdChunk + kFG * max_k) * (int)sizeof(float);
+    dim3 g1((max_n + kChainThreads - 1) / kChainThreads, c.B);
+    k_chain<<<g1, kChainThreads, 0, s>>>(c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto bytes = [](int k) {
+        return (kFG2 * kNch * kBwdChunk + kFG2 * k + kWarps * 32 * (kFG2 + 1)) * (int)sizeof(float);
+    };
     // set once, at the largest size any batch can ask for, so no attribute call happens while
     // a stream is being captured
     static int attr_device = -1;
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if (attr_device != dev) {
-        const int most = (kFG * kNch * kBwdChunk + kFG * RGBA_MAX_K) * (int)sizeof(float);
-        e = cudaFuncSetAttribute(k_gauss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        e = cudaFuncSetAttribute(k_blend_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes(RGBA_MAX_K));
         if (e != cudaSuccess) return e;
         attr_device = dev;
     }
-    dim3 grid(max_chunks, c.M);
-    k_gauss_bwd<<<grid, kBwdThreads, smem, s>>>(c, max_k);
+    dim3 g2(max_chunks, c.M);
+    k_blend_bwd<<<g2, kBwdThreads, bytes(max_k), s>>>(c, max_k);
     return cudaGetLastError();
 }
 

@@ -64,7 +64,7 @@ static_assert(sizeof(Counters) <= 256, "counters fit in one 256-byte block");
 
 struct Layout {
     size_t counters, models, frames, mframes, tile_count, tile_start, cursor, work;
-    size_t records, rects, cache, grad2d, pix_T, pix_n, pix_dl, pix_img, dpsi_part;
+    size_t records, rects, cache, grad2d, dgb, pix_T, pix_n, pix_dl, pix_img, dpsi_part;
     size_t keys, sorted, total;
     long long R, T, P;     // records, tiles, pixels
     long long dpsi_floats;
@@ -93,6 +93,7 @@ struct Ctx {
     unsigned long long *keys;
     unsigned *sorted;
     float *dpsi_part;
+    float *dgb;        // [R][16]: dL/dG_b per (frame, Gaussian), 14 channels used
     long long R, T, cap;
     int B, M, k_stride, tw, th;
 };
@@ -112,8 +113,7 @@ cudaError_t launch_render_fwd(const Ctx &c, int grid, int smem_batch, float *img
                               float *dl_dimg, const long long *pix_base_dummy, cudaStream_t s);
 cudaError_t launch_render_bwd(const Ctx &c, int grid, int smem_batch, const float *dl_dimg,
                               const float *T_final, const int *n_contrib, cudaStream_t s);
-cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_nb, int max_k,
-                             cudaStream_t s);
+cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_n, int max_k, cudaStream_t s);
 cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s);
 
 }  // namespace rgba
