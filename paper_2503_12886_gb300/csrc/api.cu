@@ -149,7 +149,7 @@ int make_plan(const rgba_batch *b, Plan &p) {
     L.models = take(sizeof(ModelInfo) * (size_t)M);
     L.frames = take(sizeof(FrameInfo) * (size_t)B);
     L.mframes = take(sizeof(int) * (size_t)B);
-    L.tile_count = take(4 * (size_t)T);
+    L.tile_count = take(8 * (size_t)T);
     L.tile_start = take(4 * (size_t)(T + 1));
     L.cursor = take(4 * (size_t)T);
     L.work = take(4 * (size_t)T);
@@ -158,6 +158,7 @@ int make_plan(const rgba_batch *b, Plan &p) {
     L.cache = take(sizeof(float) * kCacheFloats * (size_t)R);
     L.grad2d = take(sizeof(float) * kG2Floats * (size_t)R);
     L.dgb = take(sizeof(float) * 16 * (size_t)R);
+    L.ranks = take(4 * kRankSlots * (size_t)R);
     L.pix_T = take(4 * (size_t)P);
     L.pix_n = take(4 * (size_t)P);
     L.pix_dl = take(12 * (size_t)P);
@@ -210,6 +211,7 @@ Ctx make_ctx(const Layout &L, unsigned char *ws, const rgba_batch *b) {
     c.sorted = reinterpret_cast<unsigned *>(ws + L.sorted);
     c.dpsi_part = reinterpret_cast<float *>(ws + L.dpsi_part);
     c.dgb = reinterpret_cast<float *>(ws + L.dgb);
+    c.ranks = reinterpret_cast<unsigned *>(ws + L.ranks);
     c.R = L.R;
     c.T = L.T;
     c.cap = L.cap;
@@ -301,7 +303,7 @@ int do_preprocess(rgba_ctx_t ctx, Call &k) {
     int rc;
     if ((rc = upload_tables(ctx, k))) return rc;
     if ((rc = memset_async(k.ws + k.p.L.counters, 256, k.s, "memset counters"))) return rc;
-    if ((rc = memset_async(k.ws + k.p.L.tile_count, 4 * (size_t)k.p.L.T, k.s, "memset tile counts"))) return rc;
+    if ((rc = memset_async(k.ws + k.p.L.tile_count, 8 * (size_t)k.p.L.T, k.s, "memset tile counts"))) return rc;
     StageScope sc(ctx, ST_PRE, k.s, 1);
     int max_rows = 0;
     for (const ModelInfo &m : k.p.models) max_rows = std::max(max_rows, kNch + m.k * m.A);

@@ -190,9 +190,28 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const FrameInfo &
         r1 = make_float4(cc, op, v[11], v[12]);
         r2 = make_float4(v[13], p[2], 0.f, 0.f);
         rc = make_ushort4((unsigned short)ix0, (unsigned short)iy0, (unsigned short)ix1, (unsigned short)iy1);
-        unsigned *tc = c.tile_count + f.tile_base;
-        for (int ty = iy0; ty < iy1; ++ty)
-            for (int tx = ix0; tx < ix1; ++tx) atomicAdd(tc + ty * f.tiles_x + tx, 1u);
+        // count the Gaussian in every tile of its rectangle; for rectangles of up to kRankSlots
+        // tiles keep the slot each count returns, so the scatter needs no atomics
+        const int rw = ix1 - ix0, area = rw * (iy1 - iy0);
+        if (area <= kRankSlots) {
+            unsigned *tc = c.tile_count + f.tile_base;
+            unsigned rk[kRankSlots];
+#pragma unroll
+            for (int q = 0; q < kRankSlots; ++q) {
+                rk[q] = 0u;
+                if (q < area) {
+                    const int dy = q / rw;
+                    rk[q] = atomicAdd(tc + (iy0 + dy) * f.tiles_x + ix0 + (q - dy * rw), 1u);
+                }
+            }
+            uint4 *rp = reinterpret_cast<uint4 *>(c.ranks + r * kRankSlots);
+            rp[0] = make_uint4(rk[0], rk[1], rk[2], rk[3]);
+            rp[1] = make_uint4(rk[4], rk[5], rk[6], rk[7]);
+        } else {
+            unsigned *tb = c.tile_count + c.T + f.tile_base;
+            for (int ty = iy0; ty < iy1; ++ty)
+                for (int tx = ix0; tx < ix1; ++tx) atomicAdd(tb + ty * f.tiles_x + tx, 1u);
+        }
     } while (0);
     c.records[r * 3 + 0] = r0;
     c.records[r * 3 + 1] = r1;

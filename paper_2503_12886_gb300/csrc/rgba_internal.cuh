@@ -24,6 +24,7 @@ constexpr int kCacheFloats = 12; // backward cache: mean(3), quat(4), log-scale(
 constexpr int kG2Floats = 12;    // 2-D gradient: du, dv, da, db, dc, dopacity, dr, dg, db, -
 constexpr int kTilePix = 256;    // pixels per screen tile (16x16 or 8x32)
 constexpr int kBwdChunk = 32;    // Gaussians per CTA in the fused preprocess/blend backward
+constexpr int kRankSlots = 8;    // tiles per Gaussian whose in-tile slot preprocess records
 
 // Per-model table (device copy in the workspace).
 struct ModelInfo {
@@ -64,7 +65,7 @@ static_assert(sizeof(Counters) <= 256, "counters fit in one 256-byte block");
 
 struct Layout {
     size_t counters, models, frames, mframes, tile_count, tile_start, cursor, work;
-    size_t records, rects, cache, grad2d, dgb, pix_T, pix_n, pix_dl, pix_img, dpsi_part;
+    size_t records, rects, cache, grad2d, dgb, ranks, pix_T, pix_n, pix_dl, pix_img, dpsi_part;
     size_t keys, sorted, total;
     long long R, T, P;     // records, tiles, pixels
     long long dpsi_floats;
@@ -82,7 +83,7 @@ struct Ctx {
     const float *fparams;
     float *grad_psi;
     Counters *cnt;
-    unsigned *tile_count;
+    unsigned *tile_count;  // [2T]: Gaussians with at most kRankSlots tiles, then the others
     unsigned *tile_start;
     unsigned *cursor;
     unsigned *work;
@@ -94,6 +95,7 @@ struct Ctx {
     unsigned *sorted;
     float *dpsi_part;
     float *dgb;        // [R][16]: dL/dG_b per (frame, Gaussian), 14 channels used
+    unsigned *ranks;   // [R][kRankSlots]: slot of the Gaussian in each tile of its rectangle
     long long R, T, cap;
     int B, M, k_stride, tw, th;
 };
