@@ -33,22 +33,23 @@ __device__ __forceinline__ int find_frame(const Ctx &c, long long t) {
 }
 
 // A Gaussian as the compositing loops read it from shared memory:
-//   a = (u, v, -a/2, -b)   b = (-c/2, opacity, r, g)   c = (b, tau)
+//   a = (u, v, -a/2, -b)   q = (-c/2, tau)   c = (opacity, r, g, b)
 // tau = -ln(255 o): alpha = o e^power < 1/255 exactly when power < tau, so most pairs (the far
-// tail of a splat, 90 % of all evaluations) are rejected before the exponential. Both kernels
-// stage and evaluate through these two functions, so their decisions agree bit for bit.
-__device__ __forceinline__ void stage_splat(const float4 *rec, unsigned idx, float4 &sa, float4 &sb,
-                                            float2 &sc) {
+// tail of a splat, 90 % of all evaluations) are rejected from a and q alone, before the
+// exponential and before the colour is read. Both kernels stage and evaluate through these
+// functions, so their decisions agree bit for bit.
+__device__ __forceinline__ void stage_splat(const float4 *rec, unsigned idx, float4 &sa, float2 &sq,
+                                            float4 &sc) {
     const float4 r0 = rec[(size_t)idx * 3 + 0], r1 = rec[(size_t)idx * 3 + 1];
     const float r2 = rec[(size_t)idx * 3 + 2].x;
     sa = make_float4(r0.x, r0.y, -0.5f * r0.z, -r0.w);
-    sb = make_float4(-0.5f * r1.x, r1.y, r1.z, r1.w);
-    sc = make_float2(r2, -__logf(255.0f * r1.y));
+    sq = make_float2(-0.5f * r1.x, -__logf(255.0f * r1.y));
+    sc = make_float4(r1.y, r1.z, r1.w, r2);
 }
 
 // power = -(a dx^2 + c dy^2)/2 - b dx dy = dx ((-a/2) dx + (-b) dy) + (-c/2) dy dy
-__device__ __forceinline__ float power_of(float dx, float dy, const float4 &A, const float4 &B) {
-    return __fmaf_rn(dx, __fmaf_rn(A.z, dx, __fmul_rn(A.w, dy)), __fmul_rn(__fmul_rn(B.x, dy), dy));
+__device__ __forceinline__ float power_of(float dx, float dy, const float4 &A, const float2 &Q) {
+    return __fmaf_rn(dx, __fmaf_rn(A.z, dx, __fmul_rn(A.w, dy)), __fmul_rn(__fmul_rn(Q.x, dy), dy));
 }
 
 // the skip decision: a positive power (never, for a positive definite conic, but kept as the
@@ -64,21 +65,24 @@ struct PixF {
 };
 
 // One list entry for one pixel (forward); marks the pixel done when it saturates.
-__device__ __forceinline__ void composite(PixF &p, const float4 &A, const float4 &Bv, const float2 &Cc,
-                                          int pos) {
+__device__ __forceinline__ void composite(PixF &p, const float4 *s_a, const float2 *s_q,
+                                          const float4 *s_c, int j, int pos) {
+    const float4 A = s_a[j];
+    const float2 Q = s_q[j];
     const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
-    const float power = power_of(dx, dy, A, Bv);
-    if (skip(power, Cc.y)) return;
-    const float alpha = fminf(kAlphaMax, __fmul_rn(Bv.y, __expf(power)));
+    const float power = power_of(dx, dy, A, Q);
+    if (skip(power, Q.y)) return;
+    const float4 Cc = s_c[j];
+    const float alpha = fminf(kAlphaMax, __fmul_rn(Cc.x, __expf(power)));
     const float testT = p.T * (1.0f - alpha);
     if (testT < kTMin) {
         p.done = true;
         return;
     }
     const float wgt = alpha * p.T;
-    p.C0 = fmaf(Bv.z, wgt, p.C0);
-    p.C1 = fmaf(Bv.w, wgt, p.C1);
-    p.C2 = fmaf(Cc.x, wgt, p.C2);
+    p.C0 = fmaf(Cc.y, wgt, p.C0);
+    p.C1 = fmaf(Cc.z, wgt, p.C1);
+    p.C2 = fmaf(Cc.w, wgt, p.C2);
     p.T = testT;
     p.last = pos;
 }
@@ -89,8 +93,8 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
              const float *__restrict__ target, int loss_kind, float *__restrict__ dl_dimg) {
     constexpr int TH = kTilePix / TW;
     __shared__ float4 s_a[BATCH];
-    __shared__ float4 s_b[BATCH];
-    __shared__ float2 s_c[BATCH];
+    __shared__ float2 s_q[BATCH];
+    __shared__ float4 s_c[BATCH];
     __shared__ unsigned s_w;
     __shared__ float s_red[kTilePix / 32];
     if (c.cnt->overflow) return;
@@ -114,11 +118,15 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
         const float4 *rec = c.records + (size_t)f.rec_base * 3;
         for (unsigned base = st; base < en; base += BATCH) {
             if (__syncthreads_count(p.done) == kTilePix) break;
-            if (tid < BATCH && base + tid < en) stage_splat(rec, c.sorted[base + tid], s_a[tid], s_b[tid], s_c[tid]);
+            if (tid < BATCH && base + tid < en) stage_splat(rec, c.sorted[base + tid], s_a[tid], s_q[tid], s_c[tid]);
             __syncthreads();
             const int cnt = min(BATCH, (int)(en - base));
             const int pos0 = (int)(base - st) + 1;
-            for (int j = 0; j < cnt && !p.done; ++j) composite(p, s_a[j], s_b[j], s_c[j], pos0 + j);
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                if (p.done) break;
+                composite(p, s_a, s_q, s_c, j, pos0 + j);
+            }
         }
         if (p.inside) {
             const float *bg = c.fparams + (size_t)b * RGBA_FP_STRIDE + 17;
@@ -169,13 +177,14 @@ struct PixB {
 
 // One list entry for one pixel, in reverse; adds this pixel's share of the entry's gradient
 // dL/d(u, v, conic a, b, c, opacity, r, g, b) into v. Returns whether the pixel blended it.
-__device__ __forceinline__ bool accumulate(PixB &p, int pos, const float4 &A, const float4 &Bv,
-                                           const float2 &Cc, float v[9]) {
+__device__ __forceinline__ bool accumulate(PixB &p, int pos, const float4 &A, const float2 &Q,
+                                           const float4 &Cc, float v[9]) {
     if (pos > p.last) return false;
     const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
-    const float power = power_of(dx, dy, A, Bv);
-    if (skip(power, Cc.y)) return false;
-    const float cb = Cc.x;
+    const float power = power_of(dx, dy, A, Q);
+    if (skip(power, Q.y)) return false;
+    const float4 Bv = make_float4(Q.x, Cc.x, Cc.y, Cc.z);  // -c/2, opacity, r, g
+    const float cb = Cc.w;
     const float G = __expf(power);
     const float araw = __fmul_rn(Bv.y, G);
     const float alpha = fminf(kAlphaMax, araw);
@@ -240,8 +249,8 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
              const int *__restrict__ n_contrib) {
     constexpr int TH = kTilePix / TW;
     __shared__ float4 s_a[BATCH];
-    __shared__ float4 s_b[BATCH];
-    __shared__ float2 s_c[BATCH];
+    __shared__ float2 s_q[BATCH];
+    __shared__ float4 s_c[BATCH];
     __shared__ unsigned s_idx[BATCH];
     __shared__ float s_g[BATCH][9];  // per entry: stride 9 keeps lanes on distinct banks
     __shared__ unsigned s_w;
@@ -298,19 +307,19 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
             for (int e = tid; e < cnt; e += kThreads) {
                 const unsigned idx = c.sorted[st + begin + e];
                 s_idx[e] = idx;
-                stage_splat(rec, idx, s_a[e], s_b[e], s_c[e]);
+                stage_splat(rec, idx, s_a[e], s_q[e], s_c[e]);
             }
             for (int e = tid; e < 9 * BATCH; e += kThreads) (&s_g[0][0])[e] = 0.f;
             __syncthreads();
             for (int j = min(cnt, warp_last - begin) - 1; j >= 0; --j) {
                 const int pos = begin + j + 1;
-                const float4 A = s_a[j], Bv = s_b[j];
-                const float2 Cc = s_c[j];
+                const float4 A = s_a[j], Cc = s_c[j];
+                const float2 Q = s_q[j];
                 float v[9];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) v[q] = 0.f;
-                bool any = accumulate(p[0], pos, A, Bv, Cc, v);
-                any |= accumulate(p[1], pos, A, Bv, Cc, v);
+                bool any = accumulate(p[0], pos, A, Q, Cc, v);
+                any |= accumulate(p[1], pos, A, Q, Cc, v);
                 if (__any_sync(0xffffffffu, any)) {
                     float mine, v8;
                     warp_reduce9(v, lane, mine, v8);
