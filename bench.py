@@ -30,7 +30,8 @@ METRIC = ("train img/s (fwd+bwd, batched) & serve frames/s + p99 ms vs per-frame
 WORKLOAD = ("batched training step: N=60,000 Gaussians, K=32 blendshapes (mean, log-scale, "
             "colour blended), B=16 frames at 512x512 per launch, per-frame weights N(0,0.3), "
             "camera yaw/pitch jitter U[-20,20] deg, random background, L1 loss, fused fwd+bwd to "
-            "G0 / blendshapes / weights, CUDA-graph replay, one host sync per step")
+            "G0 / blendshapes / weights, Adam update of G0 and blendshapes (paper learning "
+            "rates), CUDA-graph replay, one host sync per step")
 N_GAUSS, K_BASES, FRAMES, RES = 60_000, 32, 16, 512
 # FP32 FLOPs the compositing backward spends per (pixel, list entry up to the pixel's last
 # contributor): alpha recompute 15, transmittance recovery 2, colour/alpha/background terms 23,
@@ -220,6 +221,7 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.set_device(local_rank)
     from paper_2503_12886_gb300 import api
+    from paper_2503_12886_gb300.optim import Adam
     from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
 
     dev = f"cuda:{local_rank}"
@@ -237,6 +239,7 @@ def run_ours(args, rank, world, local_rank):
     lay = r.layout(dbs[0])
     host_cnt = [torch.zeros(24, dtype=torch.uint8).pin_memory() for _ in dbs]
     structs = [db.struct() for db in dbs]
+    opt = Adam(r, dbs[0])  # the variants share one model: one optimizer
     s = torch.cuda.Stream(device=dev)
     graphs = []
     with torch.cuda.stream(s):
@@ -250,6 +253,7 @@ def run_ours(args, rank, world, local_rank):
                 api.rgba_step_async(r.ctx, structs[j], ws.data_ptr(), ws.numel(),
                                     tgs[j].data_ptr(), api.RGBA_LOSS_L1, img.data_ptr(),
                                     s.cuda_stream)
+                opt.step(s.cuda_stream)
                 host_cnt[j].copy_(ws[lay.counters: lay.counters + 24], non_blocking=True)
             graphs.append(g)
     torch.cuda.synchronize()
@@ -292,14 +296,21 @@ def run_ours(args, rank, world, local_rank):
 
     # per-stage device time (CUDA events on the launching stream), eager steps
     api.rgba_profile_enable(r.ctx, True)
-    prof = []
+    prof, adam_ms = [], []
     with torch.cuda.stream(s):
         for j in range(len(dbs)):
             api.rgba_step_async(r.ctx, structs[j], ws.data_ptr(), ws.numel(), tgs[j].data_ptr(),
                                 api.RGBA_LOSS_L1, img.data_ptr(), s.cuda_stream)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(s)
+            opt.step(s.cuda_stream)
+            a1.record(s)
             prof.append(api.rgba_profile_read(r.ctx))
+            torch.cuda.synchronize()
+            adam_ms.append(a0.elapsed_time(a1))
     api.rgba_profile_enable(r.ctx, False)
     stage_ms = {k: float(np.mean([p[k] for p in prof])) for k in api.STAGES}
+    stage_ms["adam"] = float(np.mean(adam_ms))
     launches_per_step = prof[-1]["launches"]
     # units of the compositing backward of the last profiled step: sum over pixels of
     # n_contrib, which rgba_step keeps in the workspace
@@ -331,6 +342,9 @@ def run_ours(args, rank, world, local_rank):
     stages["preprocess"]["frac_hbm"] = stages["preprocess"]["GB/s"] / peaks["hbm_gbs"]
     stages["gauss_bwd"]["GB/s"] = gbwd_bytes / (stage_ms["gauss_bwd"] / 1e3) / 1e9
     stages["gauss_bwd"]["frac_hbm"] = stages["gauss_bwd"]["GB/s"] / peaks["hbm_gbs"]
+    adam_bytes = 7 * 4 * N_GAUSS * (14 + K * A)  # param, grad, m, v read; param, m, v written
+    stages["adam"]["GB/s"] = adam_bytes / (stage_ms["adam"] / 1e3) / 1e9
+    stages["adam"]["frac_hbm"] = stages["adam"]["GB/s"] / peaks["hbm_gbs"]
 
     # end to end through the C ABI with host buffers: per step the inputs (targets, weights,
     # cameras) travel from pinned host memory, rgba_step runs and reads its result back
@@ -339,14 +353,15 @@ def run_ours(args, rank, world, local_rank):
         host_in.append((tgs[dbs.index(db)].cpu().pin_memory(), db.psi.cpu().pin_memory(),
                         db.fparams.cpu().pin_memory()))
     h2d = sum(x.numel() * x.element_size() for x in host_in[0])
+    e2e_cnt = torch.zeros(24, dtype=torch.uint8).pin_memory()
     with torch.cuda.stream(s):
         for i in range(3):
-            e2e_step(api, r, dbs, tgs, structs, host_in, ws, img, s, i)
+            e2e_step(api, r, dbs, tgs, structs, host_in, ws, img, s, i, opt, lay, e2e_cnt)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         n_e2e = max(10, min(args.steps, 100))
         for i in range(n_e2e):
-            e2e_step(api, r, dbs, tgs, structs, host_in, ws, img, s, i)
+            e2e_step(api, r, dbs, tgs, structs, host_in, ws, img, s, i, opt, lay, e2e_cnt)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
     e2e_value = world * FRAMES * n_e2e / t_e2e
@@ -386,7 +401,8 @@ def run_ours(args, rank, world, local_rank):
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "img/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": 24, "steps": n_e2e,
-                        "path": "rgba_step through the C ABI, inputs copied from pinned host"},
+                        "path": "rgba_step_async + rgba_adam through the C ABI, inputs copied "
+                                "from pinned host, counters read back, one sync per step"},
                 "per_frame": per_frame,
                 "speedup_vs_per_frame": (value / per_frame["value"]) if per_frame else None,
                 "gpu_launches": launches_per_step * args.steps,
@@ -398,17 +414,20 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def e2e_step(api, r, dbs, tgs, structs, host_in, ws, img, s, i):
+def e2e_step(api, r, dbs, tgs, structs, host_in, ws, img, s, i, opt, lay, cnt_host):
+    import numpy as np
     j = i % len(dbs)
     tg_h, psi_h, fp_h = host_in[j]
     tgs[j].copy_(tg_h, non_blocking=True)
     dbs[j].psi.copy_(psi_h, non_blocking=True)
     dbs[j].fparams.copy_(fp_h, non_blocking=True)
-    rc, out = api.rgba_step(r.ctx, structs[j], ws.data_ptr(), ws.numel(), tgs[j].data_ptr(),
-                            api.RGBA_LOSS_L1, img.data_ptr(), s.cuda_stream)
-    if rc != api.RGBA_OK:
+    api.rgba_step_async(r.ctx, structs[j], ws.data_ptr(), ws.numel(), tgs[j].data_ptr(),
+                        api.RGBA_LOSS_L1, img.data_ptr(), s.cuda_stream)
+    opt.step(s.cuda_stream)
+    cnt_host.copy_(ws[lay.counters: lay.counters + 24], non_blocking=True)
+    s.synchronize()  # the step's one host synchronisation: its loss and pair count
+    if cnt_host[:8].numpy().view(np.uint32)[1]:
         raise RuntimeError("e2e step overflowed")
-    return out
 
 
 def per_frame_path(api, work0, dev, r):
@@ -424,19 +443,23 @@ def per_frame_path(api, work0, dev, r):
         db = DeviceBatch(sub, dev, models=base)
         base = db.models
         singles.append((db, db.pack_images(targets[f:f + 1])))
+    from paper_2503_12886_gb300.optim import Adam
     img = torch.empty(3 * RES * RES, dtype=torch.float32, device=dev)
+    opt = Adam(r, singles[0][0])
     for db, tg in singles[:3]:
         r.step(db, tg, api.RGBA_LOSS_L1, img)
+        opt.step()
     torch.cuda.synchronize()
     reps = 3
     t0 = time.perf_counter()
     for _ in range(reps):
         for db, tg in singles:
             r.step(db, tg, api.RGBA_LOSS_L1, img)
+            opt.step()
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     return {"value": reps * FRAMES / t, "unit": "img/s",
-            "path": "one frame per rgba_step (B=1), one host sync per frame"}
+            "path": "one frame per rgba_step (B=1) + Adam, one host sync per frame"}
 
 
 def run_uneven(local_rank, steps=20):

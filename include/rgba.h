@@ -192,6 +192,31 @@ int rgba_step(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes
 int rgba_step_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
                     const float *target, int loss_kind, float *img, void *stream);
 
+/* Adam update of the models' base Gaussians and blendshapes in place, from the gradients a
+ * previous rgba_render_bwd / rgba_step wrote to grad_g0 / grad_dg (Supp. A.3: Adam with
+ * per-attribute learning rates, blendshape rates scaled per attribute; Kingma & Ba 2015):
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;  p -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps)
+ * cfg (host): lr[14] for G0 channels, lr_delta[14] for the blendshape of each blended channel.
+ * states (host array [n_models]): caller-owned device moment buffers shaped like g0 and dg,
+ * zero before the first step; a model whose gradient or moment pointer is NULL is skipped.
+ * step: 1-based Adam step count t, used when step_dev is NULL. step_dev (device int32 or
+ * NULL): the number of completed steps; the call uses t = *step_dev + 1 and increments it on
+ * the device, so a captured graph advances the bias correction on every replay.
+ * Writes models[m].g0 / dg (cast from const). */
+typedef struct {
+    float lr[RGBA_NCH];
+    float lr_delta[RGBA_NCH];
+    float beta1, beta2, eps;
+} rgba_adam_cfg;
+
+typedef struct {
+    float *m_g0, *v_g0;  /* device [14][n_pad] */
+    float *m_dg, *v_dg;  /* device [k][A][n_pad] */
+} rgba_adam_state;
+
+int rgba_adam(rgba_ctx_t ctx, const rgba_batch *batch, const rgba_adam_cfg *cfg,
+              const rgba_adam_state *states, int step, int32_t *step_dev, void *stream);
+
 /* Per-stage device timing with CUDA events on the call's stream (off by default). Stages, in
  * launch order: 0 table upload, 1 preprocess (fused blend + projection), 2 tile-count scan,
  * 3 pair scatter, 4 per-tile depth sort, 5 compositing forward (+ fused loss), 6 compositing

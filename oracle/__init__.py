@@ -295,3 +295,12 @@ def decision_signature(res) -> int:
     for r in res:
         h = hash((h, r.rect.tobytes(), r.hash))
     return h
+
+
+def adam(p, g, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba, ICLR 2015, Algorithm 1) in FP64; lr broadcasts against p."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v

@@ -25,7 +25,7 @@ RGBA_NCH = 14
 EXPORTS = ("rgba_last_error", "rgba_create", "rgba_destroy", "rgba_workspace_size",
            "rgba_workspace_layout", "rgba_blend", "rgba_preprocess", "rgba_bin_sort",
            "rgba_render_fwd", "rgba_render_bwd", "rgba_step", "rgba_step_async",
-           "rgba_profile_enable", "rgba_profile_read", "rgba_render_fwd_noalloc")
+           "rgba_profile_enable", "rgba_profile_read", "rgba_render_fwd_noalloc", "rgba_adam")
 RGBA_N_STAGES = 9
 STAGES = ("upload", "preprocess", "scan", "scatter", "sort", "render_fwd", "render_bwd",
           "gauss_bwd", "dpsi_reduce")
@@ -61,6 +61,16 @@ class RgbaWsLayout(C.Structure):
                 ("pix_T", C.c_size_t), ("pix_n", C.c_size_t), ("pix_dl", C.c_size_t),
                 ("pix_img", C.c_size_t), ("total_bytes", C.c_size_t), ("records_total", C.c_int64),
                 ("tiles_total", C.c_int64), ("pair_capacity", C.c_int64)]
+
+
+class RgbaAdamCfg(C.Structure):
+    _fields_ = [("lr", C.c_float * RGBA_NCH), ("lr_delta", C.c_float * RGBA_NCH),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
+class RgbaAdamState(C.Structure):
+    _fields_ = [("m_g0", C.c_void_p), ("v_g0", C.c_void_p), ("m_dg", C.c_void_p),
+                ("v_dg", C.c_void_p)]
 
 
 class RgbaProfile(C.Structure):
@@ -100,6 +110,8 @@ def lib() -> C.CDLL:
             L.rgba_render_bwd.argtypes = [P, Bp, P, sz, P, P, P, P]
             L.rgba_step.argtypes = [P, Bp, P, sz, P, i32, P, C.POINTER(RgbaStepOut), P]
             L.rgba_step_async.argtypes = [P, Bp, P, sz, P, i32, P, P]
+            L.rgba_adam.argtypes = [P, Bp, C.POINTER(RgbaAdamCfg), C.POINTER(RgbaAdamState), i32, P, P]
+            L.rgba_adam.restype = i32
             L.rgba_render_fwd_noalloc.argtypes = [P, Bp, P, P, P, C.POINTER(RgbaStepOut), P]
             L.rgba_render_fwd_noalloc.restype = i32
             L.rgba_profile_enable.argtypes = [P, i32]
@@ -203,3 +215,10 @@ def rgba_render_fwd_noalloc(ctx, batch, img, T_final, n_contrib, stream) -> tupl
     if rc not in (RGBA_OK, RGBA_ERR_CAPACITY):
         check(rc)
     return rc, out
+
+
+def rgba_adam(ctx, batch, cfg: RgbaAdamCfg, states, step: int, step_dev, stream) -> int:
+    """states: ctypes array of RgbaAdamState, one per model of the batch; step_dev: device
+    int32 pointer (completed steps, advanced on the device) or None to use `step`."""
+    return check(lib().rgba_adam(ctx, C.byref(batch), C.byref(cfg), states, step, step_dev,
+                                 stream))

@@ -29,8 +29,9 @@ class GraphStep:
 
     def __init__(self, renderer: Renderer, db: DeviceBatch, target: torch.Tensor,
                  loss_kind: int = api.RGBA_LOSS_L1, img: torch.Tensor | None = None,
-                 headroom: float = 1.1):
+                 headroom: float = 1.1, optimizer=None):
         self.r, self.db, self.target, self.loss_kind = renderer, db, target, loss_kind
+        self.opt = optimizer  # optim.Adam: its update becomes part of the captured step
         self.img = img if img is not None else torch.empty(
             3 * db.total_pix, dtype=torch.float32, device=target.device)
         self.headroom = headroom
@@ -57,6 +58,8 @@ class GraphStep:
                 api.rgba_step_async(r.ctx, b, self.ws.data_ptr(), self.ws.numel(),
                                     self.target.data_ptr(), self.loss_kind, self.img.data_ptr(),
                                     self.stream.cuda_stream)
+                if self.opt is not None:
+                    self.opt.step(self.stream.cuda_stream)
                 c0 = self.layout.counters
                 self.host.copy_(self.ws[c0: c0 + 24], non_blocking=True)
         torch.cuda.synchronize()

@@ -1,0 +1,129 @@
+// Fused Adam update of every base Gaussian and blendshape of every model in a batch (RGBAvatar
+// Supp. A.3: Adam with per-attribute learning rates; blendshape rates scaled per attribute).
+//   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,  p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
+// (Kingma & Ba, ICLR 2015). Rows are n_pad floats (a multiple of 4), so every thread moves
+// float4s; padding slots carry zero gradients and stay unchanged.
+#include "rgba_internal.cuh"
+
+namespace rgba {
+namespace {
+
+struct AdamModel {
+    float *p0, *g0, *m0, *v0;  // [14][n_pad]
+    float *pd, *gd, *md, *vd;  // [k][A][n_pad]
+    int n_pad, k, A, pad_;
+    float lr0[kNch];
+    float lrd[kNch];           // per blended slot a (first A used)
+};
+
+constexpr int kAdamModels = 16;
+struct AdamChunk {
+    AdamModel m[kAdamModels];
+};
+
+__device__ __forceinline__ void adam4(float4 &p, const float4 g, float4 &m, float4 &v, float lr,
+                                      float b1, float b2, float eps, float ibc1, float ibc2) {
+    const float gs[4] = {g.x, g.y, g.z, g.w};
+    float ps[4] = {p.x, p.y, p.z, p.w}, ms[4] = {m.x, m.y, m.z, m.w}, vs[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        ms[q] = fmaf(b1, ms[q], (1.f - b1) * gs[q]);
+        vs[q] = fmaf(b2, vs[q], (1.f - b2) * gs[q] * gs[q]);
+        ps[q] -= lr * (ms[q] * ibc1) / (sqrtf(vs[q] * ibc2) + eps);
+    }
+    p = make_float4(ps[0], ps[1], ps[2], ps[3]);
+    m = make_float4(ms[0], ms[1], ms[2], ms[3]);
+    v = make_float4(vs[0], vs[1], vs[2], vs[3]);
+}
+
+__global__ void k_adam(AdamChunk ch, float b1, float b2, float eps, float ibc1, float ibc2,
+                       const int *step_dev) {
+    if (step_dev) {  // t = completed steps + 1, read from the device (graph replays advance it)
+        // 1 - b^t = -expm1(t log1p(b - 1)): no cancellation when b^t is close to 1 (1 - b is
+        // exact in binary32 for b in [0.5, 1])
+        const float t = (float)(*step_dev + 1);
+        ibc1 = -1.0f / expm1f(t * log1pf(-(1.0f - b1)));
+        ibc2 = -1.0f / expm1f(t * log1pf(-(1.0f - b2)));
+    }
+    const AdamModel &M = ch.m[blockIdx.y];
+    const long long rows0 = kNch, rowsd = (long long)M.k * M.A;
+    const long long q4 = M.n_pad / 4;                  // float4s per row
+    const long long total = (rows0 + rowsd) * q4;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long row = e / q4;
+        if (row < rows0) {
+            if (!M.p0) continue;
+            float4 *p = reinterpret_cast<float4 *>(M.p0) + e;
+            float4 *m = reinterpret_cast<float4 *>(M.m0) + e;
+            float4 *v = reinterpret_cast<float4 *>(M.v0) + e;
+            const float4 g = reinterpret_cast<const float4 *>(M.g0)[e];
+            float4 pp = *p, mm = *m, vv = *v;
+            adam4(pp, g, mm, vv, M.lr0[row], b1, b2, eps, ibc1, ibc2);
+            *p = pp;
+            *m = mm;
+            *v = vv;
+        } else {
+            if (!M.pd) continue;
+            const long long ed = e - rows0 * q4;
+            const int a = (int)((row - rows0) % M.A);
+            float4 *p = reinterpret_cast<float4 *>(M.pd) + ed;
+            float4 *m = reinterpret_cast<float4 *>(M.md) + ed;
+            float4 *v = reinterpret_cast<float4 *>(M.vd) + ed;
+            const float4 g = reinterpret_cast<const float4 *>(M.gd)[ed];
+            float4 pp = *p, mm = *m, vv = *v;
+            adam4(pp, g, mm, vv, M.lrd[a], b1, b2, eps, ibc1, ibc2);
+            *p = pp;
+            *m = mm;
+            *v = vv;
+        }
+    }
+}
+
+__global__ void k_step_advance(int *step_dev) { *step_dev += 1; }
+
+}  // namespace
+
+cudaError_t launch_adam(const ModelInfo *models, int n_models, const rgba_adam_cfg &cfg,
+                        const rgba_adam_state *st, int step, int *step_dev, int sms, cudaStream_t s) {
+    const double bc1 = 1.0 - pow((double)cfg.beta1, step), bc2 = 1.0 - pow((double)cfg.beta2, step);
+    for (int m0 = 0; m0 < n_models; m0 += kAdamModels) {
+        const int nm = n_models - m0 < kAdamModels ? n_models - m0 : kAdamModels;
+        AdamChunk ch;
+        memset(&ch, 0, sizeof(ch));
+        for (int j = 0; j < nm; ++j) {
+            const ModelInfo &mi = models[m0 + j];
+            const rgba_adam_state &sj = st[m0 + j];
+            AdamModel &M = ch.m[j];
+            M.n_pad = mi.n_pad;
+            M.k = mi.k;
+            M.A = mi.A;
+            if (mi.gg0 && sj.m_g0 && sj.v_g0) {
+                M.p0 = const_cast<float *>(mi.g0);
+                M.g0 = mi.gg0;
+                M.m0 = sj.m_g0;
+                M.v0 = sj.v_g0;
+            }
+            if (mi.A > 0 && mi.gdg && sj.m_dg && sj.v_dg) {
+                M.pd = const_cast<float *>(mi.dg);
+                M.gd = mi.gdg;
+                M.md = sj.m_dg;
+                M.vd = sj.v_dg;
+            }
+            for (int c = 0; c < kNch; ++c) M.lr0[c] = cfg.lr[c];
+            for (int a = 0; a < mi.A; ++a) M.lrd[a] = cfg.lr_delta[mi.chans[a]];
+        }
+        dim3 grid(sms * 4, nm);
+        k_adam<<<grid, 256, 0, s>>>(ch, cfg.beta1, cfg.beta2, cfg.eps, (float)(1.0 / bc1),
+                                    (float)(1.0 / bc2), step_dev);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (step_dev) {
+        k_step_advance<<<1, 1, 0, s>>>(step_dev);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
+}  // namespace rgba

@@ -528,6 +528,29 @@ int rgba_render_bwd(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
     return do_render_bwd(ctx, k, dL_dimg, T_final, n_contrib);
 }
 
+int rgba_adam(rgba_ctx_t ctx, const rgba_batch *batch, const rgba_adam_cfg *cfg,
+              const rgba_adam_state *states, int step, int32_t *step_dev, void *stream) {
+    if (!ctx || !cfg || !states) return fail(RGBA_ERR_INVALID_ARG, "ctx/cfg/states is NULL");
+    if (!step_dev && step < 1) return fail(RGBA_ERR_INVALID_ARG, "Adam step count starts at 1");
+    if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps > 0.f))
+        return fail(RGBA_ERR_INVALID_ARG, "Adam betas must lie in [0, 1) and eps be positive");
+    Plan p;
+    int rc = make_plan(batch, p);
+    if (rc) return rc;
+    if (p.models.empty()) return RGBA_OK;
+    for (size_t m = 0; m < p.models.size(); ++m) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(states[m].m_g0) | reinterpret_cast<uintptr_t>(states[m].v_g0) |
+                            reinterpret_cast<uintptr_t>(states[m].m_dg) | reinterpret_cast<uintptr_t>(states[m].v_dg);
+        if (a & 15) return fail(RGBA_ERR_INVALID_ARG, "Adam moment buffers must be 16-byte aligned");
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    ctx->launches += ((int)p.models.size() + 15) / 16 + (step_dev ? 1 : 0);
+    e = launch_adam(p.models.data(), (int)p.models.size(), *cfg, states, step < 1 ? 1 : step, step_dev,
+                    ctx->sms, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "adam");
+}
+
 int rgba_step_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *target,
                     int loss_kind, float *img, void *stream) {
     Call k;

@@ -117,5 +117,7 @@ cudaError_t launch_render_bwd(const Ctx &c, int grid, int smem_batch, const floa
                               const float *T_final, const int *n_contrib, cudaStream_t s);
 cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_n, int max_k, cudaStream_t s);
 cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s);
+cudaError_t launch_adam(const ModelInfo *models, int n_models, const rgba_adam_cfg &cfg,
+                        const rgba_adam_state *st, int step, int *step_dev, int sms, cudaStream_t s);
 
 }  // namespace rgba
