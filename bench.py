@@ -468,13 +468,14 @@ def run_uneven(local_rank, steps=20):
     import torch
     from paper_2503_12886_gb300 import synth
     from paper_2503_12886_gb300.batching import GraphStep, autotune
+    from paper_2503_12886_gb300.optim import Adam
     from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
     batch = synth.workload_uneven()
     targets = synth.make_targets(batch, 4001)
     r = Renderer(local_rank)
     tune = autotune(r, batch, targets, steps=3)
     db = DeviceBatch(batch, f"cuda:{local_rank}", tile=tune.tile, smem_batch=tune.smem_batch)
-    gs = GraphStep(r, db, db.pack_images(targets))
+    gs = GraphStep(r, db, db.pack_images(targets), optimizer=Adam(r, db))
     for _ in range(3):
         gs.replay()
     torch.cuda.synchronize()
@@ -484,7 +485,7 @@ def run_uneven(local_rank, steps=20):
     t = time.perf_counter() - t0
     r.close()
     return {"workload": "8 avatars N 20k..100k, K 16/24/32, 64 frames at 256/512/1024 px, one "
-                        "batch per step (fwd+bwd, L1), CUDA-graph replay",
+                        "batch per step (fwd+bwd+Adam, L1), CUDA-graph replay",
             "img_per_s": len(batch.frames) * steps / t, "ms_per_step": 1e3 * t / steps,
             "pairs": pairs, "tuned": {"tile": list(tune.tile), "smem_batch": tune.smem_batch},
             "autotune_ms": tune.table}

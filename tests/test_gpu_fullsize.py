@@ -1,0 +1,121 @@
+"""Parity at the full workload sizes, in the launch configuration the bench times: all tile
+decisions and lists bit-exact, pixels and per-Gaussian 2-D gradients on sampled tile blocks
+(the oracle renders only those tiles), and sampled frames of the uneven 64-frame batch."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2503_12886_gb300 import api, synth
+from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
+
+from gpu_helpers import (GRAD_FLOOR, GRAD_RTOL, compare_decisions, compare_images,
+                         read_intermediates)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def renderer():
+    import __graft_entry__
+    __graft_entry__.build()
+    r = Renderer(0)
+    yield r
+    r.close()
+
+
+def _block_mask(fr, ores_f, TW, TH, size=4):
+    """A size x size block of tiles centred on the frame's densest tile."""
+    tx, ty = (fr.width + TW - 1) // TW, (fr.height + TH - 1) // TH
+    counts = np.diff(ores_f.tile_start).reshape(ty, tx)
+    cy, cx = np.unravel_index(np.argmax(counts), counts.shape)
+    y0, x0 = max(0, min(ty - size, cy - size // 2)), max(0, min(tx - size, cx - size // 2))
+    mask = np.zeros(ty * tx, np.uint8)
+    pix = np.zeros((fr.height, fr.width), bool)
+    for y in range(y0, y0 + size):
+        mask[y * tx + x0: y * tx + x0 + size] = 1
+    pix[y0 * TH:(y0 + size) * TH, x0 * TW:(x0 + size) * TW] = True
+    return mask, pix, (x0, y0, x0 + size, y0 + size)
+
+
+def test_batched_workload_full_size(renderer):
+    batch = synth.workload_batched()           # N=60,000, K=32, B=16, 512x512
+    db = DeviceBatch(batch, "cuda:0", tile=(16, 16), smem_batch=256)
+    img, T, n = renderer.forward(db)
+    torch.cuda.synchronize()
+    inter = read_intermediates(renderer, db)
+    ores = oracle.forward(batch, do_render=False)
+    st = compare_decisions(batch, ores, inter, db)
+    assert st["pairs"] > 3_000_000
+    # sampled tile blocks of three frames: pixels, then 2-D gradients of the Gaussians that lie
+    # entirely inside the block (so the oracle, rendering only the block, sees all of them)
+    rng = np.random.default_rng(0)
+    dl = torch.from_numpy(rng.standard_normal(3 * db.total_pix).astype(np.float32) * 1e-6).cuda()
+    renderer.backward(db, dl, T, n)
+    torch.cuda.synchronize()
+    g2_gpu = read_intermediates(renderer, db)["grad2d"]
+    dl_views = [v.cpu().numpy().astype(np.float64) for v in db.image_views(dl)]
+    checked = 0
+    for b in (0, 7, 15):
+        fr = batch.frames[b]
+        mask, pix, (x0, y0, x1, y1) = _block_mask(fr, ores[b], 16, 16)
+        sub = synth.Batch(batch.models, [fr], batch.psi[b:b + 1], batch.fparams[b:b + 1], batch.k_stride)
+        o = oracle.forward(sub, splat="spec", tile_masks={0: mask})
+        s = compare_images(sub, o, _view_batch(db, b), img, T, n, tiles_only=[pix])
+        assert s["max_err"] <= 1e-4 and s["n_mismatch"] == 0, s
+        # the block is the frame's densest (most evaluations per pixel, so more cutoff
+        # decisions near their threshold); whole frames stay under 0.1 % flagged
+        assert s["flagged"] <= 0.005 * s["pixels"]
+        g2 = oracle.render_bwd(fr.width, fr.height, 16, 16, o[0].rec, o[0].tile_start, o[0].lst,
+                               batch.fparams[b, 17:20].astype(np.float64), dl_views[b],
+                               batch.models[0].n, mask)
+        r = o[0].rect
+        inside = (r[:, 0] >= x0) & (r[:, 2] <= x1) & (r[:, 1] >= y0) & (r[:, 3] <= y1) & (r[:, 2] > r[:, 0])
+        idx = np.nonzero(inside)[0]
+        assert len(idx) > 100
+        got = g2_gpu[db.rec_offsets[b] + idx, :9].astype(np.float64)
+        ref = g2[idx]
+        scale = np.abs(ref).max(0, keepdims=True)
+        err = np.abs(got - ref) / (GRAD_RTOL * np.abs(ref) + GRAD_FLOOR * scale + 1e-30)
+        assert err.max() <= 1.0, (b, err.max())
+        checked += len(idx)
+    assert checked > 300
+
+
+class _view_batch:
+    """DeviceBatch-like view of one frame of a batch (for compare_images)."""
+
+    def __init__(self, db, b):
+        self.db, self.b = db, b
+
+    def image_views(self, flat):
+        return [self.db.image_views(flat)[self.b]]
+
+    def pix_views(self, flat):
+        return [self.db.pix_views(flat)[self.b]]
+
+
+def test_uneven_workload_sampled_frames(renderer):
+    batch = synth.workload_uneven()            # 8 avatars N 20k..100k, 64 frames 256/512/1024
+    db = DeviceBatch(batch, "cuda:0", tile=(16, 16), smem_batch=256, grads=False)
+    img, T, n = renderer.forward(db)
+    torch.cuda.synchronize()
+    inter = read_intermediates(renderer, db)
+    for b in (0, 9, 18, 21, 47, 63):          # 256, 512 and 1024 px frames, all 8 avatars
+        fr = batch.frames[b]
+        sub = synth.Batch(batch.models, [fr], batch.psi[b:b + 1], batch.fparams[b:b + 1],
+                          batch.k_stride)
+        o = oracle.forward(sub, do_render=False)
+        # decisions of frame b against the oracle (its records and lists inside the batch)
+        m = batch.models[fr.model]
+        rb = db.rec_offsets[b]
+        np.testing.assert_array_equal(inter["rects"][rb: rb + m.n].astype(np.int32), o[0].rect)
+        tb = sum(((f.width + 15) // 16) * ((f.height + 15) // 16) for f in batch.frames[:b])
+        nt = ((fr.width + 15) // 16) * ((fr.height + 15) // 16)
+        ts = inter["tile_start"][tb: tb + nt + 1].astype(np.int64)
+        np.testing.assert_array_equal(ts - ts[0], o[0].tile_start)
+        np.testing.assert_array_equal(inter["sorted"][ts[0]: ts[-1]].astype(np.int64), o[0].lst)
+        mask, pix, _ = _block_mask(fr, o[0], 16, 16, size=3)
+        o = oracle.forward(sub, splat="spec", tile_masks={0: mask})
+        s = compare_images(sub, o, _view_batch(db, b), img, T, n, tiles_only=[pix])
+        assert s["max_err"] <= 1e-4 and s["n_mismatch"] == 0, (b, s)
