@@ -150,6 +150,20 @@ def make_workload(seed_base=3000, variants=4):
     return out
 
 
+def max_over_ranks(x: float, device) -> float:
+    """Max of a per-rank float over the default process group (the slowest rank's time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, frames: int, steps: int, elapsed_max: float) -> float:
+    """Images per second of the whole job: every rank's frames over the slowest rank's time."""
+    return world * frames * steps / elapsed_max
+
+
 def cpu_baseline_sample(batch, targets):
     """The oracle, as it stands (single thread), on frame 0 of the workload: fwd + loss + bwd."""
     import oracle
@@ -287,10 +301,8 @@ def run_ours(args, rank, world, local_rank):
     ck = clocks.stop()
     elapsed = e0.elapsed_time(e1) / 1e3
     if world > 1:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = world * FRAMES * args.steps / elapsed
+        elapsed = max_over_ranks(elapsed, dev)
+    value = whole_job_rate(world, FRAMES, args.steps, elapsed)
     ms_per_step = 1e3 * elapsed / args.steps
     last_loss = float(host_cnt[(args.steps - 1) % len(graphs)][16:24].numpy().view(np.float64)[0])
 
