@@ -149,9 +149,9 @@ int make_plan(const rgba_batch *b, Plan &p) {
     L.models = take(sizeof(ModelInfo) * (size_t)M);
     L.frames = take(sizeof(FrameInfo) * (size_t)B);
     L.mframes = take(sizeof(int) * (size_t)B);
-    L.tile_count = take(8 * (size_t)T);
+    L.tile_count = take(4 * (size_t)T * (1 + kSubCounters));
     L.tile_start = take(4 * (size_t)(T + 1));
-    L.cursor = take(4 * (size_t)T);
+    L.cursor = take(4 * (size_t)T * kSubCounters);
     L.work = take(4 * (size_t)T);
     L.records = take(sizeof(float) * kRecFloats * (size_t)R);
     L.rects = take(8 * (size_t)R);
@@ -164,13 +164,15 @@ int make_plan(const rgba_batch *b, Plan &p) {
     L.pix_dl = take(12 * (size_t)P);
     L.pix_img = take(12 * (size_t)P);
     L.dpsi_part = take(4 * (size_t)dpsi);
-    L.keys = o;  // pair buffers follow: 8 + 4 bytes per pair
+    L.keys = o;  // pair buffers follow: 8 + 8 + 4 bytes per pair
     return RGBA_OK;
 }
 
 void finish_layout(Layout &L, long long cap) {
     L.cap = cap;
     size_t o = L.keys;
+    o = align256(o + 8 * (size_t)cap);
+    L.keys2 = o;
     o = align256(o + 8 * (size_t)cap);
     L.sorted = o;
     o = align256(o + 4 * (size_t)cap);
@@ -181,11 +183,11 @@ long long cap_for_bytes(const Layout &L, size_t bytes) {
     Layout t = L;
     finish_layout(t, 0);
     if (bytes < t.total) return -1;
-    long long c = (long long)((bytes - L.keys) / 12);
+    long long c = (long long)((bytes - L.keys) / 20);
     while (c > 0) {
         finish_layout(t, c);
         if (t.total <= bytes) break;
-        c -= (long long)((t.total - bytes + 11) / 12);
+        c -= (long long)((t.total - bytes + 19) / 20);
     }
     return c < 0 ? 0 : c;
 }
@@ -208,6 +210,7 @@ Ctx make_ctx(const Layout &L, unsigned char *ws, const rgba_batch *b) {
     c.cache = reinterpret_cast<float4 *>(ws + L.cache);
     c.grad2d = reinterpret_cast<float *>(ws + L.grad2d);
     c.keys = reinterpret_cast<unsigned long long *>(ws + L.keys);
+    c.keys2 = reinterpret_cast<unsigned long long *>(ws + L.keys2);
     c.sorted = reinterpret_cast<unsigned *>(ws + L.sorted);
     c.dpsi_part = reinterpret_cast<float *>(ws + L.dpsi_part);
     c.dgb = reinterpret_cast<float *>(ws + L.dgb);
@@ -303,7 +306,9 @@ int do_preprocess(rgba_ctx_t ctx, Call &k) {
     int rc;
     if ((rc = upload_tables(ctx, k))) return rc;
     if ((rc = memset_async(k.ws + k.p.L.counters, 256, k.s, "memset counters"))) return rc;
-    if ((rc = memset_async(k.ws + k.p.L.tile_count, 8 * (size_t)k.p.L.T, k.s, "memset tile counts"))) return rc;
+    if ((rc = memset_async(k.ws + k.p.L.tile_count, 4 * (size_t)k.p.L.T * (1 + kSubCounters), k.s,
+                           "memset tile counts")))
+        return rc;
     StageScope sc(ctx, ST_PRE, k.s, 1);
     int max_rows = 0;
     for (const ModelInfo &m : k.p.models) max_rows = std::max(max_rows, kNch + m.k * m.A);
@@ -315,7 +320,7 @@ int do_bin_sort(rgba_ctx_t ctx, Call &k) {
     cudaError_t e;
     int rc;
     {
-        StageScope sc(ctx, ST_SCAN, k.s, 1);
+        StageScope sc(ctx, ST_SCAN, k.s, 2);
         if ((e = launch_scan(k.c, k.s)) != cudaSuccess) return cuda_fail(e, "scan");
     }
     {

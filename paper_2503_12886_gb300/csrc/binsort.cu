@@ -6,15 +6,31 @@
 // give each Gaussian its slot in up to 8 tiles), one CTA scans them into list offsets and a
 // work list, a scatter kernel drops (depth << 32 | index) keys into their tile's segment (by
 // slot, or by a cursor atomic for larger rectangles), and one CTA per non-empty tile sorts its
-// shared memory (a stable LSD radix sort on the key compressed to (depth - segment minimum,
-// index); bitonic networks for segments beyond its capacity). Because the key carries the
-// index, the result is unique.
+// shared memory, or through L2 for long segments (a stable LSD radix sort on the key compressed
+// to (depth - segment minimum, index); a bitonic network when that key would need more than 64
+// bits). Because the key carries the index, the result is unique.
 #include "rgba_internal.cuh"
 
 namespace rgba {
 namespace {
 
 constexpr int kScanThreads = 1024;
+
+// Per tile (one thread each, coalesced): the total count into tile_start (the scan below turns
+// it into the list start) and, for the larger rectangles, each sub-counter's fill offset
+// relative to the tile's start (after the ranked slots).
+__global__ void k_tile_totals(Ctx c) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= c.T) return;
+    const unsigned *sub = c.tile_count + c.T + t * kSubCounters;
+    unsigned v = c.tile_count[t];
+#pragma unroll
+    for (int q = 0; q < kSubCounters; ++q) {
+        c.cursor[t * kSubCounters + q] = v;
+        v += sub[q];
+    }
+    c.tile_start[t] = v;
+}
 
 // Exclusive scan of the tile counts (frame-major), pair total and capacity check, and the work
 // list: non-empty tiles first, longest lists first (bucketed by floor(log2(length))), then the
@@ -33,7 +49,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Ctx c) {
     unsigned long long sum = 0;
     unsigned ne = 0;
     for (long long t = lo; t < hi; ++t) {
-        unsigned v = c.tile_count[t] + c.tile_count[T + t];
+        unsigned v = c.tile_start[t];  // the tile's total (k_tile_totals)
         sum += v;
         ne += v > 0;
         if (v > 0) atomicAdd(&s_hist[31 - __clz(v)], 1u);
@@ -65,10 +81,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Ctx c) {
     unsigned ne_run = s_ne[tid] - ne;
     unsigned e_run = (unsigned)lo - ne_run;  // empty tiles before lo
     for (long long t = lo; t < hi; ++t) {
-        unsigned v = c.tile_count[t] + c.tile_count[T + t];
+        const unsigned v = c.tile_start[t];
         unsigned st = run > 0xffffffffull ? 0xffffffffu : (unsigned)run;
         c.tile_start[t] = st;
-        c.cursor[t] = st + c.tile_count[t];  // large rectangles fill in after the ranked slots
         if (v > 0) c.work[atomicAdd(&s_hist[31 - __clz(v)], 1u)] = (unsigned)t;
         else c.work[n_ne + e_run++] = (unsigned)t;
         run += v;
@@ -109,10 +124,11 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(Ctx c) {
         }
         return;
     }
+    unsigned *cur = c.cursor + (r & (kSubCounters - 1));
     for (int ty = rc.y; ty < rc.w; ++ty)
         for (int tx = rc.x; tx < rc.z; ++tx) {
             const long long gt = f.tile_base + (long long)ty * f.tiles_x + tx;
-            const unsigned pos = atomicAdd(c.cursor + gt, 1u);
+            const unsigned pos = c.tile_start[gt] + atomicAdd(cur + gt * kSubCounters, 1u);
             c.keys[pos] = key;
         }
 }
@@ -255,7 +271,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
         const unsigned st = c.tile_start[t], L = c.tile_start[t + 1] - st;
         unsigned long long *g = c.keys + st;
         bool sorted = false;
-        if (L <= (unsigned)kRadixCap) {
+        {
             // compress the key to (depth - min depth) << index bits | index
             unsigned dmin = 0xffffffffu, dmax = 0u, imax = 0u;
             for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
@@ -280,12 +296,16 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
             const int ib = 32 - __clz(s_imax);            // bits of the largest index (0 if 0)
             const int db = 32 - __clz(s_dmax - d0);       // bits of the depth spread
             if (db + ib <= 64) {
+                // in shared memory when the segment fits, else in place in global memory (L2)
+                const bool in_smem = L <= (unsigned)kRadixCap;
+                unsigned long long *a = in_smem ? s_keys : c.keys2 + st;
+                unsigned long long *bb = in_smem ? s_keys + kRadixCap : g;
                 for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
                     const unsigned long long k = g[e];
-                    s_keys[e] = ((unsigned long long)((unsigned)(k >> 32) - d0) << ib) | (unsigned)k;
+                    a[e] = ((unsigned long long)((unsigned)(k >> 32) - d0) << ib) | (unsigned)k;
                 }
                 __syncthreads();
-                const unsigned long long *res = radix_sort(s_keys, s_keys + kRadixCap, (int)L, db + ib, s_cnt);
+                const unsigned long long *res = radix_sort(a, bb, (int)L, db + ib, s_cnt);
                 const unsigned long long imask = (1ull << ib) - 1ull;
                 for (unsigned e = threadIdx.x; e < L; e += blockDim.x)
                     c.sorted[st + e] = (unsigned)(res[e] & imask);
@@ -312,6 +332,9 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
 }  // namespace
 
 cudaError_t launch_scan(const Ctx &c, cudaStream_t s) {
+    k_tile_totals<<<(unsigned)((c.T + 255) / 256), 256, 0, s>>>(c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     k_scan<<<1, kScanThreads, 0, s>>>(c);
     return cudaGetLastError();
 }

@@ -207,10 +207,10 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const FrameInfo &
             uint4 *rp = reinterpret_cast<uint4 *>(c.ranks + r * kRankSlots);
             rp[0] = make_uint4(rk[0], rk[1], rk[2], rk[3]);
             rp[1] = make_uint4(rk[4], rk[5], rk[6], rk[7]);
-        } else {
-            unsigned *tb = c.tile_count + c.T + f.tile_base;
+        } else {  // spread over kSubCounters counters per tile, chosen by the Gaussian index
+            unsigned *tb = c.tile_count + c.T + (size_t)f.tile_base * kSubCounters + (r & (kSubCounters - 1));
             for (int ty = iy0; ty < iy1; ++ty)
-                for (int tx = ix0; tx < ix1; ++tx) atomicAdd(tb + ty * f.tiles_x + tx, 1u);
+                for (int tx = ix0; tx < ix1; ++tx) atomicAdd(tb + (size_t)(ty * f.tiles_x + tx) * kSubCounters, 1u);
         }
     } while (0);
     c.records[r * 3 + 0] = r0;

@@ -25,6 +25,7 @@ constexpr int kG2Floats = 12;    // 2-D gradient: du, dv, da, db, dc, dopacity, 
 constexpr int kTilePix = 256;    // pixels per screen tile (16x16 or 8x32)
 constexpr int kBwdChunk = 32;    // Gaussians per CTA in the fused preprocess/blend backward
 constexpr int kRankSlots = 8;    // tiles per Gaussian whose in-tile slot preprocess records
+constexpr int kSubCounters = 8;  // per-tile counters for larger rectangles (by Gaussian index)
 
 // Per-model table (device copy in the workspace).
 struct ModelInfo {
@@ -66,7 +67,7 @@ static_assert(sizeof(Counters) <= 256, "counters fit in one 256-byte block");
 struct Layout {
     size_t counters, models, frames, mframes, tile_count, tile_start, cursor, work;
     size_t records, rects, cache, grad2d, dgb, ranks, pix_T, pix_n, pix_dl, pix_img, dpsi_part;
-    size_t keys, sorted, total;
+    size_t keys, keys2, sorted, total;
     long long R, T, P;     // records, tiles, pixels
     long long dpsi_floats;
     long long cap;
@@ -83,15 +84,16 @@ struct Ctx {
     const float *fparams;
     float *grad_psi;
     Counters *cnt;
-    unsigned *tile_count;  // [2T]: Gaussians with at most kRankSlots tiles, then the others
+    unsigned *tile_count;  // [T] ranked (<= kRankSlots tiles), then [T][kSubCounters] the others
     unsigned *tile_start;
-    unsigned *cursor;
+    unsigned *cursor;      // [T][kSubCounters]: fill positions of the larger rectangles
     unsigned *work;
     float4 *records;   // [R][3]
     ushort4 *rects;    // [R]
     float4 *cache;     // [R][3]
     float *grad2d;     // [R][12]
     unsigned long long *keys;
+    unsigned long long *keys2;  // [cap]: second buffer of the global-memory radix passes
     unsigned *sorted;
     float *dpsi_part;
     float *dgb;        // [R][16]: dL/dG_b per (frame, Gaussian), 14 channels used

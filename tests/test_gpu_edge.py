@@ -132,4 +132,4 @@ def test_pair_overflow_reports_and_retries(renderer):
                              tg.data_ptr(), api.RGBA_LOSS_L1, None, s)
     assert rc == api.RGBA_OK and out2.pairs == out.pairs_needed
     ref = Renderer(0).step(DeviceBatch(batch, "cuda:0"), tg, api.RGBA_LOSS_L1)
-    assert abs(out2.loss - ref.loss) <= 1e-9 * ref.loss
+    assert abs(out2.loss - ref.loss) <= 1e-6 * ref.loss

@@ -134,7 +134,8 @@ def test_graph_replay_equals_eager(renderer):
     for _ in range(3):
         loss, pairs = gs.replay()
     assert pairs == out.pairs
-    assert abs(loss - out.loss) <= 1e-9 * abs(out.loss)
+    # the loss is a sum of per-CTA fp32 partials whose tile sets depend on scheduling
+    assert abs(loss - out.loss) <= 1e-6 * abs(out.loss)
     assert torch.equal(gs.img, img_e)
     n = batch.models[0].n
     assert grad_error(db.models[0].grad_g0.cpu().numpy()[:, :n], g_e.cpu().numpy()[:, :n]) <= 0.1
@@ -148,7 +149,7 @@ def test_graph_step_grows_workspace_on_overflow(renderer):
     gs = GraphStep(Renderer(0), db, tg, headroom=0.5)  # capture with too few pairs
     loss, pairs = gs.replay()
     ref = Renderer(0).step(DeviceBatch(batch, "cuda:0"), tg, api.RGBA_LOSS_L1)
-    assert pairs == ref.pairs and abs(loss - ref.loss) <= 1e-9 * ref.loss
+    assert pairs == ref.pairs and abs(loss - ref.loss) <= 1e-6 * ref.loss
 
 
 def test_autotune_returns_a_candidate(renderer, tmp_path):
