@@ -165,18 +165,6 @@ def whole_job_rate(world: int, frames: int, steps: int, elapsed_max: float) -> f
     return world * frames * steps / elapsed_max
 
 
-def reference_avatar(model, seed):
-    """The avatar the training step fits: the workload's avatar with its colours perturbed by
-    N(0, 0.1) and its means by N(0, 1 mm) (seeded)."""
-    import numpy as np
-    from paper_2503_12886_gb300 import synth
-    g0 = model.g0.copy()
-    n = model.n
-    g0[11:14, :n] += (0.1 * synth.Stream(seed, 40).normal(3 * n)).reshape(3, n).astype(np.float32)
-    g0[0:3, :n] += (1e-3 * synth.Stream(seed, 41).normal(3 * n)).reshape(3, n).astype(np.float32)
-    return synth.Model(n=model.n, k=model.k, mask=model.mask, g0=g0, dg=model.dg.copy())
-
-
 def cpu_baseline_sample(batch, targets):
     """The oracle, as it stands (single thread), on frame 0 of the workload: fwd + loss + bwd."""
     import oracle
@@ -254,7 +242,7 @@ def run_ours(args, rank, world, local_rank):
     dev = f"cuda:{local_rank}"
     work = make_workload(variants=args.variants)
     r = Renderer(local_rank)
-    ref = reference_avatar(work[0][0].models[0], 3999)
+    ref = synth.reference_avatar(work[0][0].models[0], 3999)
     dbs, tgs = [], []
     for j, (b, _) in enumerate(work):
         db = DeviceBatch(b, dev, models=dbs[0].models if dbs else None)
@@ -517,7 +505,7 @@ def run_uneven(local_rank, steps=20):
     batch = synth.workload_uneven()
     r = Renderer(local_rank)
     dev = f"cuda:{local_rank}"
-    refs = [reference_avatar(m, 4100 + a) for a, m in enumerate(batch.models)]
+    refs = [synth.reference_avatar(m, 4100 + a) for a, m in enumerate(batch.models)]
     rb = synth.Batch(refs, batch.frames, batch.psi, batch.fparams, batch.k_stride)
     timg, _, _ = r.forward(DeviceBatch(rb, dev, grads=False))
     dtmp = DeviceBatch(batch, dev, grads=False)

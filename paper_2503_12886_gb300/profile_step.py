@@ -1,11 +1,14 @@
 """Runs eager training steps of a named workload, for profilers (ncu) and quick timing.
 
     python -m paper_2503_12886_gb300.profile_step [--workload batched|single|uneven]
-        [--steps N] [--tile 16x16|8x32] [--smem-batch 64|128|256]
+        [--steps N] [--tile 16x16|8x32] [--smem-batch 64|128|256] [--train T]
 
-One sizing step (grows the workspace to the pair count), then N rgba_step calls, each one
-launch sequence of the whole hot path plus its single host synchronisation. Prints per-stage
-device times of the last step (CUDA events) as one JSON line.
+With --train T the avatar first fits images of its reference avatar (synth.reference_avatar)
+for T training steps with Adam, reaching the state a training benchmark times; the targets are
+then those images (else seeded U[0,1] images). One sizing step (grows the workspace to the pair
+count), then N rgba_step calls, each one launch sequence of the whole hot path plus its single
+host synchronisation. Prints per-stage device times of the last step (CUDA events) as one JSON
+line.
 """
 from __future__ import annotations
 
@@ -16,6 +19,7 @@ import time
 import torch
 
 from . import api, synth
+from .optim import Adam
 from .rasterizer import DeviceBatch, Renderer
 
 
@@ -35,12 +39,23 @@ def main():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--tile", default="16x16")
     p.add_argument("--smem-batch", type=int, default=256)
+    p.add_argument("--train", type=int, default=0)
     a = p.parse_args()
     tw, th = (int(x) for x in a.tile.split("x"))
     batch = make(a.workload)
     r = Renderer(0)
     db = DeviceBatch(batch, "cuda:0", tile=(tw, th), smem_batch=a.smem_batch)
-    tg = db.pack_images(synth.make_targets(batch, 5))
+    if a.train:
+        refs = [synth.reference_avatar(m, 3999 + j) for j, m in enumerate(batch.models)]
+        rb = synth.Batch(refs, batch.frames, batch.psi, batch.fparams, batch.k_stride)
+        tg, _, _ = r.forward(DeviceBatch(rb, "cuda:0", tile=(tw, th), grads=False))
+        tg = tg.clone()
+        opt = Adam(r, db)
+        for _ in range(a.train):
+            r.step(db, tg, api.RGBA_LOSS_L1)
+            opt.step()
+    else:
+        tg = db.pack_images(synth.make_targets(batch, 5))
     img = torch.empty(3 * db.total_pix, dtype=torch.float32, device="cuda:0")
     out = r.step(db, tg, api.RGBA_LOSS_L1, img)
     wall = []

@@ -234,6 +234,16 @@ def make_batch(models: list[Model], frames: list[Frame], seed: int, psi_sd: floa
     return Batch(models=models, frames=frames, psi=psi, fparams=fps, k_stride=ks)
 
 
+def reference_avatar(model: Model, seed: int) -> Model:
+    """The avatar a training benchmark fits: `model` with colours perturbed by N(0, 0.1) and
+    means by N(0, 1 mm) (its images are rendered and used as targets)."""
+    g0 = model.g0.copy()
+    n = model.n
+    g0[11:14, :n] += (0.1 * Stream(seed, 40).normal(3 * n)).reshape(3, n).astype(np.float32)
+    g0[0:3, :n] += (1e-3 * Stream(seed, 41).normal(3 * n)).reshape(3, n).astype(np.float32)
+    return Model(n=model.n, k=model.k, mask=model.mask, g0=g0, dg=model.dg.copy())
+
+
 def make_targets(batch: Batch, seed: int) -> list[np.ndarray]:
     """Seeded U[0,1] target images, one float32 [3][H][W] array per frame."""
     st = Stream(seed, 11)
