@@ -1,10 +1,11 @@
 // Front-to-back alpha compositing ("rasterize", RGBAvatar Sec. 3.2 on the 3DGS renderer) and
 // its exact reverse. One 256-thread CTA owns one screen tile (16x16 or 8x32 pixels) at a time;
 // persistent CTAs pull (frame, tile) items from the device work list, so every frame of every
-// avatar in the batch shares one launch. Each of the 128 threads owns two pixels of the tile
-// (rows y and y + TH/2), so every shared-memory read of a Gaussian and every warp reduction of
-// its gradient serves two pixels. Gaussians are staged in shared memory in rounds of BATCH
-// entries; a CTA stops as soon as every pixel of its tile is saturated.
+// avatar in the batch shares one launch. Gaussians are staged in shared memory in rounds of
+// BATCH entries, each with the box of its alpha >= 1/255 ellipse; every warp owns a compact
+// block of pixels (8 x 4 in the forward, 8 x 8 with two pixels per lane in the backward) and
+// skips, with one uniform test, the entries whose box misses its block. A CTA stops as soon as
+// every pixel of its tile is saturated.
 //
 // Per pixel, with d = pixel centre - mean:
 //   power = -(a dx^2 + c dy^2) / 2 - b dx dy  (skip if > 0)
@@ -39,12 +40,29 @@ __device__ __forceinline__ int find_frame(const Ctx &c, long long t) {
 // exponential and before the colour is read. Both kernels stage and evaluate through these
 // functions, so their decisions agree bit for bit.
 __device__ __forceinline__ void stage_splat(const float4 *rec, unsigned idx, float4 &sa, float2 &sq,
-                                            float4 &sc) {
+                                            float4 &sc, float4 &sb) {
     const float4 r0 = rec[(size_t)idx * 3 + 0], r1 = rec[(size_t)idx * 3 + 1];
     const float r2 = rec[(size_t)idx * 3 + 2].x;
     sa = make_float4(r0.x, r0.y, -0.5f * r0.z, -r0.w);
-    sq = make_float2(-0.5f * r1.x, -__logf(255.0f * r1.y));
+    const float tau = -__logf(255.0f * r1.y);
+    sq = make_float2(-0.5f * r1.x, tau);
     sc = make_float4(r1.y, r1.z, r1.w, r2);
+    // bounding box of the ellipse power >= tau, i.e. d^T conic d <= -2 tau: half-extents
+    // sqrt(-2 tau Sigma'_xx) and sqrt(-2 tau Sigma'_yy) with Sigma' = conic^-1, widened by 1 %
+    // + 0.05 px so that everything it excludes fails the per-pixel test with room to spare
+    const float det = r0.z * r1.x - r0.w * r0.w;
+    if (tau < 0.0f && det > 0.0f) {
+        const float s = -2.0f * tau / det;
+        const float hx = 1.01f * sqrtf(s * r1.x) + 0.05f, hy = 1.01f * sqrtf(s * r0.z) + 0.05f;
+        sb = make_float4(r0.x - hx, r0.x + hx, r0.y - hy, r0.y + hy);
+    } else {
+        sb = make_float4(1.0f, -1.0f, 1.0f, -1.0f);  // empty: the splat never reaches 1/255
+    }
+}
+
+// Whether a staged splat's box misses a block of pixel centres [x0, x1] x [y0, y1].
+__device__ __forceinline__ bool box_misses(const float4 &b, float x0, float x1, float y0, float y1) {
+    return b.y < x0 || b.x > x1 || b.w < y0 || b.z > y1;
 }
 
 // power = -(a dx^2 + c dy^2)/2 - b dx dy = dx ((-a/2) dx + (-b) dy) + (-c/2) dy dy
@@ -95,6 +113,7 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
     __shared__ float4 s_a[BATCH];
     __shared__ float2 s_q[BATCH];
     __shared__ float4 s_c[BATCH];
+    __shared__ float4 s_box[BATCH];
     __shared__ unsigned s_w;
     __shared__ float s_red[kTilePix / 32];
     if (c.cnt->overflow) return;
@@ -111,20 +130,26 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
         const FrameInfo &f = c.frames[b];
         const int lt = (int)(t - f.tile_base);
         const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
-        const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
+        // warp w owns an 8 x 4 block of the tile: column block w % (TW / 8), row block w / (TW / 8)
+        const int warp = tid >> 5, lane = tid & 31;
+        const int bx = tx * TW + (warp % (TW / 8)) * 8, by = ty * TH + (warp / (TW / 8)) * 4;
+        const int px = bx + (lane & 7), py = by + (lane >> 3);
+        const float bx0 = (float)bx + 0.5f, bx1 = (float)bx + 7.5f, by0 = (float)by + 0.5f, by1 = (float)by + 3.5f;
         PixF p{(float)px + 0.5f, (float)py + 0.5f, 1.f, 0.f, 0.f, 0.f, 0, px < f.W && py < f.H, false};
         p.done = !p.inside;
         const unsigned st = c.tile_start[t], en = c.tile_start[t + 1];
         const float4 *rec = c.records + (size_t)f.rec_base * 3;
         for (unsigned base = st; base < en; base += BATCH) {
             if (__syncthreads_count(p.done) == kTilePix) break;
-            if (tid < BATCH && base + tid < en) stage_splat(rec, c.sorted[base + tid], s_a[tid], s_q[tid], s_c[tid]);
+            if (tid < BATCH && base + tid < en)
+                stage_splat(rec, c.sorted[base + tid], s_a[tid], s_q[tid], s_c[tid], s_box[tid]);
             __syncthreads();
             const int cnt = min(BATCH, (int)(en - base));
             const int pos0 = (int)(base - st) + 1;
 #pragma unroll 4
             for (int j = 0; j < cnt; ++j) {
                 if (p.done) break;
+                if (box_misses(s_box[j], bx0, bx1, by0, by1)) continue;  // whole warp, uniform
                 composite(p, s_a, s_q, s_c, j, pos0 + j);
             }
         }
@@ -251,6 +276,7 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
     __shared__ float4 s_a[BATCH];
     __shared__ float2 s_q[BATCH];
     __shared__ float4 s_c[BATCH];
+    __shared__ float4 s_box[BATCH];
     __shared__ unsigned s_idx[BATCH];
     __shared__ float s_g[BATCH][9];  // per entry: stride 9 keeps lanes on distinct banks
     __shared__ unsigned s_w;
@@ -271,7 +297,12 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
         const FrameInfo &f = c.frames[b];
         const int lt = (int)(t - f.tile_base);
         const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
-        const int px = tx * TW + (tid % TW), py0 = ty * TH + (tid / TW);
+        // warp w owns an 8 x 8 block: column block w % (TW / 8), row block w / (TW / 8); each
+        // lane two pixels of the block, rows lane / 8 and lane / 8 + 4
+        const int warp = tid >> 5;
+        const int bx = tx * TW + (warp % (TW / 8)) * 8, by = ty * TH + (warp / (TW / 8)) * 8;
+        const int px = bx + (lane & 7), py0 = by + (lane >> 3);
+        const float bx0 = (float)bx + 0.5f, bx1 = (float)bx + 7.5f, by0 = (float)by + 0.5f, by1 = (float)by + 7.5f;
         const unsigned st = c.tile_start[t], list_len = c.tile_start[t + 1] - st;
         const float4 *rec = c.records + (size_t)f.rec_base * 3;
         float *g2 = c.grad2d + (size_t)f.rec_base * kG2Floats;
@@ -281,7 +312,7 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
         int m = 0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int py = py0 + h * (TH / 2);
+            const int py = py0 + h * 4;
             p[h] = PixB{(float)px + 0.5f, (float)py + 0.5f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
             if (px < f.W && py < f.H) {
                 const long long pix = (long long)py * f.W + px;
@@ -307,11 +338,12 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
             for (int e = tid; e < cnt; e += kThreads) {
                 const unsigned idx = c.sorted[st + begin + e];
                 s_idx[e] = idx;
-                stage_splat(rec, idx, s_a[e], s_q[e], s_c[e]);
+                stage_splat(rec, idx, s_a[e], s_q[e], s_c[e], s_box[e]);
             }
             for (int e = tid; e < 9 * BATCH; e += kThreads) (&s_g[0][0])[e] = 0.f;
             __syncthreads();
             for (int j = min(cnt, warp_last - begin) - 1; j >= 0; --j) {
+                if (box_misses(s_box[j], bx0, bx1, by0, by1)) continue;  // whole warp, uniform
                 const int pos = begin + j + 1;
                 const float4 A = s_a[j], Cc = s_c[j];
                 const float2 Q = s_q[j];
