@@ -251,8 +251,6 @@ int prologue(rgba_ctx_t ctx, const rgba_batch *b, void *ws, size_t ws_bytes, voi
     return RGBA_OK;
 }
 
-int grid_for(rgba_ctx_t ctx, int per_sm) { return ctx->sms * per_sm; }
-
 enum Stage { ST_UPLOAD, ST_PRE, ST_SCAN, ST_SCATTER, ST_SORT, ST_FWD, ST_BWD, ST_GBWD, ST_DPSI };
 
 // Brackets one stage with events when profiling is on; counts the kernels it launches.
@@ -329,7 +327,7 @@ int do_bin_sort(rgba_ctx_t ctx, Call &k) {
     }
     if ((rc = memset_async(&k.c.cnt->next_sort, 4, k.s, "memset sort counter"))) return rc;
     StageScope sc(ctx, ST_SORT, k.s, 1);
-    if ((e = launch_tile_sort(k.c, grid_for(ctx, 1), k.s)) != cudaSuccess) return cuda_fail(e, "tile sort");
+    if ((e = launch_tile_sort(k.c, ctx->sms, k.s)) != cudaSuccess) return cuda_fail(e, "tile sort");
     return RGBA_OK;
 }
 

@@ -135,51 +135,42 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(Ctx c) {
 
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kRadixCap = 8192;       // keys a segment may have for the shared-memory radix sort
-constexpr int kSortSmemKeys = 16384;  // bitonic fallback in shared memory up to this length
+constexpr int kRadixCap = 8192;                  // keys a segment may have for the shared-memory radix sort
+constexpr int kDigitParts = kSortThreads / 256;  // threads sharing one digit's column of warp counts
+static_assert(kSortThreads % 256 == 0 && 32 % kDigitParts == 0, "whole digits per warp");
 
-// Ascending bitonic network without direction flags (each merge opens with a mirrored compare),
-// over a virtual power-of-two length whose entries past L are +inf: a compare whose upper
-// index is >= L is skipped, so any L works and the padding never moves.
-__device__ void bitonic_sort(unsigned long long *k, int L) {
-    int N = 1;
-    while (N < L) N <<= 1;
-    for (int size = 2; size <= N; size <<= 1) {
-        for (int j = size >> 1; j > 0; j >>= 1) {
-            for (int p = threadIdx.x; p < (N >> 1); p += blockDim.x) {
-                int blk = p / j, off = p - blk * j, i, q;
-                if (j == (size >> 1)) {
-                    i = blk * size + off;
-                    q = blk * size + size - 1 - off;
-                } else {
-                    i = blk * 2 * j + off;
-                    q = i + j;
-                }
-                if (q < L) {
-                    unsigned long long a = k[i], bq = k[q];
-                    if (a > bq) {
-                        k[i] = bq;
-                        k[q] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
+// Lanes of `act` holding the same 8-bit digit as this lane: one ballot per digit bit (a warp
+// multi-split), all on the full-rate vote path.
+__device__ __forceinline__ unsigned digit_peers(unsigned act, unsigned d) {
+    unsigned m = act;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const unsigned bit = (d >> b) & 1u;
+        const unsigned v = __ballot_sync(act, bit);
+        m &= bit ? v : ~v;
     }
+    return m;
 }
 
-// Stable LSD radix sort of L keys in shared memory, 8-bit digits, `bits` significant bits.
-// Warp w owns the contiguous run [w S, (w+1) S) of the input; within a warp, rounds of 32 keys
-// go in order and lanes are ranked by lane index among equal digits (__match_any_sync), so the
-// order of equal digits is kept and the result after the last pass is fully sorted.
-// Returns the buffer holding the result (a or b).
+// Stable LSD radix sort of L keys, 8-bit digits, `bits` significant bits; a and b are both in
+// shared memory or both in global memory. Warp w owns the contiguous run [w S, (w+1) S) of the
+// input; within a warp, rounds of 32 keys go in order and lanes are ranked by lane index among
+// equal digits (digit_peers), so the order of equal digits is kept and the result after the
+// last pass is fully sorted. With kCacheRanks each key's rank within its warp's run of equal
+// digits is kept from the counting sweep (s_rank, L entries) and the scatter sweep only adds the
+// digit base; without it the scatter sweep ranks again. Returns the buffer holding the result.
+template <bool kCacheRanks>
 __device__ unsigned long long *radix_sort(unsigned long long *a, unsigned long long *b, int L,
-                                          int bits, unsigned *s_cnt /* [warps][256] */) {
+                                          int bits, unsigned *s_cnt /* [warps][256] + [warps] */,
+                                          unsigned short *s_rank) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int S = ((L + kSortWarps - 1) / kSortWarps + 31) & ~31;
     const int lo = warp * S, hi = min(L, lo + S);
     unsigned *cnt = s_cnt + warp * 256;
+    unsigned *wsum = s_cnt + kSortWarps * 256;
     const unsigned lt_mask = (1u << lane) - 1u;
+    // thread (digit d, part q) owns the counts of digit d in warps [q W/P, (q+1) W/P)
+    const int d_own = threadIdx.x / kDigitParts, w_own = (threadIdx.x % kDigitParts) * (kSortWarps / kDigitParts);
     for (int shift = 0; shift < bits; shift += 8) {
         for (int d = lane; d < 256; d += 32) cnt[d] = 0;
         __syncwarp();
@@ -187,61 +178,69 @@ __device__ unsigned long long *radix_sort(unsigned long long *a, unsigned long l
             const int e = base + lane;
             const bool ok = e < hi;
             const unsigned act = __ballot_sync(0xffffffffu, ok);
+            unsigned d = 0, peers = 0, before = 0;
             if (ok) {
-                const unsigned d = (unsigned)(a[e] >> shift) & 255u;
-                const unsigned peers = __match_any_sync(act, d);
-                if ((peers & lt_mask) == 0) cnt[d] += __popc(peers);
+                d = (unsigned)(a[e] >> shift) & 255u;
+                peers = digit_peers(act, d);
+                before = cnt[d];
+                if (kCacheRanks) s_rank[e] = (unsigned short)(before + __popc(peers & lt_mask));
             }
+            __syncwarp();
+            if (ok && (peers & lt_mask) == 0) cnt[d] = before + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
-        // bases in (digit, warp) order: digit totals scanned, then warps in order within a digit
-        if (threadIdx.x < 256) {
-            const int d = threadIdx.x;
+        // the scatter base of (digit d, warp w) is the count of all (digit, warp) pairs before it
+        // in digit-major order: an exclusive scan over the CTA's threads, which are ordered the
+        // same way, of each thread's sum over its warps, plus the running sum within them
+        {
             unsigned run = 0;
-            for (int w = 0; w < kSortWarps; ++w) {
-                const unsigned c = s_cnt[w * 256 + d];
-                s_cnt[w * 256 + d] = run;
+#pragma unroll
+            for (int w = w_own; w < w_own + kSortWarps / kDigitParts; ++w) {
+                const unsigned c = s_cnt[w * 256 + d_own];
+                s_cnt[w * 256 + d_own] = run;
                 run += c;
             }
-            s_cnt[kSortWarps * 256 + d] = run;  // digit total
+            unsigned x = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[warp] = x;
+            __syncthreads();
+            unsigned off = x - run;
+#pragma unroll
+            for (int q = 0; q < kSortWarps; ++q) off += q < warp ? wsum[q] : 0u;
+#pragma unroll
+            for (int w = w_own; w < w_own + kSortWarps / kDigitParts; ++w) s_cnt[w * 256 + d_own] += off;
         }
         __syncthreads();
-        if (threadIdx.x < 32) {  // exclusive scan of the 256 digit totals by one warp
-            unsigned *tot = s_cnt + kSortWarps * 256;
-            unsigned carry = 0;
-            for (int c0 = 0; c0 < 256; c0 += 32) {
-                const unsigned v = tot[c0 + lane];
-                unsigned x = v;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
+        if (kCacheRanks) {
+            for (int e = lo + lane; e < hi; e += 32) {
+                const unsigned long long k = a[e];
+                b[cnt[(unsigned)(k >> shift) & 255u] + s_rank[e]] = k;
+            }
+        } else {
+            for (int base = lo; base < hi; base += 32) {
+                const int e = base + lane;
+                const bool ok = e < hi;
+                const unsigned act = __ballot_sync(0xffffffffu, ok);
+                unsigned d = 0, peers = 0, pos = 0;
+                unsigned long long k = 0;
+                if (ok) {
+                    k = a[e];
+                    d = (unsigned)(k >> shift) & 255u;
+                    peers = digit_peers(act, d);
+                    pos = cnt[d] + __popc(peers & lt_mask);
                 }
-                tot[c0 + lane] = carry + x - v;
-                carry += __shfl_sync(0xffffffffu, x, 31);
+                __syncwarp();
+                if (ok) {
+                    b[pos] = k;
+                    if ((peers & lt_mask) == 0) cnt[d] += __popc(peers);
+                }
+                __syncwarp();
             }
-        }
-        __syncthreads();
-        for (int d = lane; d < 256; d += 32) cnt[d] += s_cnt[kSortWarps * 256 + d];
-        __syncwarp();
-        for (int base = lo; base < hi; base += 32) {
-            const int e = base + lane;
-            const bool ok = e < hi;
-            const unsigned act = __ballot_sync(0xffffffffu, ok);
-            unsigned d = 0, peers = 0, pos = 0;
-            unsigned long long k = 0;
-            if (ok) {
-                k = a[e];
-                d = (unsigned)(k >> shift) & 255u;
-                peers = __match_any_sync(act, d);
-                pos = cnt[d] + __popc(peers & lt_mask);
-            }
-            __syncwarp();
-            if (ok) {
-                b[pos] = k;
-                if ((peers & lt_mask) == 0) cnt[d] += __popc(peers);
-            }
-            __syncwarp();
         }
         __syncthreads();
         unsigned long long *t = a;
@@ -251,79 +250,74 @@ __device__ unsigned long long *radix_sort(unsigned long long *a, unsigned long l
     return a;
 }
 
+// Persistent: CTAs take (frame, tile) segments from the LPT-ordered work list. The key of a
+// segment is compressed to (depth - min depth) << index bits | index, at most 32 + 32 bits, and
+// radix-sorted on its significant bits (in shared memory up to kRadixCap keys, else in place in
+// global memory, mostly L2). The next work item is claimed while the current one is sorted.
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
-    extern __shared__ unsigned long long s_keys[];  // [kRadixCap] x 2 or [kSortSmemKeys]
-    unsigned *s_cnt = reinterpret_cast<unsigned *>(s_keys + 2 * kRadixCap);  // [warps + 1][256]
+    extern __shared__ unsigned long long s_keys[];  // [kRadixCap] x 2, counts, ranks
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(s_keys + 2 * kRadixCap);
+    unsigned short *s_rank = reinterpret_cast<unsigned short *>(s_cnt + kSortWarps * 256 + kSortWarps);
     __shared__ unsigned s_w, s_dmin, s_dmax, s_imax;
     if (c.cnt->overflow) return;
     const unsigned n_work = c.cnt->n_work;
+    if (threadIdx.x == 0) {
+        s_w = atomicAdd(&c.cnt->next_sort, 1u);
+        s_dmin = 0xffffffffu;
+        s_dmax = 0u;
+        s_imax = 0u;
+    }
+    __syncthreads();
     while (true) {
+        const unsigned w = s_w;
+        if (w >= n_work) break;
+        unsigned nxt = 0;
+        if (threadIdx.x == 0) nxt = atomicAdd(&c.cnt->next_sort, 1u);
+        const unsigned t = c.work[w];
+        const unsigned st = c.tile_start[t], L = c.tile_start[t + 1] - st;
+        const unsigned long long *g = c.keys + st;
+        unsigned dmin = 0xffffffffu, dmax = 0u, imax = 0u;
+        for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
+            const unsigned long long k = g[e];
+            const unsigned d = (unsigned)(k >> 32), i = (unsigned)k;
+            dmin = min(dmin, d);
+            dmax = max(dmax, d);
+            imax = max(imax, i);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+            dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+            imax = max(imax, __shfl_xor_sync(0xffffffffu, imax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&s_dmin, dmin);
+            atomicMax(&s_dmax, dmax);
+            atomicMax(&s_imax, imax);
+        }
+        __syncthreads();
+        const unsigned d0 = s_dmin;
+        const int ib = 32 - __clz(s_imax);       // bits of the largest index (0 if 0)
+        const int db = 32 - __clz(s_dmax - d0);  // bits of the depth spread
+        const bool in_smem = L <= (unsigned)kRadixCap;
+        unsigned long long *a = in_smem ? s_keys : c.keys2 + st;
+        unsigned long long *bb = in_smem ? s_keys + kRadixCap : c.keys + st;
+        for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
+            const unsigned long long k = g[e];
+            a[e] = ((unsigned long long)((unsigned)(k >> 32) - d0) << ib) | (unsigned)k;
+        }
+        __syncthreads();
+        const unsigned long long *res =
+            in_smem ? radix_sort<true>(a, bb, (int)L, db + ib, s_cnt, s_rank)
+                    : radix_sort<false>(a, bb, (int)L, db + ib, s_cnt, nullptr);
+        const unsigned long long imask = (1ull << ib) - 1ull;
+        for (unsigned e = threadIdx.x; e < L; e += blockDim.x)
+            c.sorted[st + e] = (unsigned)(res[e] & imask);
+        __syncthreads();
         if (threadIdx.x == 0) {
-            s_w = atomicAdd(&c.cnt->next_sort, 1u);
+            s_w = nxt;
             s_dmin = 0xffffffffu;
             s_dmax = 0u;
             s_imax = 0u;
-        }
-        __syncthreads();
-        const unsigned w = s_w;
-        if (w >= n_work) break;
-        const unsigned t = c.work[w];
-        const unsigned st = c.tile_start[t], L = c.tile_start[t + 1] - st;
-        unsigned long long *g = c.keys + st;
-        bool sorted = false;
-        {
-            // compress the key to (depth - min depth) << index bits | index
-            unsigned dmin = 0xffffffffu, dmax = 0u, imax = 0u;
-            for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
-                const unsigned long long k = g[e];
-                const unsigned d = (unsigned)(k >> 32), i = (unsigned)k;
-                dmin = min(dmin, d);
-                dmax = max(dmax, d);
-                imax = max(imax, i);
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
-                dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-                imax = max(imax, __shfl_xor_sync(0xffffffffu, imax, o));
-            }
-            if ((threadIdx.x & 31) == 0) {
-                atomicMin(&s_dmin, dmin);
-                atomicMax(&s_dmax, dmax);
-                atomicMax(&s_imax, imax);
-            }
-            __syncthreads();
-            const unsigned d0 = s_dmin;
-            const int ib = 32 - __clz(s_imax);            // bits of the largest index (0 if 0)
-            const int db = 32 - __clz(s_dmax - d0);       // bits of the depth spread
-            if (db + ib <= 64) {
-                // in shared memory when the segment fits, else in place in global memory (L2)
-                const bool in_smem = L <= (unsigned)kRadixCap;
-                unsigned long long *a = in_smem ? s_keys : c.keys2 + st;
-                unsigned long long *bb = in_smem ? s_keys + kRadixCap : g;
-                for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
-                    const unsigned long long k = g[e];
-                    a[e] = ((unsigned long long)((unsigned)(k >> 32) - d0) << ib) | (unsigned)k;
-                }
-                __syncthreads();
-                const unsigned long long *res = radix_sort(a, bb, (int)L, db + ib, s_cnt);
-                const unsigned long long imask = (1ull << ib) - 1ull;
-                for (unsigned e = threadIdx.x; e < L; e += blockDim.x)
-                    c.sorted[st + e] = (unsigned)(res[e] & imask);
-                sorted = true;
-            }
-        }
-        if (sorted) {
-        } else if (L <= (unsigned)kSortSmemKeys) {
-            for (unsigned e = threadIdx.x; e < L; e += blockDim.x) s_keys[e] = g[e];
-            __syncthreads();
-            bitonic_sort(s_keys, (int)L);
-            for (unsigned e = threadIdx.x; e < L; e += blockDim.x)
-                c.sorted[st + e] = (unsigned)(s_keys[e] & 0xffffffffull);
-        } else {
-            // oversized list: the same network in place in global memory
-            bitonic_sort(g, (int)L);
-            for (unsigned e = threadIdx.x; e < L; e += blockDim.x)
-                c.sorted[st + e] = (unsigned)(g[e] & 0xffffffffull);
         }
         __syncthreads();
     }
@@ -346,19 +340,22 @@ cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_sort(const Ctx &c, int grid, cudaStream_t s) {
-    static int attr_device = -1;
-    const int smem = 2 * kRadixCap * (int)sizeof(unsigned long long) + (kSortWarps + 1) * 256 * 4;
-    static_assert(2 * kRadixCap >= kSortSmemKeys, "bitonic fallback fits the radix buffers");
+cudaError_t launch_tile_sort(const Ctx &c, int sms, cudaStream_t s) {
+    static int attr_device = -1, per_sm = 1;
+    const int smem = 2 * kRadixCap * (int)sizeof(unsigned long long) + (kSortWarps * 256 + kSortWarps) * 4 +
+                     kRadixCap * (int)sizeof(unsigned short);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (attr_device != dev) {
         e = cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_sort, kSortThreads, smem);
+        if (e != cudaSuccess) return e;
+        per_sm = per_sm < 1 ? 1 : per_sm;
         attr_device = dev;
     }
-    k_tile_sort<<<grid, kSortThreads, smem, s>>>(c);
+    k_tile_sort<<<sms * per_sm, kSortThreads, smem, s>>>(c);
     return cudaGetLastError();
 }
 

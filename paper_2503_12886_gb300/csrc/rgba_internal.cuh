@@ -111,7 +111,7 @@ cudaError_t launch_preprocess(const Ctx &c, int max_n, int max_k, int max_rows, 
 cudaError_t launch_blend(const Ctx &c, int max_n, float *out, cudaStream_t s);
 cudaError_t launch_scan(const Ctx &c, cudaStream_t s);
 cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s);
-cudaError_t launch_tile_sort(const Ctx &c, int grid, cudaStream_t s);
+cudaError_t launch_tile_sort(const Ctx &c, int sms, cudaStream_t s);
 cudaError_t launch_render_fwd(const Ctx &c, int grid, int smem_batch, float *img, float *T_final,
                               int *n_contrib, const float *target, int loss_kind,
                               float *dl_dimg, const long long *pix_base_dummy, cudaStream_t s);
