@@ -152,7 +152,7 @@ __device__ __forceinline__ unsigned digit_peers(unsigned act, unsigned d) {
     return m;
 }
 
-// Stable LSD radix sort of L keys, 8-bit digits, `bits` significant bits; a and b are both in
+// Stable LSD radix sort of L keys on the bits [shift0, shift_end), 8-bit digits; a and b are both in
 // shared memory or both in global memory. Warp w owns the contiguous run [w S, (w+1) S) of the
 // input; within a warp, rounds of 32 keys go in order and lanes are ranked by lane index among
 // equal digits (digit_peers), so the order of equal digits is kept and the result after the
@@ -161,7 +161,8 @@ __device__ __forceinline__ unsigned digit_peers(unsigned act, unsigned d) {
 // digit base; without it the scatter sweep ranks again. Returns the buffer holding the result.
 template <bool kCacheRanks>
 __device__ unsigned long long *radix_sort(unsigned long long *a, unsigned long long *b, int L,
-                                          int bits, unsigned *s_cnt /* [warps][256] + [warps] */,
+                                          int shift0, int shift_end,
+                                          unsigned *s_cnt /* [warps][256] + [warps] */,
                                           unsigned short *s_rank) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int S = ((L + kSortWarps - 1) / kSortWarps + 31) & ~31;
@@ -171,7 +172,7 @@ __device__ unsigned long long *radix_sort(unsigned long long *a, unsigned long l
     const unsigned lt_mask = (1u << lane) - 1u;
     // thread (digit d, part q) owns the counts of digit d in warps [q W/P, (q+1) W/P)
     const int d_own = threadIdx.x / kDigitParts, w_own = (threadIdx.x % kDigitParts) * (kSortWarps / kDigitParts);
-    for (int shift = 0; shift < bits; shift += 8) {
+    for (int shift = shift0; shift < shift_end; shift += 8) {
         for (int d = lane; d < 256; d += 32) cnt[d] = 0;
         __syncwarp();
         for (int base = lo; base < hi; base += 32) {
@@ -250,15 +251,20 @@ __device__ unsigned long long *radix_sort(unsigned long long *a, unsigned long l
     return a;
 }
 
-// Persistent: CTAs take (frame, tile) segments from the LPT-ordered work list. The key of a
-// segment is compressed to (depth - min depth) << index bits | index, at most 32 + 32 bits, and
-// radix-sorted on its significant bits (in shared memory up to kRadixCap keys, else in place in
-// global memory, mostly L2). The next work item is claimed while the current one is sorted.
+constexpr int kTieRun = 32;  // longest run of equal depths the tie pass orders by itself
+
+// Persistent: CTAs take (frame, tile) segments from the LPT-ordered work list. A key is
+// (depth, Gaussian index); it is compressed to (depth - min depth) << 32 | index and
+// radix-sorted on the depth bits only (in shared memory up to kRadixCap keys, else in place in
+// global memory, mostly L2), which leaves runs of equal depth in list order. A tie pass then
+// orders each such run by index (insertion sort by the run's first thread); if any run is
+// longer than kTieRun the segment is instead sorted again on the index bits and then on the
+// depth bits, the full key. The next work item is claimed while the current one is sorted.
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
     extern __shared__ unsigned long long s_keys[];  // [kRadixCap] x 2, counts, ranks
     unsigned *s_cnt = reinterpret_cast<unsigned *>(s_keys + 2 * kRadixCap);
     unsigned short *s_rank = reinterpret_cast<unsigned short *>(s_cnt + kSortWarps * 256 + kSortWarps);
-    __shared__ unsigned s_w, s_dmin, s_dmax, s_imax;
+    __shared__ unsigned s_w, s_dmin, s_dmax, s_imax, s_long;
     if (c.cnt->overflow) return;
     const unsigned n_work = c.cnt->n_work;
     if (threadIdx.x == 0) {
@@ -266,6 +272,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
         s_dmin = 0xffffffffu;
         s_dmax = 0u;
         s_imax = 0u;
+        s_long = 0u;
     }
     __syncthreads();
     while (true) {
@@ -303,21 +310,48 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
         unsigned long long *bb = in_smem ? s_keys + kRadixCap : c.keys + st;
         for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
             const unsigned long long k = g[e];
-            a[e] = ((unsigned long long)((unsigned)(k >> 32) - d0) << ib) | (unsigned)k;
+            a[e] = ((unsigned long long)((unsigned)(k >> 32) - d0) << 32) | (unsigned)k;
         }
         __syncthreads();
-        const unsigned long long *res =
-            in_smem ? radix_sort<true>(a, bb, (int)L, db + ib, s_cnt, s_rank)
-                    : radix_sort<false>(a, bb, (int)L, db + ib, s_cnt, nullptr);
-        const unsigned long long imask = (1ull << ib) - 1ull;
-        for (unsigned e = threadIdx.x; e < L; e += blockDim.x)
-            c.sorted[st + e] = (unsigned)(res[e] & imask);
+        unsigned long long *res =
+            in_smem ? radix_sort<true>(a, bb, (int)L, 32, 32 + db, s_cnt, s_rank)
+                    : radix_sort<false>(a, bb, (int)L, 32, 32 + db, s_cnt, nullptr);
+        // ties: a run keeps its depth under any reordering, so run starts found by other
+        // threads do not change while a run is being ordered
+        for (unsigned e = threadIdx.x; e + 1 < L; e += blockDim.x) {
+            const unsigned dep = (unsigned)(res[e] >> 32);
+            if ((unsigned)(res[e + 1] >> 32) != dep || (e > 0 && (unsigned)(res[e - 1] >> 32) == dep))
+                continue;
+            unsigned end = e + 2;
+            while (end < L && end - e <= (unsigned)kTieRun && (unsigned)(res[end] >> 32) == dep) ++end;
+            if (end - e > (unsigned)kTieRun) {
+                s_long = 1u;
+                continue;
+            }
+            for (unsigned i = e + 1; i < end; ++i) {
+                const unsigned long long k = res[i];
+                unsigned j = i;
+                for (; j > e && res[j - 1] > k; --j) res[j] = res[j - 1];
+                res[j] = k;
+            }
+        }
+        __syncthreads();
+        if (s_long) {
+            unsigned long long *other = res == a ? bb : a;
+            res = in_smem ? radix_sort<true>(res, other, (int)L, 0, ib, s_cnt, s_rank)
+                          : radix_sort<false>(res, other, (int)L, 0, ib, s_cnt, nullptr);
+            other = res == a ? bb : a;
+            res = in_smem ? radix_sort<true>(res, other, (int)L, 32, 32 + db, s_cnt, s_rank)
+                          : radix_sort<false>(res, other, (int)L, 32, 32 + db, s_cnt, nullptr);
+        }
+        for (unsigned e = threadIdx.x; e < L; e += blockDim.x) c.sorted[st + e] = (unsigned)res[e];
         __syncthreads();
         if (threadIdx.x == 0) {
             s_w = nxt;
             s_dmin = 0xffffffffu;
             s_dmax = 0u;
             s_imax = 0u;
+            s_long = 0u;
         }
         __syncthreads();
     }

@@ -4,6 +4,7 @@ Bars: bit-exact tile rectangles, fp32 splat values, tile offsets and per-tile so
 pixels within 1e-4 (pixels the oracle flags as ambiguous at a cutoff are counted and bounded
 separately); gradients within 1e-3 relative with a per-channel floor (gpu_helpers.grad_error).
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -46,6 +47,29 @@ def uneven_batch():
     return synth.make_batch(models, fr, seed=4000, jitter_deg=20, random_bg=True)
 
 
+def ties_batch():
+    """Exact depth ties: the means of avatar 0 repeat in groups of 20 and those of avatar 1 in
+    groups of 125 (no mean deltas, so blended means and depths stay equal): runs of equal depth
+    in a tile list that the tie pass orders by itself, and runs longer than it orders, which
+    take the full-key sort."""
+    models = []
+    for a, grp in enumerate((20, 125)):
+        m = synth.make_model(91 + a, 2000, 4, sd_dmean=0.0, log_scale_mu=math.log(5e-3))
+        g0 = m.g0.copy()
+        for s in range(0, m.n, grp):
+            g0[0:3, s:s + grp] = g0[0:3, s:s + 1]
+        models.append(dataclasses.replace(m, g0=g0))
+    return synth.make_batch(models, [synth.Frame(0, 96, 80), synth.Frame(1, 96, 80)], seed=91,
+                            jitter_deg=10, random_bg=True)
+
+
+def dense_batch():
+    """16,000 Gaussians within 4 px of one tile corner: lists of up to ~15,000 keys, longer
+    than a shared-memory sort holds, with natural depth ties."""
+    m = synth.make_model(93, 16_000, 4, radii=(0.05, 0.05, 0.05), log_scale_mu=math.log(6e-3))
+    return synth.make_batch([m], [synth.Frame(0, 64, 64)], seed=93)
+
+
 CASES = {
     "single_128": (lambda: synth.workload_single(), (16, 16), 256),
     "gradcheck_64": (lambda: synth.workload_gradcheck(), (16, 16), 256),
@@ -53,6 +77,8 @@ CASES = {
     "batched_reduced": (lambda: synth.workload_batched(n=20_000, k=32, frames=4, res=256), (16, 16), 256),
     "ragged_8x32": (ragged_batch, (8, 32), 64),
     "uneven": (uneven_batch, (16, 16), 128),
+    "depth_ties": (ties_batch, (16, 16), 256),
+    "dense_lists": (dense_batch, (16, 16), 256),
 }
 
 
