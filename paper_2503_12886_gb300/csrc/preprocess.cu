@@ -75,11 +75,22 @@ __device__ __forceinline__ void blend14(const ModelInfo &m, const float *__restr
     }
 }
 
-// The FP32 decision spec for one (frame, Gaussian) from its blended channels v: view transform,
-// activations, EWA covariance, conic, radius, tile rectangle, depth. Writes the render record,
-// the rectangle and the backward cache, and counts the Gaussian in every tile it touches.
-__device__ __forceinline__ void decide_and_write(const Ctx &c, const FrameInfo &f, const float *V,
-                                                 const float v[kNch], long long r) {
+// What the decision spec needs of a frame, staged in shared memory once per round. limx/limy
+// are the Jacobian clamp bounds 1.3 tan(fov/2), computed by the same operation sequence the
+// per-Gaussian spec would use, so staging them changes no bit.
+struct FrameConst {
+    float limx, limy;
+    int tiles_x, tiles_y, tile_base, rec_base, pad_[2];
+};
+
+__device__ __forceinline__ float sigmoid_spec(float x) { return fdiv(1.0f, fadd(1.0f, exp_spec(-x))); }
+
+// The FP32 decision spec for one (frame, Gaussian) from its blended channels v and activated
+// opacity op: view transform, activations, EWA covariance, conic, radius, tile rectangle, depth.
+// Writes the render record, the rectangle and the backward cache, and counts the Gaussian in
+// every tile it touches.
+__device__ __forceinline__ void decide_and_write(const Ctx &c, const FrameConst &f, const float *V,
+                                                 const float v[kNch], float op, long long r) {
     c.cache[r * 3 + 0] = make_float4(v[0], v[1], v[2], v[3]);
     c.cache[r * 3 + 1] = make_float4(v[4], v[5], v[6], v[7]);
     c.cache[r * 3 + 2] = make_float4(v[8], v[9], 0.f, 0.f);
@@ -141,8 +152,7 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const FrameInfo &
                 Cm[ii][jj] = ffma(Tm[ii][2], V[4 * jj + 2], ffma(Tm[ii][1], V[4 * jj + 1], fmul(Tm[ii][0], V[4 * jj + 0])));
         // EWA Jacobian with the 1.3 x half-fov ratio clamp
         const float fx = V[12], fy = V[13];
-        float limx = fmul(1.3f, fdiv(fmul(0.5f, (float)f.W), fx));
-        float limy = fmul(1.3f, fdiv(fmul(0.5f, (float)f.H), fy));
+        const float limx = f.limx, limy = f.limy;
         float rx = fdiv(p[0], p[2]), ry = fdiv(p[1], p[2]);
         rx = fminf(limx, fmaxf(-limx, rx));
         ry = fminf(limy, fmaxf(-limy, ry));
@@ -185,7 +195,6 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const FrameInfo &
         if (x0 != x0 || y0 != y0 || x1 != x1 || y1 != y1) break;
         int ix0 = (int)x0, ix1 = (int)x1, iy0 = (int)y0, iy1 = (int)y1;
         if ((ix1 - ix0) * (iy1 - iy0) <= 0) break;
-        float op = fdiv(1.0f, fadd(1.0f, exp_spec(-v[10])));
         r0 = make_float4(u, vv, ca, cb);
         r1 = make_float4(cc, op, v[11], v[12]);
         r2 = make_float4(v[13], p[2], 0.f, 0.f);
@@ -220,9 +229,9 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const FrameInfo &
 }
 
 constexpr int kPreThreads = 128;  // standalone blend
-constexpr int kPreG = 64;         // Gaussians per CTA
-constexpr int kPreSlots = 4;      // frame slots per Gaussian
-constexpr int kPreFB = 4;         // frames per thread per round (register block)
+constexpr int kPreG = 32;         // Gaussians per CTA
+constexpr int kPreSlots = 8;      // frame slots per Gaussian
+constexpr int kPreFB = 2;         // frames per thread per round (register block)
 constexpr int kPreRound = kPreSlots * kPreFB;
 constexpr int kPreBlock = kPreG * kPreSlots;
 
@@ -250,18 +259,21 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned phas
     return false;
 }
 
-// One CTA = 64 Gaussians of one model and every frame that renders it. The model's G0 rows and
-// blendshape rows for the chunk arrive once in shared memory by bulk async copies; each thread
-// then blends its Gaussian for 4 frames at a time from shared memory (each blendshape value read
-// once per 4 frames) and runs the decision spec per frame.
-__global__ void __launch_bounds__(kPreBlock, 2)
+// One CTA = kPreG (32) Gaussians of one model and every frame that renders it. The model's G0
+// rows and blendshape rows for the chunk arrive once in shared memory by bulk async copies
+// (39 KB at K = 32 with 9 blended channels, so several CTAs share an SM); its kPreSlots (8)
+// thread slots per Gaussian then each blend kPreFB (2) frames at a time from shared memory
+// (each blendshape value read once per 2 frames) and run the decision spec per frame.
+__global__ void __launch_bounds__(kPreBlock, 3)
 k_preprocess(Ctx c, int max_k) {
     extern __shared__ float4 smem4[];
     __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ FrameConst s_fc[kPreRound];
     const ModelInfo &m = c.models[blockIdx.y];
     const int i0 = blockIdx.x * kPreG;
     if (i0 >= m.n || m.nb == 0) return;
     const int K = m.k, A = m.A, rows = kNch + K * A;
+    const unsigned mask = m.mask;
     float *s_rows = reinterpret_cast<float *>(smem4);      // [rows][64]: G0 then blendshapes
     float *s_psi = s_rows + (size_t)rows * kPreG;          // [16][max_k]
     float *s_fp = s_psi + kPreRound * max_k;               // [16][20]
@@ -293,6 +305,9 @@ k_preprocess(Ctx c, int max_k) {
     const int g = tid % kPreG, slot = tid / kPreG;
     const int i = i0 + g;
     const bool valid = i < m.n;
+    // opacity is the same for every frame unless it is blended
+    const bool op_blended = (mask >> 10) & 1u;
+    const float op0 = sigmoid_spec(s_rows[10 * kPreG + g]);
     for (int round = 0; round < m.nb; round += kPreRound) {
         const int nr = min(kPreRound, m.nb - round);
         for (int e = tid; e < nr * K; e += kPreBlock) {
@@ -305,34 +320,60 @@ k_preprocess(Ctx c, int max_k) {
             const int b = c.mframes[m.frame_off + round + fl];
             s_fp[e] = c.fparams[(size_t)b * RGBA_FP_STRIDE + q];
         }
+        if (tid < nr) {
+            const int b = c.mframes[m.frame_off + round + tid];
+            const FrameInfo &f = c.frames[b];
+            const float *fp = c.fparams + (size_t)b * RGBA_FP_STRIDE;
+            FrameConst fc;
+            fc.limx = fmul(1.3f, fdiv(fmul(0.5f, (float)f.W), fp[12]));
+            fc.limy = fmul(1.3f, fdiv(fmul(0.5f, (float)f.H), fp[13]));
+            fc.tiles_x = f.tiles_x;
+            fc.tiles_y = f.tiles_y;
+            fc.tile_base = f.tile_base;
+            fc.rec_base = f.rec_base;
+            fc.pad_[0] = fc.pad_[1] = 0;
+            s_fc[tid] = fc;
+        }
         __syncthreads();
         const int f0 = slot * kPreFB;
         if (valid && f0 < nr) {
+            // Eq. 1 for kPreFB frames: v = g0, then v = fma(psi_k, dG_k, v) for k ascending in
+            // every blended channel (the order of the loops over k and channels is free)
             float v[kPreFB][kNch];
-            int a = 0;
 #pragma unroll
             for (int ch = 0; ch < kNch; ++ch) {
                 const float x = s_rows[ch * kPreG + g];
 #pragma unroll
                 for (int q = 0; q < kPreFB; ++q) v[q][ch] = x;
-                if ((m.mask >> ch) & 1u) {
-                    const float *d = s_rows + (size_t)(kNch + a) * kPreG + g;
-                    for (int kk = 0; kk < K; ++kk) {
-                        const float dv = d[(size_t)kk * A * kPreG];
+            }
+            for (int kk = 0; kk < K; ++kk) {
+                float ps[kPreFB];
 #pragma unroll
-                        for (int q = 0; q < kPreFB; ++q)
-                            v[q][ch] = __fmaf_rn(s_psi[(f0 + q) * max_k + kk], dv, v[q][ch]);
+                for (int q = 0; q < kPreFB; ++q) ps[q] = s_psi[(f0 + q) * max_k + kk];
+                const float *d = s_rows + (size_t)(kNch + kk * A) * kPreG + g;
+                int a = 0;
+#pragma unroll
+                for (int ch = 0; ch < kNch; ++ch) {
+                    if ((mask >> ch) & 1u) {
+                        const float dv = d[a * kPreG];
+#pragma unroll
+                        for (int q = 0; q < kPreFB; ++q) v[q][ch] = __fmaf_rn(ps[q], dv, v[q][ch]);
+                        ++a;
                     }
-                    ++a;
                 }
             }
-#pragma unroll
+            // one frame at a time through v[0] (a rolled loop keeps the code small)
+#pragma unroll 1
             for (int q = 0; q < kPreFB; ++q) {
                 if (f0 + q < nr) {
-                    const int b = c.mframes[m.frame_off + round + f0 + q];
-                    const FrameInfo &f = c.frames[b];
-                    decide_and_write(c, f, s_fp + (f0 + q) * RGBA_FP_STRIDE, v[q], f.rec_base + i);
+                    const FrameConst &fc = s_fc[f0 + q];
+                    decide_and_write(c, fc, s_fp + (f0 + q) * RGBA_FP_STRIDE, v[0],
+                                     op_blended ? sigmoid_spec(v[0][10]) : op0, fc.rec_base + i);
                 }
+#pragma unroll
+                for (int q2 = 0; q2 + 1 < kPreFB; ++q2)
+#pragma unroll
+                    for (int ch = 0; ch < kNch; ++ch) v[q2][ch] = v[q2 + 1][ch];
             }
         }
         __syncthreads();
