@@ -157,7 +157,6 @@ int make_plan(const rgba_batch *b, Plan &p) {
     L.rects = take(8 * (size_t)R);
     L.cache = take(sizeof(float) * kCacheFloats * (size_t)R);
     L.grad2d = take(sizeof(float) * kG2Floats * (size_t)R);
-    L.dgb = take(sizeof(float) * 16 * (size_t)R);
     L.ranks = take(4 * kRankSlots * (size_t)R);
     L.pix_T = take(4 * (size_t)P);
     L.pix_n = take(4 * (size_t)P);
@@ -213,7 +212,6 @@ Ctx make_ctx(const Layout &L, unsigned char *ws, const rgba_batch *b) {
     c.keys2 = reinterpret_cast<unsigned long long *>(ws + L.keys2);
     c.sorted = reinterpret_cast<unsigned *>(ws + L.sorted);
     c.dpsi_part = reinterpret_cast<float *>(ws + L.dpsi_part);
-    c.dgb = reinterpret_cast<float *>(ws + L.dgb);
     c.ranks = reinterpret_cast<unsigned *>(ws + L.ranks);
     c.R = L.R;
     c.T = L.T;
@@ -356,7 +354,7 @@ int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, cons
         if (m.gdg && (rc = memset_async(m.gdg, sizeof(float) * (size_t)m.k * m.A * m.n_pad, k.s, "memset grad_dg"))) return rc;
     }
     {
-        StageScope sc(ctx, ST_GBWD, k.s, 2);
+        StageScope sc(ctx, ST_GBWD, k.s, 1);
         if ((e = launch_gauss_bwd(k.c, k.p.max_chunks, k.p.max_n, k.p.max_k, k.s)) != cudaSuccess)
             return cuda_fail(e, "gauss bwd");
     }

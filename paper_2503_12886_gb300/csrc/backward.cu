@@ -1,15 +1,15 @@
 // Backward through the projection (EWA splatting, activations) and the linear blend (Eq. 1).
 //
-//   k_chain      one thread per (frame, Gaussian): the 2-D gradients dL/d(u, v, conic,
-//                opacity, colour) from compositing -> dL/dG_b over the 14 blended channels
-//                (chain rule through conic inversion, J W Sigma W^T J^T, R diag(s^2) R^T,
-//                quaternion normalisation, exp and sigmoid), streamed to the workspace;
-//   k_blend_bwd  one CTA per 32 Gaussians of one model, lane = Gaussian, the adjoint of Eq. 1:
+//   k_gauss_bwd  one CTA per 32 Gaussians of one model, lane = Gaussian, frames 16 at a time:
+//                first, per (frame, Gaussian), the 2-D gradients dL/d(u, v, conic, opacity,
+//                colour) from compositing -> dL/dG_b over the 14 channels (chain rule through
+//                conic inversion, J W Sigma W^T J^T, R diag(s^2) R^T, quaternion
+//                normalisation, exp and sigmoid) into shared memory; then the adjoint of Eq. 1:
 //                dG0[ch][i]    += sum_b dG_b[ch][i]
 //                ddG[k][a][i]  += sum_b psi_b[k] dG_b[ch_a][i]
 //                dpsi_b[k]     partial = sum_{a, i in chunk} dG_k[a][i] dG_b[ch_a][i]
 // The reduction over frames happens in registers in a fixed order, so dG0 and ddG are
-// deterministic; dpsi partials go to a [frame][k][chunk] buffer that a third kernel sums.
+// deterministic; dpsi partials go to a [frame][k][chunk] buffer that a second kernel sums.
 #include "rgba_internal.cuh"
 
 namespace rgba {
@@ -184,51 +184,53 @@ __device__ __forceinline__ void chain(const float v[10], float op, const float *
     for (int c = 0; c < 3; ++c) dG[c] = V[c] * dp0 + V[4 + c] * dp1 + V[8 + c] * dp2;
 }
 
-// Phase 1, streaming: one thread per (frame, Gaussian); dL/dG_b over the 14 channels into the
-// workspace ([R][16] floats, channels 14 and 15 zero).
-constexpr int kChainThreads = 256;
-
-__global__ void __launch_bounds__(kChainThreads)
-k_chain(Ctx c) {
-    __shared__ float s_fp[RGBA_FP_STRIDE];
-    const int b = blockIdx.y;
-    const FrameInfo f = c.frames[b];
-    if (threadIdx.x < RGBA_FP_STRIDE) s_fp[threadIdx.x] = c.fparams[(size_t)b * RGBA_FP_STRIDE + threadIdx.x];
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= f.n) return;
-    const long long r = f.rec_base + i;
-    float dG[kNch];
-#pragma unroll
-    for (int q = 0; q < kNch; ++q) dG[q] = 0.f;
-    const ushort4 rc = c.rects[r];
-    if (rc.z > rc.x && rc.w > rc.y) {
-        const float4 c0 = c.cache[r * 3 + 0], c1 = c.cache[r * 3 + 1], c2 = c.cache[r * 3 + 2];
-        const float v[10] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y};
-        const float4 *gp = reinterpret_cast<const float4 *>(c.grad2d + r * kG2Floats);
-        const float4 ga = gp[0], gb = gp[1], gc = gp[2];
-        const float g2[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
-        const float op = c.records[r * 3 + 1].y;
-        chain(v, op, s_fp, f.W, f.H, g2, dG);
-    }
-    float4 *o = reinterpret_cast<float4 *>(c.dgb + r * 16);
-    o[0] = make_float4(dG[0], dG[1], dG[2], dG[3]);
-    o[1] = make_float4(dG[4], dG[5], dG[6], dG[7]);
-    o[2] = make_float4(dG[8], dG[9], dG[10], dG[11]);
-    o[3] = make_float4(dG[12], dG[13], 0.f, 0.f);
-}
-
-// Phase 2: the adjoint of Eq. 1. One CTA = 32 Gaussians (lane = Gaussian) of one model; the
-// frames that render it go through shared memory 16 at a time.
+// The backward of one model chunk. One CTA = 32 Gaussians (lane = Gaussian) of one model; the
+// frames that render it go 16 at a time. First the chain rule per (frame, Gaussian) turns the
+// 2-D gradients into dL/dG_b over the 14 channels, straight into shared memory; then the
+// adjoint of Eq. 1 reduces them over the frames. A warp takes two adjacent
+// blendshapes k, k+1 at a time with the 16 frames' weights psi_b[k], psi_b[k+1] in registers,
+// so each dG_b value read from shared memory feeds four FMAs; its dpsi partials (16 frames x 2
+// blendshapes per lane) are summed over the warp by a shuffle reduce-scatter.
 constexpr int kFG2 = 16;
 constexpr int kWarps = kBwdThreads / 32;
 
+// Sum of v[j] over the 32 lanes for j = 0..15, by recursive halving: after the call lane l
+// holds the total of j = l >> 1 in v[0] (lanes 2j and 2j+1 both hold it).
+__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {  // xor 16: keep the half selected by bit 4
+        const bool hi = lane & 16;
+        const float send = hi ? v[j] : v[j + 8], keep = hi ? v[j + 8] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // xor 8: bit 3
+        const bool hi = lane & 8;
+        const float send = hi ? v[j] : v[j + 4], keep = hi ? v[j + 4] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {  // xor 4: bit 2
+        const bool hi = lane & 4;
+        const float send = hi ? v[j] : v[j + 2], keep = hi ? v[j + 2] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {  // xor 2: bit 1
+        const bool hi = lane & 2;
+        const float send = hi ? v[0] : v[1], keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 __global__ void __launch_bounds__(kBwdThreads)
-k_blend_bwd(Ctx c, int max_k) {
+k_gauss_bwd(Ctx c, int max_k) {
     extern __shared__ float smem[];
     float *s_dG = smem;                                   // [16][14][32]
     float *s_psi = s_dG + kFG2 * kNch * kBwdChunk;        // [16][max_k]
-    float *s_red = s_psi + kFG2 * max_k;                  // [warps][32][17]
+    __shared__ long long s_rec[kFG2];
+    __shared__ int s_wh[kFG2][2];
+    __shared__ float s_fp[kFG2][RGBA_FP_STRIDE];
     const ModelInfo &m = c.models[blockIdx.y];
     const int chunk = blockIdx.x;
     const int i0 = chunk * kBwdChunk;
@@ -238,33 +240,47 @@ k_blend_bwd(Ctx c, int max_k) {
     const bool valid = i < m.n;      // real Gaussian
     const bool in_pad = i < m.n_pad; // row slot (padding slots receive zeros)
     const int K = m.k, A = m.A;
-    float *red = s_red + warp * 32 * (kFG2 + 1);
     for (int g0 = 0; g0 < m.nb; g0 += kFG2) {
         const int ng = min(kFG2, m.nb - g0);
-        // dL/dG_b of the chunk: 4 float4 per (frame, Gaussian), coalesced
-        for (int e = threadIdx.x; e < ng * kBwdChunk * 4; e += kBwdThreads) {
-            const int fl = e / (kBwdChunk * 4), rem = e - fl * kBwdChunk * 4;
-            const int li = rem >> 2, q4 = rem & 3;
-            const int gi = i0 + li;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gi < m.n) {
-                const FrameInfo &f = c.frames[c.mframes[m.frame_off + g0 + fl]];
-                v = reinterpret_cast<const float4 *>(c.dgb + (f.rec_base + (long long)gi) * 16)[q4];
-            }
-            float *d = s_dG + (fl * kNch + q4 * 4) * kBwdChunk + li;
-            d[0] = v.x;
-            d[kBwdChunk] = v.y;
-            if (q4 < 3) {
-                d[2 * kBwdChunk] = v.z;
-                d[3 * kBwdChunk] = v.w;
-            }
+        if (threadIdx.x < ng) {
+            const FrameInfo &f = c.frames[c.mframes[m.frame_off + g0 + threadIdx.x]];
+            s_rec[threadIdx.x] = f.rec_base;
+            s_wh[threadIdx.x][0] = f.W;
+            s_wh[threadIdx.x][1] = f.H;
         }
-        // frames past the group's end read as zero (the loops below run over all 16 slots)
-        for (int e = ng * kNch * kBwdChunk + threadIdx.x; e < kFG2 * kNch * kBwdChunk; e += kBwdThreads)
-            s_dG[e] = 0.f;
+        for (int e = threadIdx.x; e < ng * RGBA_FP_STRIDE; e += kBwdThreads) {
+            const int fl = e / RGBA_FP_STRIDE, q = e - fl * RGBA_FP_STRIDE;
+            s_fp[fl][q] = c.fparams[(size_t)c.mframes[m.frame_off + g0 + fl] * RGBA_FP_STRIDE + q];
+        }
         for (int e = threadIdx.x; e < kFG2 * max_k; e += kBwdThreads) {
             const int fl = e / max_k, kk = e % max_k;
             s_psi[e] = (fl < ng && kk < K) ? c.psi[(size_t)c.mframes[m.frame_off + g0 + fl] * c.k_stride + kk] : 0.f;
+        }
+        __syncthreads();
+        // dL/dG_b per (frame, Gaussian) of the chunk (zero for culled Gaussians and for frames
+        // past the group's end, which the loops below run over too); a warp takes 32
+        // consecutive Gaussians of one frame
+        for (int e = threadIdx.x; e < kFG2 * kBwdChunk; e += kBwdThreads) {
+            const int fl = e / kBwdChunk, li = e & (kBwdChunk - 1);
+            const int gi = i0 + li;
+            float dG[kNch];
+#pragma unroll
+            for (int q = 0; q < kNch; ++q) dG[q] = 0.f;
+            if (fl < ng && gi < m.n) {
+                const long long r = s_rec[fl] + gi;
+                const ushort4 rc = c.rects[r];
+                if (rc.z > rc.x && rc.w > rc.y) {
+                    const float4 c0 = c.cache[r * 3 + 0], c1 = c.cache[r * 3 + 1], c2 = c.cache[r * 3 + 2];
+                    const float v[10] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y};
+                    const float4 *gp = reinterpret_cast<const float4 *>(c.grad2d + r * kG2Floats);
+                    const float4 ga = gp[0], gb = gp[1], gc = gp[2];
+                    const float g2[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
+                    const float op = c.records[r * 3 + 1].y;
+                    chain(v, op, s_fp[fl], s_wh[fl][0], s_wh[fl][1], g2, dG);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kNch; ++q) s_dG[(fl * kNch + q) * kBwdChunk + li] = dG[q];
         }
         __syncthreads();
         // dG0[ch][i] = sum_b dG_b[ch][i]
@@ -277,38 +293,57 @@ k_blend_bwd(Ctx c, int max_k) {
             }
         }
         // ddG[k][a][i] = sum_b psi_b[k] dG_b[ch_a][i];  dpsi_b[k] partial = sum_a,i dG_k[a][i] dG_b[ch_a][i]
-        for (int kk = warp; kk < K; kk += kWarps) {
-            float psum[kFG2];
+        for (int kk = 2 * warp; kk < K; kk += 2 * kWarps) {
+            const bool two = kk + 1 < K;
+            float p0[kFG2], p1[kFG2], s0[kFG2], s1[kFG2];
 #pragma unroll
-            for (int fl = 0; fl < kFG2; ++fl) psum[fl] = 0.f;
+            for (int fl = 0; fl < kFG2; ++fl) {
+                p0[fl] = s_psi[fl * max_k + kk];
+                p1[fl] = two ? s_psi[fl * max_k + kk + 1] : 0.f;
+                s0[fl] = 0.f;
+                s1[fl] = 0.f;
+            }
+            // the blendshape values of channel a + 1 are loaded while channel a is summed
+            const float *dgp0 = m.dg + (size_t)kk * A * m.n_pad + i;
+            const float *dgp1 = dgp0 + (size_t)A * m.n_pad;
+            float nx0 = valid ? __ldg(dgp0) : 0.f;
+            float nx1 = (valid && two) ? __ldg(dgp1) : 0.f;
             for (int a = 0; a < A; ++a) {
                 const int ch = m.chans[a];
-                const size_t off = ((size_t)kk * A + a) * m.n_pad + i;
-                const float dgv = valid ? __ldg(m.dg + off) : 0.f;
-                float acc = 0.f;
+                const size_t off0 = ((size_t)kk * A + a) * m.n_pad + i;
+                const size_t off1 = off0 + (size_t)A * m.n_pad;
+                const float dg0 = nx0, dg1 = nx1;
+                if (a + 1 < A) {
+                    nx0 = valid ? __ldg(dgp0 + (size_t)(a + 1) * m.n_pad) : 0.f;
+                    nx1 = (valid && two) ? __ldg(dgp1 + (size_t)(a + 1) * m.n_pad) : 0.f;
+                }
+                float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
                 for (int fl = 0; fl < kFG2; ++fl) {
                     const float d = s_dG[(fl * kNch + ch) * kBwdChunk + lane];
-                    acc = fmaf(s_psi[fl * max_k + kk], d, acc);
-                    psum[fl] = fmaf(dgv, d, psum[fl]);
+                    acc0 = fmaf(p0[fl], d, acc0);
+                    acc1 = fmaf(p1[fl], d, acc1);
+                    s0[fl] = fmaf(dg0, d, s0[fl]);
+                    s1[fl] = fmaf(dg1, d, s1[fl]);
                 }
                 if (m.gdg && in_pad) {
-                    float *o = m.gdg + off;
-                    *o = (g0 == 0 ? 0.f : *o) + acc;
+                    float *o = m.gdg + off0;
+                    *o = (g0 == 0 ? 0.f : *o) + acc0;
+                    if (two) {
+                        o = m.gdg + off1;
+                        *o = (g0 == 0 ? 0.f : *o) + acc1;
+                    }
                 }
             }
             if (c.grad_psi) {
-                // warp sum of psum[fl] for every fl: transpose through shared memory
-#pragma unroll
-                for (int fl = 0; fl < kFG2; ++fl) red[lane * (kFG2 + 1) + fl] = psum[fl];
-                __syncwarp();
-                if (lane < ng) {
-                    float x = 0.f;
-#pragma unroll 8
-                    for (int l = 0; l < 32; ++l) x += red[l * (kFG2 + 1) + lane];
-                    c.dpsi_part[m.dpsi_off + ((long long)(g0 + lane) * K + kk) * m.n_chunks + chunk] = x;
+                const float t0 = warp_reduce_scatter16(s0, lane);
+                const float t1 = warp_reduce_scatter16(s1, lane);
+                const int fl = lane >> 1;
+                if ((lane & 1) == 0 && fl < ng) {
+                    float *dp = c.dpsi_part + m.dpsi_off + ((long long)(g0 + fl) * K + kk) * m.n_chunks + chunk;
+                    dp[0] = t0;
+                    if (two) dp[m.n_chunks] = t1;
                 }
-                __syncwarp();
             }
         }
         __syncthreads();
@@ -339,26 +374,22 @@ __global__ void k_dpsi_reduce(Ctx c) {
 }  // namespace
 
 cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_n, int max_k, cudaStream_t s) {
+    (void)max_n;
     if (c.M == 0 || max_chunks == 0) return cudaSuccess;
-    dim3 g1((max_n + kChainThreads - 1) / kChainThreads, c.B);
-    k_chain<<<g1, kChainThreads, 0, s>>>(c);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    auto bytes = [](int k) {
-        return (kFG2 * kNch * kBwdChunk + kFG2 * k + kWarps * 32 * (kFG2 + 1)) * (int)sizeof(float);
-    };
+    auto bytes = [](int k) { return (kFG2 * kNch * kBwdChunk + kFG2 * k) * (int)sizeof(float); };
     // set once, at the largest size any batch can ask for, so no attribute call happens while
     // a stream is being captured
     static int attr_device = -1;
     int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
     if (attr_device != dev) {
-        e = cudaFuncSetAttribute(k_blend_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes(RGBA_MAX_K));
+        e = cudaFuncSetAttribute(k_gauss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes(RGBA_MAX_K));
         if (e != cudaSuccess) return e;
         attr_device = dev;
     }
     dim3 g2(max_chunks, c.M);
-    k_blend_bwd<<<g2, kBwdThreads, bytes(max_k), s>>>(c, max_k);
+    k_gauss_bwd<<<g2, kBwdThreads, bytes(max_k), s>>>(c, max_k);
     return cudaGetLastError();
 }
 

@@ -66,7 +66,7 @@ static_assert(sizeof(Counters) <= 256, "counters fit in one 256-byte block");
 
 struct Layout {
     size_t counters, models, frames, mframes, tile_count, tile_start, cursor, work;
-    size_t records, rects, cache, grad2d, dgb, ranks, pix_T, pix_n, pix_dl, pix_img, dpsi_part;
+    size_t records, rects, cache, grad2d, ranks, pix_T, pix_n, pix_dl, pix_img, dpsi_part;
     size_t keys, keys2, sorted, total;
     long long R, T, P;     // records, tiles, pixels
     long long dpsi_floats;
@@ -96,7 +96,6 @@ struct Ctx {
     unsigned long long *keys2;  // [cap]: second buffer of the global-memory radix passes
     unsigned *sorted;
     float *dpsi_part;
-    float *dgb;        // [R][16]: dL/dG_b per (frame, Gaussian), 14 channels used
     unsigned *ranks;   // [R][kRankSlots]: slot of the Gaussian in each tile of its rectangle
     long long R, T, cap;
     int B, M, k_stride, tw, th;
