@@ -17,8 +17,11 @@ namespace {
 
 constexpr int kBwdThreads = 256;
 
+// The backward needs no bit-exact replay of the forward decisions (those come from the
+// records), only fp32 values to the gradient tolerance, so it uses the hardware's fast
+// reciprocal, reciprocal square root and exponential.
 struct Fwd {
-    float p[3], qn[4], qlen, s[3], R[3][3], M[3][3], J[2][3], rx, ry;
+    float p[3], qn[4], il, s[3], R[3][3], M[3][3], J[2][3], rx, ry, ipz;
     bool clx, cly;
     float A, B, C, det;
 };
@@ -27,11 +30,10 @@ __device__ __forceinline__ void recompute(const float v[10], const float *V, int
 #pragma unroll
     for (int j = 0; j < 3; ++j) f.p[j] = V[4 * j] * v[0] + V[4 * j + 1] * v[1] + V[4 * j + 2] * v[2] + V[4 * j + 3];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) f.s[m] = expf(v[7 + m]);
-    f.qlen = sqrtf(v[3] * v[3] + v[4] * v[4] + v[5] * v[5] + v[6] * v[6]);
-    const float il = 1.0f / f.qlen;
+    for (int m = 0; m < 3; ++m) f.s[m] = __expf(v[7 + m]);
+    f.il = rsqrtf(v[3] * v[3] + v[4] * v[4] + v[5] * v[5] + v[6] * v[6]);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) f.qn[m] = v[3 + m] * il;
+    for (int m = 0; m < 4; ++m) f.qn[m] = v[3 + m] * f.il;
     const float w = f.qn[0], x = f.qn[1], y = f.qn[2], z = f.qn[3];
     f.R[0][0] = 1.f - 2.f * (y * y + z * z);
     f.R[0][1] = 2.f * (x * y - w * z);
@@ -62,18 +64,19 @@ __device__ __forceinline__ void recompute(const float v[10], const float *V, int
 #pragma unroll
         for (int j = 0; j < 3; ++j) f.M[i][j] = Tm[i][0] * V[4 * j] + Tm[i][1] * V[4 * j + 1] + Tm[i][2] * V[4 * j + 2];
     const float fx = V[12], fy = V[13], pz = f.p[2];
-    const float limx = 1.3f * (0.5f * W / fx), limy = 1.3f * (0.5f * H / fy);
-    const float rx = f.p[0] / pz, ry = f.p[1] / pz;
+    const float limx = 1.3f * __fdividef(0.5f * W, fx), limy = 1.3f * __fdividef(0.5f * H, fy);
+    f.ipz = __frcp_rn(pz);
+    const float rx = f.p[0] * f.ipz, ry = f.p[1] * f.ipz;
     f.clx = rx > limx || rx < -limx;
     f.cly = ry > limy || ry < -limy;
     f.rx = fminf(limx, fmaxf(-limx, rx));
     f.ry = fminf(limy, fmaxf(-limy, ry));
-    f.J[0][0] = fx / pz;
+    f.J[0][0] = fx * f.ipz;
     f.J[0][1] = 0.f;
-    f.J[0][2] = -fx * f.rx / pz;
+    f.J[0][2] = -fx * f.rx * f.ipz;
     f.J[1][0] = 0.f;
-    f.J[1][1] = fy / pz;
-    f.J[1][2] = -fy * f.ry / pz;
+    f.J[1][1] = fy * f.ipz;
+    f.J[1][2] = -fy * f.ry * f.ipz;
     float S2[2][2];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -102,7 +105,7 @@ __device__ __forceinline__ void chain(const float v[10], float op, const float *
     dG[11] = g2[6];
     dG[12] = g2[7];
     dG[13] = g2[8];
-    const float A = f.A, B = f.B, C = f.C, D = f.det, iD = 1.f / D, iD2 = iD * iD;
+    const float A = f.A, B = f.B, C = f.C, D = f.det, iD = __frcp_rn(D), iD2 = iD * iD;
     const float dA = dca * (-C * C * iD2) + dcb * (B * C * iD2) + dcc * (iD - A * C * iD2);
     const float dC = dca * (iD - A * C * iD2) + dcb * (A * B * iD2) + dcc * (-A * A * iD2);
     const float dB = dca * (2.f * B * C * iD2) + dcb * (-iD - 2.f * B * B * iD2) + dcc * (2.f * A * B * iD2);
@@ -158,13 +161,13 @@ __device__ __forceinline__ void chain(const float v[10], float op, const float *
     const float dz = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
                             y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
     const float dot = w * dw + x * dx + y * dy + z * dz;
-    const float il = 1.f / f.qlen;
+    const float il = f.il;
     dG[3] = (dw - w * dot) * il;
     dG[4] = (dx - x * dot) * il;
     dG[5] = (dy - y * dot) * il;
     dG[6] = (dz - z * dot) * il;
     // mean
-    const float fx = V[12], fy = V[13], pz = f.p[2], ipz = 1.f / pz, ipz2 = ipz * ipz;
+    const float fx = V[12], fy = V[13], ipz = f.ipz, ipz2 = ipz * ipz;
     float dp0 = du * fx * ipz, dp1 = dv * fy * ipz;
     float dp2 = -du * fx * f.p[0] * ipz2 - dv * fy * f.p[1] * ipz2;
     dp2 += -(dJ[0][0] * fx + dJ[1][1] * fy) * ipz2;
@@ -260,27 +263,58 @@ k_gauss_bwd(Ctx c, int max_k) {
         // dL/dG_b per (frame, Gaussian) of the chunk (zero for culled Gaussians and for frames
         // past the group's end, which the loops below run over too); a warp takes 32
         // consecutive Gaussians of one frame
-        for (int e = threadIdx.x; e < kFG2 * kBwdChunk; e += kBwdThreads) {
-            const int fl = e / kBwdChunk, li = e & (kBwdChunk - 1);
-            const int gi = i0 + li;
-            float dG[kNch];
+        {
+            constexpr int kItems = kFG2 * kBwdChunk / kBwdThreads;
+            float4 c0[kItems], c1[kItems], c2[kItems], ga[kItems], gb[kItems], gc[kItems];
+            float op[kItems];
+            bool live[kItems];
 #pragma unroll
-            for (int q = 0; q < kNch; ++q) dG[q] = 0.f;
-            if (fl < ng && gi < m.n) {
-                const long long r = s_rec[fl] + gi;
-                const ushort4 rc = c.rects[r];
-                if (rc.z > rc.x && rc.w > rc.y) {
-                    const float4 c0 = c.cache[r * 3 + 0], c1 = c.cache[r * 3 + 1], c2 = c.cache[r * 3 + 2];
-                    const float v[10] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y};
+            for (int u = 0; u < kItems; ++u) {  // every load of both items in flight at once
+                const int e = threadIdx.x + u * kBwdThreads;
+                const int fl = e / kBwdChunk, gi = i0 + (e & (kBwdChunk - 1));
+                live[u] = fl < ng && gi < m.n;
+                const long long r = live[u] ? s_rec[fl] + gi : 0;
+                c0[u] = c1[u] = c2[u] = ga[u] = gb[u] = gc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                op[u] = 0.f;
+                if (live[u]) {
+                    const ushort4 rc = c.rects[r];
+                    live[u] = rc.z > rc.x && rc.w > rc.y;
+                    c0[u] = c.cache[r * 3 + 0];
+                    c1[u] = c.cache[r * 3 + 1];
+                    c2[u] = c.cache[r * 3 + 2];
                     const float4 *gp = reinterpret_cast<const float4 *>(c.grad2d + r * kG2Floats);
-                    const float4 ga = gp[0], gb = gp[1], gc = gp[2];
-                    const float g2[9] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w, gc.x};
-                    const float op = c.records[r * 3 + 1].y;
-                    chain(v, op, s_fp[fl], s_wh[fl][0], s_wh[fl][1], g2, dG);
+                    ga[u] = gp[0];
+                    gb[u] = gp[1];
+                    gc[u] = gp[2];
+                    op[u] = c.records[r * 3 + 1].y;
                 }
             }
+#pragma unroll 1
+            for (int u = 0; u < kItems; ++u) {
+                const int e = threadIdx.x + u * kBwdThreads;
+                const int fl = e / kBwdChunk, li = e & (kBwdChunk - 1);
+                float dG[kNch];
 #pragma unroll
-            for (int q = 0; q < kNch; ++q) s_dG[(fl * kNch + q) * kBwdChunk + li] = dG[q];
+                for (int q = 0; q < kNch; ++q) dG[q] = 0.f;
+                if (live[0]) {  // item u sits in slot 0 (a rolled loop keeps the code small)
+                    const float v[10] = {c0[0].x, c0[0].y, c0[0].z, c0[0].w, c1[0].x, c1[0].y, c1[0].z, c1[0].w, c2[0].x, c2[0].y};
+                    const float g2[9] = {ga[0].x, ga[0].y, ga[0].z, ga[0].w, gb[0].x, gb[0].y, gb[0].z, gb[0].w, gc[0].x};
+                    chain(v, op[0], s_fp[fl], s_wh[fl][0], s_wh[fl][1], g2, dG);
+                }
+#pragma unroll
+                for (int q = 0; q < kNch; ++q) s_dG[(fl * kNch + q) * kBwdChunk + li] = dG[q];
+#pragma unroll
+                for (int w = 0; w + 1 < kItems; ++w) {
+                    c0[w] = c0[w + 1];
+                    c1[w] = c1[w + 1];
+                    c2[w] = c2[w + 1];
+                    ga[w] = ga[w + 1];
+                    gb[w] = gb[w + 1];
+                    gc[w] = gc[w + 1];
+                    op[w] = op[w + 1];
+                    live[w] = live[w + 1];
+                }
+            }
         }
         __syncthreads();
         // dG0[ch][i] = sum_b dG_b[ch][i]
