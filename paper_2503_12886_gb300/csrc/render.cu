@@ -146,11 +146,17 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
             __syncthreads();
             const int cnt = min(BATCH, (int)(en - base));
             const int pos0 = (int)(base - st) + 1;
-#pragma unroll 4
-            for (int j = 0; j < cnt; ++j) {
-                if (p.done) break;
-                if (box_misses(s_box[j], bx0, bx1, by0, by1)) continue;  // whole warp, uniform
-                composite(p, s_a, s_q, s_c, j, pos0 + j);
+            // 32 entries at a time: each lane tests one box against the warp's block, and the
+            // warp then visits only the entries that hit, in list order
+            for (int j0 = 0; j0 < cnt; j0 += 32) {
+                if (__all_sync(0xffffffffu, p.done)) break;
+                const int jl = j0 + lane;
+                unsigned hits = __ballot_sync(0xffffffffu, jl < cnt && !box_misses(s_box[jl], bx0, bx1, by0, by1));
+                while (hits) {
+                    const int j = j0 + __ffs(hits) - 1;
+                    hits &= hits - 1;
+                    if (!p.done) composite(p, s_a, s_q, s_c, j, pos0 + j);
+                }
             }
         }
         if (p.inside) {
@@ -342,21 +348,30 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
             }
             for (int e = tid; e < 9 * BATCH; e += kThreads) (&s_g[0][0])[e] = 0.f;
             __syncthreads();
-            for (int j = min(cnt, warp_last - begin) - 1; j >= 0; --j) {
-                if (box_misses(s_box[j], bx0, bx1, by0, by1)) continue;  // whole warp, uniform
-                const int pos = begin + j + 1;
-                const float4 A = s_a[j], Cc = s_c[j];
-                const float2 Q = s_q[j];
-                float v[9];
+            // 32 entries at a time from the top: each lane tests one box against the warp's
+            // block, and the warp then visits only the entries that hit, in reverse list order
+            const int jtop = min(cnt, warp_last - begin);
+            for (int j0 = (jtop - 1) & ~31; j0 >= 0; j0 -= 32) {
+                const int jl = j0 + lane;
+                unsigned hits = __ballot_sync(0xffffffffu, jl < jtop && !box_misses(s_box[jl], bx0, bx1, by0, by1));
+                while (hits) {
+                    const int bit = 31 - __clz(hits);
+                    hits &= ~(1u << bit);
+                    const int j = j0 + bit;
+                    const int pos = begin + j + 1;
+                    const float4 A = s_a[j], Cc = s_c[j];
+                    const float2 Q = s_q[j];
+                    float v[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) v[q] = 0.f;
-                bool any = accumulate(p[0], pos, A, Q, Cc, v);
-                any |= accumulate(p[1], pos, A, Q, Cc, v);
-                if (__any_sync(0xffffffffu, any)) {
-                    float mine, v8;
-                    warp_reduce9(v, lane, mine, v8);
-                    if ((lane & 3) == 0) atomicAdd(&s_g[j][lane >> 2], mine);
-                    if (lane == 0) atomicAdd(&s_g[j][8], v8);
+                    for (int q = 0; q < 9; ++q) v[q] = 0.f;
+                    bool any = accumulate(p[0], pos, A, Q, Cc, v);
+                    any |= accumulate(p[1], pos, A, Q, Cc, v);
+                    if (__any_sync(0xffffffffu, any)) {
+                        float mine, v8;
+                        warp_reduce9(v, lane, mine, v8);
+                        if ((lane & 3) == 0) atomicAdd(&s_g[j][lane >> 2], mine);
+                        if (lane == 0) atomicAdd(&s_g[j][8], v8);
+                    }
                 }
             }
             __syncthreads();
