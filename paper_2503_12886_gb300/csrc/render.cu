@@ -1,11 +1,13 @@
 // Front-to-back alpha compositing ("rasterize", RGBAvatar Sec. 3.2 on the 3DGS renderer) and
-// its exact reverse. One 256-thread CTA owns one screen tile (16x16 or 8x32 pixels) at a time;
-// persistent CTAs pull (frame, tile) items from the device work list, so every frame of every
-// avatar in the batch shares one launch. Gaussians are staged in shared memory in rounds of
-// BATCH entries, each with the box of its alpha >= 1/255 ellipse; every warp owns a compact
-// block of pixels (8 x 4 in the forward, 8 x 8 with two pixels per lane in the backward) and
-// skips, with one uniform test, the entries whose box misses its block. A CTA stops as soon as
-// every pixel of its tile is saturated.
+// its exact reverse. The binning tile (16x16 or 8x32 pixels) fixes the lists; the compositing
+// work is split finer: every warp is an independent persistent worker that takes (tile, pixel
+// block) items from one counter, so the few heavy tiles of a face-centred frame spread over
+// many warps and no warp ever waits at a CTA barrier. A forward block is 8 x 4 pixels (one per
+// lane); a backward block 8 x 4 or 8 x 8 (two pixels per lane). A warp walks its tile's list in
+// steps of BATCH entries: each lane stages BATCH / 32 of them into the warp's shared-memory
+// slots together with the box of the entry's alpha >= 1/255 ellipse, a ballot marks the entries
+// whose box meets the warp's block, and only those are visited, in list order (in reverse in
+// the backward). The forward stops once every pixel of the block is saturated.
 //
 // Per pixel, with d = pixel centre - mean:
 //   power = -(a dx^2 + c dy^2) / 2 - b dx dy  (skip if > 0)
@@ -13,9 +15,8 @@
 //   stop, without blending, once T (1 - alpha) < 1e-4
 // The backward recomputes each alpha with the same instruction sequence as the forward, walks
 // the list backwards from the stored contributor count, and recovers T by division by
-// (1 - alpha). Per-Gaussian gradients are reduced across the warp (reduce-scatter), then
-// across the CTA in shared memory, and reach global memory as one atomic per Gaussian, tile
-// and component.
+// (1 - alpha). Per-Gaussian gradients are reduced across the warp (reduce-scatter) and reach
+// global memory as one atomic per Gaussian, pixel block and component.
 #include "rgba_internal.cuh"
 
 namespace rgba {
@@ -39,14 +40,12 @@ __device__ __forceinline__ int find_frame(const Ctx &c, long long t) {
 // tail of a splat, 90 % of all evaluations) are rejected from a and q alone, before the
 // exponential and before the colour is read. Both kernels stage and evaluate through these
 // functions, so their decisions agree bit for bit.
-__device__ __forceinline__ void stage_splat(const float4 *rec, unsigned idx, float4 &sa, float2 &sq,
-                                            float4 &sc, float4 &sb) {
-    const float4 r0 = rec[(size_t)idx * 3 + 0], r1 = rec[(size_t)idx * 3 + 1];
-    const float r2 = rec[(size_t)idx * 3 + 2].x;
+__device__ __forceinline__ void splat_from_record(const float4 &r0, const float4 &r1, float r2x, float4 &sa,
+                                                  float2 &sq, float4 &sc, float4 &sb) {
     sa = make_float4(r0.x, r0.y, -0.5f * r0.z, -r0.w);
     const float tau = -__logf(255.0f * r1.y);
     sq = make_float2(-0.5f * r1.x, tau);
-    sc = make_float4(r1.y, r1.z, r1.w, r2);
+    sc = make_float4(r1.y, r1.z, r1.w, r2x);
     // bounding box of the ellipse power >= tau, i.e. d^T conic d <= -2 tau: half-extents
     // sqrt(-2 tau Sigma'_xx) and sqrt(-2 tau Sigma'_yy) with Sigma' = conic^-1, widened by 1 %
     // + 0.05 px so that everything it excludes fails the per-pixel test with room to spare
@@ -73,8 +72,6 @@ __device__ __forceinline__ float power_of(float dx, float dy, const float4 &A, c
 // the skip decision: a positive power (never, for a positive definite conic, but kept as the
 // definition) or alpha below 1/255
 __device__ __forceinline__ bool skip(float power, float tau) { return power > 0.0f || power < tau; }
-
-constexpr int kThreads = kTilePix / 2;  // backward: two pixels per thread, rows y and y + TH/2
 
 struct PixF {
     float pxc, pyc, T, C0, C1, C2;
@@ -105,97 +102,189 @@ __device__ __forceinline__ void composite(PixF &p, const float4 *s_a, const floa
     p.last = pos;
 }
 
+constexpr int kWarpsPerCta = 4;  // independent warps per CTA (they share nothing but the loss sum)
+
+// A warp's staging of BATCH list entries [lo, lo + BATCH) (those in [0, hi)), lane l taking
+// slots l, l + 32, ...: first the entries' Gaussian indices, then their records, then the
+// staged form in the warp's shared-memory slots with, per 32-slot word, the ballot of entries
+// whose box meets the block. The three steps run one and two batches ahead of the compositing,
+// so the loads of the next batch are in flight while the current one is composited.
+template <int S>
+struct Stage {
+    unsigned idx[S];
+    float4 r0[S], r1[S];
+    float r2[S];
+};
+
+template <int S>
+__device__ __forceinline__ void load_idx(const Ctx &c, int lo, int hi, unsigned st, unsigned idx[S]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        const int e = lo + lane + 32 * q;
+        idx[q] = (e >= 0 && e < hi) ? c.sorted[st + e] : 0u;
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void load_rec(const float4 *rec, int lo, int hi, const unsigned idx[S], Stage<S> &g) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        g.idx[q] = idx[q];
+        if (lo + lane + 32 * q >= 0 && lo + lane + 32 * q < hi) {
+            const float4 *r = rec + (size_t)idx[q] * 3;
+            g.r0[q] = r[0];
+            g.r1[q] = r[1];
+            g.r2[q] = r[2].x;
+        }
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void commit(const Stage<S> &g, int lo, int hi, float4 *wa, float2 *wq, float4 *wc,
+                                       unsigned *widx, float bx0, float bx1, float by0, float by1, unsigned hit[S]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        bool h = false;
+        if (lo + lane + 32 * q >= 0 && lo + lane + 32 * q < hi) {
+            float4 sa, sc, sb;
+            float2 sq;
+            splat_from_record(g.r0[q], g.r1[q], g.r2[q], sa, sq, sc, sb);
+            const int k = lane + 32 * q;
+            wa[k] = sa;
+            wq[k] = sq;
+            wc[k] = sc;
+            if (widx) widx[k] = g.idx[q];
+            h = !box_misses(sb, bx0, bx1, by0, by1);
+        }
+        hit[q] = __ballot_sync(0xffffffffu, h);
+    }
+}
+
+// Writes one finished pixel (colour over the background, T, contributor count) and, with a
+// target, its loss term and dL/dpixel.
+__device__ __forceinline__ void finish_pixel(const Ctx &c, const FrameInfo &f, int b, int px, int py,
+                                             const PixF &p, float *img, float *T_final, int *n_contrib,
+                                             const float *target, int loss_kind, float *dl_dimg,
+                                             float &loss_acc) {
+    const float *bg = c.fparams + (size_t)b * RGBA_FP_STRIDE + 17;
+    const long long hw = (long long)f.W * f.H;
+    const long long pix = (long long)py * f.W + px;
+    float *im = img + f.pix_base * 3 + pix;
+    const float o0 = fmaf(p.T, bg[0], p.C0), o1 = fmaf(p.T, bg[1], p.C1), o2 = fmaf(p.T, bg[2], p.C2);
+    im[0] = o0;
+    im[hw] = o1;
+    im[2 * hw] = o2;
+    T_final[f.pix_base + pix] = p.T;
+    n_contrib[f.pix_base + pix] = p.last;
+    if (target) {
+        const float *tg = target + f.pix_base * 3 + pix;
+        const float scale = 1.0f / (3.0f * (float)hw * (float)c.B);
+        const float d0 = o0 - tg[0], d1 = o1 - tg[hw], d2 = o2 - tg[2 * hw];
+        float *dl = dl_dimg + f.pix_base * 3 + pix;
+        if (loss_kind == RGBA_LOSS_L1) {
+            loss_acc += (fabsf(d0) + fabsf(d1) + fabsf(d2)) * scale;
+            dl[0] = d0 > 0.f ? scale : (d0 < 0.f ? -scale : 0.f);
+            dl[hw] = d1 > 0.f ? scale : (d1 < 0.f ? -scale : 0.f);
+            dl[2 * hw] = d2 > 0.f ? scale : (d2 < 0.f ? -scale : 0.f);
+        } else {
+            loss_acc += 0.5f * (d0 * d0 + d1 * d1 + d2 * d2) * scale;
+            dl[0] = d0 * scale;
+            dl[hw] = d1 * scale;
+            dl[2 * hw] = d2 * scale;
+        }
+    }
+}
+
+// Items: the pixel blocks of the non-empty tiles (work list order, heaviest tiles first), then
+// one item per empty tile, which the warp fills with the background eight pixels per lane.
 template <int TW, int BATCH>
-__global__ void __launch_bounds__(kTilePix)
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *__restrict__ n_contrib,
              const float *__restrict__ target, int loss_kind, float *__restrict__ dl_dimg) {
-    constexpr int TH = kTilePix / TW;
-    __shared__ float4 s_a[BATCH];
-    __shared__ float2 s_q[BATCH];
-    __shared__ float4 s_c[BATCH];
-    __shared__ float4 s_box[BATCH];
-    __shared__ unsigned s_w;
-    __shared__ float s_red[kTilePix / 32];
+    constexpr int TH = kTilePix / TW, BH = 4, NBX = TW / 8, NB = NBX * (TH / BH), S = BATCH / 32;
+    __shared__ float4 s_a[kWarpsPerCta][BATCH];
+    __shared__ float2 s_q[kWarpsPerCta][BATCH];
+    __shared__ float4 s_c[kWarpsPerCta][BATCH];
+    __shared__ float s_red[kWarpsPerCta];
     if (c.cnt->overflow) return;
-    const int tid = threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4 *wa = s_a[wid], *wc = s_c[wid];
+    float2 *wq = s_q[wid];
+    const unsigned n_work = c.cnt->n_work, n_blocks = n_work * NB;
+    const unsigned n_items = n_blocks + ((unsigned)c.T - n_work);
     float loss_acc = 0.0f;
     while (true) {
-        if (tid == 0) s_w = atomicAdd(&c.cnt->next_fwd, 1u);
-        __syncthreads();
-        const unsigned w = s_w;
-        __syncthreads();
-        if (w >= (unsigned)c.T) break;
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(&c.cnt->next_fwd, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        if (item >= n_blocks) {  // an empty tile: background, T = 1, no contributors
+            const long long t = c.work[n_work + (item - n_blocks)];
+            const int b = find_frame(c, t);
+            const FrameInfo &f = c.frames[b];
+            const int lt = (int)(t - f.tile_base);
+            const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
+#pragma unroll 1
+            for (int k = lane; k < kTilePix; k += 32) {
+                const int px = tx * TW + (k % TW), py = ty * TH + (k / TW);
+                if (px < f.W && py < f.H) {
+                    const PixF p{(float)px + 0.5f, (float)py + 0.5f, 1.f, 0.f, 0.f, 0.f, 0, true, true};
+                    finish_pixel(c, f, b, px, py, p, img, T_final, n_contrib, target, loss_kind, dl_dimg, loss_acc);
+                }
+            }
+            continue;
+        }
+        const unsigned w = item / NB, blk = item - w * NB;
         const long long t = c.work[w];
         const int b = find_frame(c, t);
         const FrameInfo &f = c.frames[b];
         const int lt = (int)(t - f.tile_base);
         const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
-        // warp w owns an 8 x 4 block of the tile: column block w % (TW / 8), row block w / (TW / 8)
-        const int warp = tid >> 5, lane = tid & 31;
-        const int bx = tx * TW + (warp % (TW / 8)) * 8, by = ty * TH + (warp / (TW / 8)) * 4;
+        const int bx = tx * TW + (int)(blk % NBX) * 8, by = ty * TH + (int)(blk / NBX) * BH;
         const int px = bx + (lane & 7), py = by + (lane >> 3);
         const float bx0 = (float)bx + 0.5f, bx1 = (float)bx + 7.5f, by0 = (float)by + 0.5f, by1 = (float)by + 3.5f;
         PixF p{(float)px + 0.5f, (float)py + 0.5f, 1.f, 0.f, 0.f, 0.f, 0, px < f.W && py < f.H, false};
         p.done = !p.inside;
-        const unsigned st = c.tile_start[t], en = c.tile_start[t + 1];
+        const unsigned st = c.tile_start[t];
+        const int len = (int)(c.tile_start[t + 1] - st);
         const float4 *rec = c.records + (size_t)f.rec_base * 3;
-        for (unsigned base = st; base < en; base += BATCH) {
-            if (__syncthreads_count(p.done) == kTilePix) break;
-            if (tid < BATCH && base + tid < en)
-                stage_splat(rec, c.sorted[base + tid], s_a[tid], s_q[tid], s_c[tid], s_box[tid]);
-            __syncthreads();
-            const int cnt = min(BATCH, (int)(en - base));
-            const int pos0 = (int)(base - st) + 1;
-            // 32 entries at a time: each lane tests one box against the warp's block, and the
-            // warp then visits only the entries that hit, in list order
-            for (int j0 = 0; j0 < cnt; j0 += 32) {
-                if (__all_sync(0xffffffffu, p.done)) break;
-                const int jl = j0 + lane;
-                unsigned hits = __ballot_sync(0xffffffffu, jl < cnt && !box_misses(s_box[jl], bx0, bx1, by0, by1));
-                while (hits) {
-                    const int j = j0 + __ffs(hits) - 1;
-                    hits &= hits - 1;
-                    if (!p.done) composite(p, s_a, s_q, s_c, j, pos0 + j);
+        Stage<S> g;
+        unsigned nidx[S];
+        load_idx<S>(c, 0, len, st, nidx);
+        load_rec<S>(rec, 0, len, nidx, g);
+        load_idx<S>(c, BATCH, len, st, nidx);
+        for (int lo = 0; lo < len; lo += BATCH) {
+            if (__all_sync(0xffffffffu, p.done)) break;
+            unsigned hit[S];
+            __syncwarp();  // the previous batch's slots are no longer read
+            commit<S>(g, lo, len, wa, wq, wc, nullptr, bx0, bx1, by0, by1, hit);
+            load_rec<S>(rec, lo + BATCH, len, nidx, g);
+            load_idx<S>(c, lo + 2 * BATCH, len, st, nidx);
+            __syncwarp();
+            const int pos0 = lo + 1;
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                unsigned hm = hit[q];
+                while (hm) {
+                    const int j = 32 * q + __ffs(hm) - 1;
+                    hm &= hm - 1;
+                    if (!p.done) composite(p, wa, wq, wc, j, pos0 + j);
                 }
             }
         }
-        if (p.inside) {
-            const float *bg = c.fparams + (size_t)b * RGBA_FP_STRIDE + 17;
-            const long long hw = (long long)f.W * f.H;
-            const long long pix = (long long)py * f.W + px;
-            float *im = img + f.pix_base * 3 + pix;
-            const float o0 = fmaf(p.T, bg[0], p.C0), o1 = fmaf(p.T, bg[1], p.C1), o2 = fmaf(p.T, bg[2], p.C2);
-            im[0] = o0;
-            im[hw] = o1;
-            im[2 * hw] = o2;
-            T_final[f.pix_base + pix] = p.T;
-            n_contrib[f.pix_base + pix] = p.last;
-            if (target) {
-                const float *tg = target + f.pix_base * 3 + pix;
-                const float scale = 1.0f / (3.0f * (float)hw * (float)c.B);
-                const float d0 = o0 - tg[0], d1 = o1 - tg[hw], d2 = o2 - tg[2 * hw];
-                float *dl = dl_dimg + f.pix_base * 3 + pix;
-                if (loss_kind == RGBA_LOSS_L1) {
-                    loss_acc += (fabsf(d0) + fabsf(d1) + fabsf(d2)) * scale;
-                    dl[0] = d0 > 0.f ? scale : (d0 < 0.f ? -scale : 0.f);
-                    dl[hw] = d1 > 0.f ? scale : (d1 < 0.f ? -scale : 0.f);
-                    dl[2 * hw] = d2 > 0.f ? scale : (d2 < 0.f ? -scale : 0.f);
-                } else {
-                    loss_acc += 0.5f * (d0 * d0 + d1 * d1 + d2 * d2) * scale;
-                    dl[0] = d0 * scale;
-                    dl[hw] = d1 * scale;
-                    dl[2 * hw] = d2 * scale;
-                }
-            }
-        }
+        if (p.inside)
+            finish_pixel(c, f, b, px, py, p, img, T_final, n_contrib, target, loss_kind, dl_dimg, loss_acc);
     }
     if (target) {
         for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
-        if ((tid & 31) == 0) s_red[tid >> 5] = loss_acc;
+        if (lane == 0) s_red[wid] = loss_acc;
         __syncthreads();
-        if (tid == 0) {
+        if (threadIdx.x == 0) {
             float sum = 0.f;
-            for (int i = 0; i < kTilePix / 32; ++i) sum += s_red[i];
+            for (int i = 0; i < kWarpsPerCta; ++i) sum += s_red[i];
             atomicAdd(&c.cnt->loss, (double)sum);
         }
     }
@@ -274,50 +363,46 @@ __device__ __forceinline__ void warp_reduce9(const float v[9], int lane, float &
     v8 = x;
 }
 
-template <int TW, int BATCH>
-__global__ void __launch_bounds__(kThreads)
+template <int TW, int BATCH, int PXL>
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__ T_final,
              const int *__restrict__ n_contrib) {
-    constexpr int TH = kTilePix / TW;
-    __shared__ float4 s_a[BATCH];
-    __shared__ float2 s_q[BATCH];
-    __shared__ float4 s_c[BATCH];
-    __shared__ float4 s_box[BATCH];
-    __shared__ unsigned s_idx[BATCH];
-    __shared__ float s_g[BATCH][9];  // per entry: stride 9 keeps lanes on distinct banks
-    __shared__ unsigned s_w;
-    __shared__ int s_max;
+    constexpr int TH = kTilePix / TW, BH = 4 * PXL, NBX = TW / 8, NB = NBX * (TH / BH), S = BATCH / 32;
+    __shared__ float4 s_a[kWarpsPerCta][BATCH];
+    __shared__ float2 s_q[kWarpsPerCta][BATCH];
+    __shared__ float4 s_c[kWarpsPerCta][BATCH];
+    __shared__ unsigned s_idx[kWarpsPerCta][BATCH];
     if (c.cnt->overflow) return;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const unsigned n_work = c.cnt->n_work;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4 *wa = s_a[wid], *wc = s_c[wid];
+    float2 *wq = s_q[wid];
+    unsigned *widx = s_idx[wid];
+    const unsigned n_items = c.cnt->n_work * NB;
     while (true) {
-        if (tid == 0) {
-            s_w = atomicAdd(&c.cnt->next_bwd, 1u);
-            s_max = 0;
-        }
-        __syncthreads();
-        const unsigned w = s_w;
-        if (w >= n_work) break;
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(&c.cnt->next_bwd, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        const unsigned w = item / NB, blk = item - w * NB;
         const long long t = c.work[w];
         const int b = find_frame(c, t);
         const FrameInfo &f = c.frames[b];
         const int lt = (int)(t - f.tile_base);
         const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
-        // warp w owns an 8 x 8 block: column block w % (TW / 8), row block w / (TW / 8); each
-        // lane two pixels of the block, rows lane / 8 and lane / 8 + 4
-        const int warp = tid >> 5;
-        const int bx = tx * TW + (warp % (TW / 8)) * 8, by = ty * TH + (warp / (TW / 8)) * 8;
+        // the block: 8 x BH pixels; lane l owns column l % 8 of rows l / 8 + 4 h, h < PXL
+        const int bx = tx * TW + (int)(blk % NBX) * 8, by = ty * TH + (int)(blk / NBX) * BH;
         const int px = bx + (lane & 7), py0 = by + (lane >> 3);
-        const float bx0 = (float)bx + 0.5f, bx1 = (float)bx + 7.5f, by0 = (float)by + 0.5f, by1 = (float)by + 7.5f;
+        const float bx0 = (float)bx + 0.5f, bx1 = (float)bx + 7.5f, by0 = (float)by + 0.5f,
+                    by1 = (float)by + (float)BH - 0.5f;
         const unsigned st = c.tile_start[t], list_len = c.tile_start[t + 1] - st;
         const float4 *rec = c.records + (size_t)f.rec_base * 3;
         float *g2 = c.grad2d + (size_t)f.rec_base * kG2Floats;
         const float *bgp = c.fparams + (size_t)b * RGBA_FP_STRIDE + 17;
         const long long hw = (long long)f.W * f.H;
-        PixB p[2];
+        PixB p[PXL];
         int m = 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < PXL; ++h) {
             const int py = py0 + h * 4;
             p[h] = PixB{(float)px + 0.5f, (float)py + 0.5f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
             if (px < f.W && py < f.H) {
@@ -334,56 +419,48 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
             }
         }
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) atomicMax(&s_max, m);
-        __syncthreads();
-        const int max_last = min(s_max, (int)list_len);  // n_contrib comes from the caller
-        const int warp_last = m;  // entries past it are skipped by the whole warp
-        for (int end = max_last; end > 0; end -= BATCH) {
-            const int begin = max(0, end - BATCH);
-            const int cnt = end - begin;
-            for (int e = tid; e < cnt; e += kThreads) {
-                const unsigned idx = c.sorted[st + begin + e];
-                s_idx[e] = idx;
-                stage_splat(rec, idx, s_a[e], s_q[e], s_c[e], s_box[e]);
-            }
-            for (int e = tid; e < 9 * BATCH; e += kThreads) (&s_g[0][0])[e] = 0.f;
-            __syncthreads();
-            // 32 entries at a time from the top: each lane tests one box against the warp's
-            // block, and the warp then visits only the entries that hit, in reverse list order
-            const int jtop = min(cnt, warp_last - begin);
-            for (int j0 = (jtop - 1) & ~31; j0 >= 0; j0 -= 32) {
-                const int jl = j0 + lane;
-                unsigned hits = __ballot_sync(0xffffffffu, jl < jtop && !box_misses(s_box[jl], bx0, bx1, by0, by1));
-                while (hits) {
-                    const int bit = 31 - __clz(hits);
-                    hits &= ~(1u << bit);
-                    const int j = j0 + bit;
+        // n_contrib comes from the caller: entries past the list's end do not exist
+        const int top = min(m, (int)list_len);
+        // batches from the top: [top - BATCH, top), [top - 2 BATCH, top - BATCH), ...; the slots
+        // of a batch cut at 0 start at the batch's nominal start (negative positions are empty)
+        Stage<S> g;
+        unsigned nidx[S];
+        load_idx<S>(c, top - BATCH, top, st, nidx);
+        load_rec<S>(rec, top - BATCH, top, nidx, g);
+        load_idx<S>(c, top - 2 * BATCH, top - BATCH, st, nidx);
+        for (int end = top; end > 0; end -= BATCH) {
+            const int begin = end - BATCH;
+            unsigned hit[S];
+            __syncwarp();  // the previous batch's slots are no longer read
+            commit<S>(g, begin, end, wa, wq, wc, widx, bx0, bx1, by0, by1, hit);
+            load_rec<S>(rec, begin - BATCH, begin, nidx, g);
+            load_idx<S>(c, begin - 2 * BATCH, begin - BATCH, st, nidx);
+            __syncwarp();
+#pragma unroll
+            for (int q = S - 1; q >= 0; --q) {
+                unsigned hm = hit[q];
+                while (hm) {
+                    const int bit = 31 - __clz(hm);
+                    hm &= ~(1u << bit);
+                    const int j = 32 * q + bit;
                     const int pos = begin + j + 1;
-                    const float4 A = s_a[j], Cc = s_c[j];
-                    const float2 Q = s_q[j];
+                    const float4 A = wa[j], Cc = wc[j];
+                    const float2 Q = wq[j];
                     float v[9];
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) v[q] = 0.f;
-                    bool any = accumulate(p[0], pos, A, Q, Cc, v);
-                    any |= accumulate(p[1], pos, A, Q, Cc, v);
+                    for (int k = 0; k < 9; ++k) v[k] = 0.f;
+                    bool any = false;
+#pragma unroll
+                    for (int h = 0; h < PXL; ++h) any |= accumulate(p[h], pos, A, Q, Cc, v);
                     if (__any_sync(0xffffffffu, any)) {
                         float mine, v8;
                         warp_reduce9(v, lane, mine, v8);
-                        if ((lane & 3) == 0) atomicAdd(&s_g[j][lane >> 2], mine);
-                        if (lane == 0) atomicAdd(&s_g[j][8], v8);
+                        float *dst = g2 + (size_t)widx[j] * kG2Floats;
+                        if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), mine);
+                        if (lane == 0) atomicAdd(dst + 8, v8);
                     }
                 }
             }
-            __syncthreads();
-            for (int e = tid; e < cnt; e += kThreads) {
-                float *dst = g2 + (size_t)s_idx[e] * kG2Floats;
-#pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const float x = s_g[e][q];
-                    if (x != 0.f) atomicAdd(dst + q, x);
-                }
-            }
-            __syncthreads();
         }
     }
 }
@@ -407,16 +484,18 @@ int persistent_grid(K kernel, int sms_hint, int threads) {
 template <int TW, int BATCH>
 cudaError_t fwd_inst(const Ctx &c, int grid, float *img, float *T, int *n, const float *tg, int lk,
                      float *dl, cudaStream_t s) {
-    const int g = persistent_grid(k_render_fwd<TW, BATCH>, grid, kTilePix);
-    k_render_fwd<TW, BATCH><<<g, kTilePix, 0, s>>>(c, img, T, n, tg, lk, dl);
+    const int g = persistent_grid(k_render_fwd<TW, BATCH>, grid, 32 * kWarpsPerCta);
+    k_render_fwd<TW, BATCH><<<g, 32 * kWarpsPerCta, 0, s>>>(c, img, T, n, tg, lk, dl);
     return cudaGetLastError();
 }
+
+constexpr int kBwdPixPerLane = 2;
 
 template <int TW, int BATCH>
 cudaError_t bwd_inst(const Ctx &c, int grid, const float *dl, const float *T, const int *n,
                      cudaStream_t s) {
-    const int g = persistent_grid(k_render_bwd<TW, BATCH>, grid, kThreads);
-    k_render_bwd<TW, BATCH><<<g, kThreads, 0, s>>>(c, dl, T, n);
+    const int g = persistent_grid(k_render_bwd<TW, BATCH, kBwdPixPerLane>, grid, 32 * kWarpsPerCta);
+    k_render_bwd<TW, BATCH, kBwdPixPerLane><<<g, 32 * kWarpsPerCta, 0, s>>>(c, dl, T, n);
     return cudaGetLastError();
 }
 
