@@ -94,7 +94,7 @@ typedef struct {
     const float *fparams;       /* device [n_frames][RGBA_FP_STRIDE] */
     float *grad_psi;            /* device [n_frames][k_stride] or NULL, overwritten */
     int32_t tile_w, tile_h;     /* screen tile shape: 16x16 or 8x32 (tile_w * tile_h == 256) */
-    int32_t smem_batch;         /* Gaussians staged per shared-memory round: 64, 128 or 256 */
+    int32_t smem_batch;         /* list entries a compositing warp stages per step: 64, 128 or 256 (0: 64) */
 } rgba_batch;
 
 typedef struct {

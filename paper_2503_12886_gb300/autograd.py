@@ -93,7 +93,7 @@ class RasterizeBlendFn(torch.autograd.Function):
         return (None, None, None, db.grad_psi, None, *grads)
 
 
-def rasterize(renderer: Renderer, frames, psi, fparams, models, tile=(16, 16), smem_batch=256):
+def rasterize(renderer: Renderer, frames, psi, fparams, models, tile=(16, 16), smem_batch=64):
     """Differentiable batched render.
 
     frames: list of (model index, width, height); psi [B][k_stride]; fparams [B][20];

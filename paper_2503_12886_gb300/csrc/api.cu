@@ -51,7 +51,7 @@ int make_plan(const rgba_batch *b, Plan &p) {
     if (tw == 0 && th == 0) tw = th = 16;
     if (!((tw == 16 && th == 16) || (tw == 8 && th == 32)))
         return fail(RGBA_ERR_INVALID_ARG, "tile shape must be 16x16 or 8x32");
-    int sb = b->smem_batch == 0 ? 256 : b->smem_batch;
+    int sb = b->smem_batch == 0 ? 64 : b->smem_batch;
     if (sb != 64 && sb != 128 && sb != 256)
         return fail(RGBA_ERR_INVALID_ARG, "smem_batch must be 64, 128 or 256");
     const int M = b->n_frames > 0 ? b->n_models : 0;

@@ -8,7 +8,7 @@ for T training steps with Adam, reaching the state a training benchmark times; t
 then those images (else seeded U[0,1] images). One sizing step (grows the workspace to the pair
 count), then N rgba_step calls, each one launch sequence of the whole hot path plus its single
 host synchronisation. Prints per-stage device times of the last step (CUDA events) as one JSON
-line.
+line. The profiled steps run inside the NVTX range "profiled".
 """
 from __future__ import annotations
 
@@ -38,7 +38,7 @@ def main():
     p.add_argument("--workload", default="batched")
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--tile", default="16x16")
-    p.add_argument("--smem-batch", type=int, default=256)
+    p.add_argument("--smem-batch", type=int, default=64)
     p.add_argument("--train", type=int, default=0)
     a = p.parse_args()
     tw, th = (int(x) for x in a.tile.split("x"))
@@ -60,10 +60,12 @@ def main():
     out = r.step(db, tg, api.RGBA_LOSS_L1, img)
     wall = []
     api.rgba_profile_enable(r.ctx, True)
+    torch.cuda.nvtx.range_push("profiled")  # ncu --nvtx --nvtx-include profiled/ selects these steps
     for _ in range(a.steps):
         t0 = time.perf_counter()
         out = r.step(db, tg, api.RGBA_LOSS_L1, img)
         wall.append(time.perf_counter() - t0)
+    torch.cuda.nvtx.range_pop()
     prof = api.rgba_profile_read(r.ctx)
     r.close()
     print(json.dumps({"workload": a.workload, "frames": db.n_frames, "pairs": out.pairs,

@@ -31,7 +31,7 @@ class DeviceModel:
 class DeviceBatch:
     """A synth.Batch resident on one CUDA device, plus the ABI descriptor that points at it."""
 
-    def __init__(self, batch: synth.Batch, device="cuda", tile=(16, 16), smem_batch=256,
+    def __init__(self, batch: synth.Batch, device="cuda", tile=(16, 16), smem_batch=64,
                  grads=True, models: list[DeviceModel] | None = None):
         self.device = torch.device(device)
         if models is None:

@@ -62,7 +62,7 @@ class _Slot:
 class Server:
     def __init__(self, avatars: list[synth.Model], device: int = 0, hbm_budget: float = 40e9,
                  max_frames: int = 32, slots: int = 2, max_res: int = 1024, tile=(16, 16),
-                 smem_batch: int = 256, pairs_per_gaussian: float = 4.0):
+                 smem_batch: int = 64, pairs_per_gaussian: float = 4.0):
         self.device = device
         dev = f"cuda:{device}"
         self.r = Renderer(device)

@@ -23,7 +23,7 @@ AMBIG_EPS = 1e-5
 AMBIG_EPS_T = 1e-4
 
 
-def run_gpu_forward(batch: synth.Batch, tile=(16, 16), smem_batch=256, renderer=None):
+def run_gpu_forward(batch: synth.Batch, tile=(16, 16), smem_batch=64, renderer=None):
     r = renderer or Renderer(0)
     db = DeviceBatch(batch, "cuda:0", tile=tile, smem_batch=smem_batch)
     img, T, n = r.forward(db)
@@ -137,7 +137,7 @@ def oracle_fwd_bwd(batch, targets, kind, tile=(16, 16)):
     return ores, L, dls, per_model, dpsi, g2s
 
 
-def gpu_step(batch, targets, kind, tile=(16, 16), smem_batch=256, renderer=None):
+def gpu_step(batch, targets, kind, tile=(16, 16), smem_batch=64, renderer=None):
     r = renderer or Renderer(0)
     db = DeviceBatch(batch, "cuda:0", tile=tile, smem_batch=smem_batch)
     tg = db.pack_images(targets)

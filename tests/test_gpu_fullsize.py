@@ -40,7 +40,7 @@ def _block_mask(fr, ores_f, TW, TH, size=4):
 
 def test_batched_workload_full_size(renderer):
     batch = synth.workload_batched()           # N=60,000, K=32, B=16, 512x512
-    db = DeviceBatch(batch, "cuda:0", tile=(16, 16), smem_batch=256)
+    db = DeviceBatch(batch, "cuda:0", tile=(16, 16), smem_batch=64)
     img, T, n = renderer.forward(db)
     torch.cuda.synchronize()
     inter = read_intermediates(renderer, db)
@@ -97,7 +97,7 @@ class _view_batch:
 
 def test_uneven_workload_sampled_frames(renderer):
     batch = synth.workload_uneven()            # 8 avatars N 20k..100k, 64 frames 256/512/1024
-    db = DeviceBatch(batch, "cuda:0", tile=(16, 16), smem_batch=256, grads=False)
+    db = DeviceBatch(batch, "cuda:0", tile=(16, 16), smem_batch=64, grads=False)
     img, T, n = renderer.forward(db)
     torch.cuda.synchronize()
     inter = read_intermediates(renderer, db)

@@ -71,14 +71,14 @@ def dense_batch():
 
 
 CASES = {
-    "single_128": (lambda: synth.workload_single(), (16, 16), 256),
+    "single_128": (lambda: synth.workload_single(), (16, 16), 64),
     "gradcheck_64": (lambda: synth.workload_gradcheck(), (16, 16), 256),
     "gradcheck_paper_mask": (lambda: synth.workload_gradcheck(mask=synth.MASK_PAPER), (16, 16), 128),
-    "batched_reduced": (lambda: synth.workload_batched(n=20_000, k=32, frames=4, res=256), (16, 16), 256),
+    "batched_reduced": (lambda: synth.workload_batched(n=20_000, k=32, frames=4, res=256), (16, 16), 64),
     "ragged_8x32": (ragged_batch, (8, 32), 64),
     "uneven": (uneven_batch, (16, 16), 128),
-    "depth_ties": (ties_batch, (16, 16), 256),
-    "dense_lists": (dense_batch, (16, 16), 256),
+    "depth_ties": (ties_batch, (16, 16), 128),
+    "dense_lists": (dense_batch, (16, 16), 64),
 }
 
 
