@@ -465,10 +465,10 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
     }
 }
 
-// Persistent grid: every CTA the SMs can hold at once (occupancy query, cached per kernel).
+// Persistent grid: every CTA the SMs can hold at once (occupancy query, cached by the caller
+// per kernel instance: all instances of a template share one function type).
 template <typename K>
-int persistent_grid(K kernel, int sms_hint, int threads) {
-    static int cached = 0;
+int persistent_grid(K kernel, int sms_hint, int threads, int &cached) {
     if (!cached) {
         int per_sm = 0, dev = 0, sms = sms_hint;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
@@ -484,7 +484,8 @@ int persistent_grid(K kernel, int sms_hint, int threads) {
 template <int TW, int BATCH>
 cudaError_t fwd_inst(const Ctx &c, int grid, float *img, float *T, int *n, const float *tg, int lk,
                      float *dl, cudaStream_t s) {
-    const int g = persistent_grid(k_render_fwd<TW, BATCH>, grid, 32 * kWarpsPerCta);
+    static int cached = 0;
+    const int g = persistent_grid(k_render_fwd<TW, BATCH>, grid, 32 * kWarpsPerCta, cached);
     k_render_fwd<TW, BATCH><<<g, 32 * kWarpsPerCta, 0, s>>>(c, img, T, n, tg, lk, dl);
     return cudaGetLastError();
 }
@@ -494,7 +495,8 @@ constexpr int kBwdPixPerLane = 2;
 template <int TW, int BATCH>
 cudaError_t bwd_inst(const Ctx &c, int grid, const float *dl, const float *T, const int *n,
                      cudaStream_t s) {
-    const int g = persistent_grid(k_render_bwd<TW, BATCH, kBwdPixPerLane>, grid, 32 * kWarpsPerCta);
+    static int cached = 0;
+    const int g = persistent_grid(k_render_bwd<TW, BATCH, kBwdPixPerLane>, grid, 32 * kWarpsPerCta, cached);
     k_render_bwd<TW, BATCH, kBwdPixPerLane><<<g, 32 * kWarpsPerCta, 0, s>>>(c, dl, T, n);
     return cudaGetLastError();
 }
