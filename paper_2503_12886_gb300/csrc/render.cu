@@ -2,8 +2,8 @@
 // its exact reverse. The binning tile (16x16 or 8x32 pixels) fixes the lists; the compositing
 // work is split finer: every warp is an independent persistent worker that takes (tile, pixel
 // block) items from one counter, so the few heavy tiles of a face-centred frame spread over
-// many warps and no warp ever waits at a CTA barrier. A forward block is 8 x 4 pixels (one per
-// lane); a backward block 8 x 4 or 8 x 8 (two pixels per lane). A warp walks its tile's list in
+// many warps and no warp ever waits at a CTA barrier. A block is 8 x 4 pixels, one per lane (the
+// backward kernel also builds for 8 x 8 blocks, two pixels per lane). A warp walks its tile's list in
 // steps of BATCH entries: each lane stages BATCH / 32 of them into the warp's shared-memory
 // slots together with the box of the entry's alpha >= 1/255 ellipse, a ballot marks the entries
 // whose box meets the warp's block, and only those are visited, in list order (in reverse in
@@ -490,7 +490,7 @@ cudaError_t fwd_inst(const Ctx &c, int grid, float *img, float *T, int *n, const
     return cudaGetLastError();
 }
 
-constexpr int kBwdPixPerLane = 2;
+constexpr int kBwdPixPerLane = 1;  // 8 x 4 blocks: twice the items of 8 x 8, fewer registers
 
 template <int TW, int BATCH>
 cudaError_t bwd_inst(const Ctx &c, int grid, const float *dl, const float *T, const int *n,
