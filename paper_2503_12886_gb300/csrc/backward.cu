@@ -385,23 +385,31 @@ k_gauss_bwd(Ctx c, int max_k) {
 }
 
 // dpsi[b][k] = sum over chunks of the partials; zero for k >= the model's k.
-__global__ void k_dpsi_reduce(Ctx c) {
-    const int b = blockIdx.x;
+constexpr int kDpsiThreads = 256;
+
+// One CTA per (blendshape k, frame b): the CTA's threads stride over the chunk partials, then
+// a warp-shuffle and shared-memory sum.
+__global__ void __launch_bounds__(kDpsiThreads) k_dpsi_reduce(Ctx c) {
+    __shared__ float s_w[kDpsiThreads / 32];
+    const int kk = blockIdx.x, b = blockIdx.y;
     const FrameInfo &f = c.frames[b];
     const ModelInfo &m = c.models[f.model];
-    // position of frame b in its model's frame list
-    int j = 0;
-    for (int q = 0; q < m.nb; ++q)
-        if (c.mframes[m.frame_off + q] == b) j = q;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int kk = warp; kk < c.k_stride; kk += nw) {
-        float s = 0.f;
-        if (kk < m.k) {
-            const float *p = c.dpsi_part + m.dpsi_off + ((long long)j * m.k + kk) * m.n_chunks;
-            for (int q = lane; q < m.n_chunks; q += 32) s += p[q];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        }
-        if (lane == 0) c.grad_psi[(size_t)b * c.k_stride + kk] = s;
+    float s = 0.f;
+    if (kk < m.k) {
+        // position of frame b in its model's frame list
+        int j = 0;
+        for (int q = 0; q < m.nb; ++q)
+            if (c.mframes[m.frame_off + q] == b) j = q;
+        const float *p = c.dpsi_part + m.dpsi_off + ((long long)j * m.k + kk) * m.n_chunks;
+        for (int q = threadIdx.x; q < m.n_chunks; q += kDpsiThreads) s += p[q];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < kDpsiThreads / 32; ++w) t += s_w[w];
+        c.grad_psi[(size_t)b * c.k_stride + kk] = t;
     }
 }
 
@@ -429,8 +437,8 @@ cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_n, int max_k,
 
 cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s) {
     (void)max_k;
-    if (!c.grad_psi || c.B == 0) return cudaSuccess;
-    k_dpsi_reduce<<<c.B, 256, 0, s>>>(c);
+    if (!c.grad_psi || c.B == 0 || c.k_stride == 0) return cudaSuccess;
+    k_dpsi_reduce<<<dim3(c.k_stride, c.B), kDpsiThreads, 0, s>>>(c);
     return cudaGetLastError();
 }
 
