@@ -56,9 +56,11 @@ def lib():
             L.orc_blend_bwd.argtypes = [i32, i32, i32, u32, P, i32, P, P, P, P, P]
             L.orc_exp_spec.argtypes = [C.c_float]
             L.orc_exp_spec.restype = C.c_float
-            L.orc_decide.argtypes = [i32, i32, i32, u32, P, P, P, P, i32, i32, i32, i32, P, P]
-            L.orc_project.argtypes = [i32, i32, P, P, i32, i32, P, P]
-            L.orc_project_bwd.argtypes = [i32, i32, P, P, i32, i32, P, P, P]
+            L.orc_decide.argtypes = [i32, i32, i32, u32, P, P, P, P, i32, i32, i32, i32, P, P,
+                                     P, P, P, P, P]
+            L.orc_project.argtypes = [i32, i32, P, P, i32, i32, P, P, P]
+            L.orc_project_bwd.argtypes = [i32, i32, P, P, i32, i32, P, P, P, P]
+            L.orc_tbn_all.argtypes = [i32, i32, P, P, P, P, P, P]
             L.orc_bin.argtypes = [i32, P, P, i32, i32, P, P]
             L.orc_bin.restype = C.c_int64
             L.orc_render.argtypes = [i32, i32, i32, i32, P, P, P, P, P, f64, f64, P, P, P, P, P]
@@ -90,9 +92,29 @@ def blend(g0: np.ndarray, dg: np.ndarray, psi: np.ndarray, n: int, mask: int) ->
     return out
 
 
-def decide(g0, dg, psi, fp, n, mask, W, H, TW=16, TH=16):
+def _bind_args(binding, verts):
+    if binding is None:
+        return [None] * 5, None
+    arrs = [np.ascontiguousarray(binding.faces, np.int32), np.ascontiguousarray(binding.face_uv, np.float32),
+            np.ascontiguousarray(binding.face_of, np.int32), np.ascontiguousarray(binding.bary, np.float32),
+            np.ascontiguousarray(verts, np.float32)]
+    return [_p(a) for a in arrs], arrs
+
+
+def tbn(binding, verts, n):
+    """FP64 TBN matrix and barycentric point per Gaussian (Alg. 1): [n][12] = R row-major
+    (columns T, B, N), then t."""
+    ptrs, keep = _bind_args(binding, verts)
+    out = np.zeros((n, 12), np.float64)
+    lib().orc_tbn_all(n, binding.bary.shape[1], *ptrs, _p(out))
+    return out
+
+
+def decide(g0, dg, psi, fp, n, mask, W, H, TW=16, TH=16, binding=None, verts=None):
     """FP32 decision spec per Gaussian: rect[n][4] (int32) and f32[n][8] =
-    (u, v, conic a, b, c, radius, depth, opacity)."""
+    (u, v, conic a, b, c, radius, depth, opacity). With a binding the mean and covariance are
+    first mapped from tangent space by the frame mesh `verts`."""
+    ptrs, keep = _bind_args(binding, verts)
     g0 = np.ascontiguousarray(g0, np.float32)
     dg = np.ascontiguousarray(dg, np.float32)
     psi = np.ascontiguousarray(psi, np.float32)
@@ -100,24 +122,26 @@ def decide(g0, dg, psi, fp, n, mask, W, H, TW=16, TH=16):
     rect = np.zeros((n, 4), np.int32)
     f32 = np.zeros((n, 8), np.float32)
     lib().orc_decide(n, g0.shape[1], dg.shape[0], mask, _p(g0), _p(dg), _p(psi), _p(fp), W, H,
-                     TW, TH, _p(rect), _p(f32))
+                     TW, TH, _p(rect), _p(f32), *ptrs)
     return rect, f32
 
 
-def project(blended, fp, n, W, H, rect):
-    """FP64 render records [n][12] = (u, v, conic a, b, c, opacity, r, g, b, depth, 0, 0)."""
+def project(blended, fp, n, W, H, rect, tbn64=None):
+    """FP64 render records [n][12] = (u, v, conic a, b, c, opacity, r, g, b, depth, 0, 0);
+    tbn64 ([n][12] from tbn()) maps bound Gaussians from tangent space."""
     out = np.zeros((n, 12), np.float64)
     fp64 = np.ascontiguousarray(fp, np.float64)
-    lib().orc_project(n, blended.shape[1], _p(blended), _p(fp64), W, H, _p(rect), _p(out))
+    lib().orc_project(n, blended.shape[1], _p(blended), _p(fp64), W, H, _p(rect), _p(out),
+                      _p(tbn64))
     return out
 
 
-def project_bwd(blended, fp, n, W, H, rect, grad2d):
+def project_bwd(blended, fp, n, W, H, rect, grad2d, tbn64=None):
     dG = np.zeros_like(blended)
     fp64 = np.ascontiguousarray(fp, np.float64)
     g2 = np.ascontiguousarray(grad2d, np.float64)
     lib().orc_project_bwd(n, blended.shape[1], _p(blended), _p(fp64), W, H, _p(rect), _p(g2),
-                          _p(dG))
+                          _p(dG), _p(tbn64))
     return dG
 
 
@@ -189,6 +213,7 @@ class FrameResult:
     flags: np.ndarray | None = None
     hash: int = 0
     stats: np.ndarray | None = None
+    tbn64: np.ndarray | None = None
 
 
 def forward(batch, tile=(16, 16), render_frames=None, tile_masks=None, eps=1e-5,
@@ -216,9 +241,10 @@ def forward(batch, tile=(16, 16), render_frames=None, tile_masks=None, eps=1e-5,
         fp = batch.fparams[b]
         W, H = fr.width, fr.height
         rect, f32 = decide(g0.astype(np.float32), dg.astype(np.float32), psi.astype(np.float32),
-                           fp, m.n, m.mask, W, H, TW, TH)
+                           fp, m.n, m.mask, W, H, TW, TH, m.binding, fr.verts)
         bl = blend(g0, dg, psi, m.n, m.mask)
-        rec = project(bl, fp, m.n, W, H, rect)
+        t64 = None if m.binding is None else tbn(m.binding, fr.verts, m.n)
+        rec = project(bl, fp, m.n, W, H, rect, t64)
         if splat == "spec":
             kept = (rect[:, 2] > rect[:, 0]) & (rect[:, 3] > rect[:, 1])
             rec[kept, 0:5] = f32[kept, 0:5]
@@ -227,7 +253,7 @@ def forward(batch, tile=(16, 16), render_frames=None, tile_masks=None, eps=1e-5,
             raise ValueError(splat)
         tx, ty = (W + TW - 1) // TW, (H + TH - 1) // TH
         ts, lst = bin_sort(rect, f32[:, 6], tx, ty)
-        fr_res = FrameResult(rect, f32, bl, rec, ts, lst)
+        fr_res = FrameResult(rect, f32, bl, rec, ts, lst, tbn64=t64)
         if do_render and (render_frames is None or b in render_frames):
             tm = None if tile_masks is None else tile_masks.get(b)
             bg = fp[17:20].astype(np.float64)
@@ -269,7 +295,7 @@ def backward(batch, res, dL_dimg, tile=(16, 16), tile_masks=None, params=None):
         tm = None if tile_masks is None else tile_masks.get(b)
         g2 = render_bwd(fr.width, fr.height, TW, TH, r.rec, r.tile_start, r.lst,
                         fp[17:20].astype(np.float64), dL_dimg[b], m.n, tm)
-        dgb = project_bwd(r.blended, fp, m.n, fr.width, fr.height, r.rect, g2)
+        dgb = project_bwd(r.blended, fp, m.n, fr.width, fr.height, r.rect, g2, r.tbn64)
         g2s.append(g2)
         dgbs.append(dgb)
     per_model = []

@@ -28,6 +28,14 @@
  * sqrt, fused multiply-add where written, floor/ceil/rint), so that any conforming
  * implementation of the same sequence produces the same bits. Build with -ffp-contract=off.
  *
+ * Tangent space (Supp. "Gaussian Transformation", Alg. 1), optional per model: a Gaussian bound
+ * to triangle f of a mesh with UV atlas has its mean and rotation in the triangle's tangent
+ * space. Per frame the mesh is deformed; the triangle's TBN matrix R = [T B N] (T and B the
+ * derivatives of position along u and v, N the unit normal) and the barycentric point t of the
+ * Gaussian's UV sample map the Gaussian to deformed space: x^D = R x^T + t, covariance
+ * R Sigma^T R^T (the image of the Gaussian under x -> R x + t; this is the rotation q^D = R q^T
+ * whenever R is orthonormal).
+ *
  * Channel layout (planar [14][n_pad]): 0..2 mean, 3..6 quaternion (w,x,y,z), 7..9 log-scale,
  * 10 opacity logit, 11..13 RGB. Frame block [20]: 3x4 world->camera view matrix (row-major),
  * fx, fy, cx, cy, near, background RGB.
@@ -150,9 +158,62 @@ float orc_exp_spec(float x) {
  * block. Outputs: rect[4] = (x0, y0, x1, y1) half-open tile rectangle, all zero when culled;
  * f32[8] = (u, v, conic a, conic b, conic c, radius, depth, opacity) as computed by the spec
  * (radius = 0 when culled). Returns 1 when the Gaussian is kept.                               */
+/* S1b (bound models only) the TBN matrix of Gaussian i's triangle (Alg. 1) and its barycentric
+ * point, FP32 spec. With e1 = v1 - v0, e2 = v2 - v0 and UV differences (du1, dv1), (du2, dv2):
+ * e1 = du1 T + dv1 B, e2 = du2 T + dv2 B, so T = (dv2 e1 - dv1 e2) / det and
+ * B = (du1 e2 - du2 e1) / det with det = du1 dv2 - dv1 du2; N = (e1 x e2) / |e1 x e2|.
+ * R[c] = (T_c, B_c, N_c); t_c = (b0 v0_c + b1 v1_c) + b2 v2_c. Every product and sum is
+ * rounded separately, in the order written.                                                    */
+static void tbn_spec(int i, int n_pad, const int32_t *faces, const float *face_uv,
+                     const int32_t *face_of, const float *bary, const float *verts,
+                     float R[3][3], float t[3]) {
+    int f = face_of[i];
+    const float *a = verts + 3 * (size_t)faces[3 * (size_t)f + 0];
+    const float *b = verts + 3 * (size_t)faces[3 * (size_t)f + 1];
+    const float *c = verts + 3 * (size_t)faces[3 * (size_t)f + 2];
+    const float *uv = face_uv + 6 * (size_t)f;
+    float e1[3], e2[3];
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = b[k] - a[k];
+        e2[k] = c[k] - a[k];
+    }
+    float du1 = uv[2] - uv[0], dv1 = uv[3] - uv[1], du2 = uv[4] - uv[0], dv2 = uv[5] - uv[1];
+    float p1 = du1 * dv2, p2 = dv1 * du2;
+    float det = p1 - p2;
+    float rd = 1.0f / det;
+    float n[3];
+    {
+        float q1 = e1[1] * e2[2], q2 = e1[2] * e2[1];
+        n[0] = q1 - q2;
+        q1 = e1[2] * e2[0];
+        q2 = e1[0] * e2[2];
+        n[1] = q1 - q2;
+        q1 = e1[0] * e2[1];
+        q2 = e1[1] * e2[0];
+        n[2] = q1 - q2;
+    }
+    float l2 = n[0] * n[0];
+    l2 = l2 + n[1] * n[1];
+    l2 = l2 + n[2] * n[2];
+    float len = sqrtf(l2);
+    float b0 = bary[i], b1 = bary[(size_t)n_pad + i], b2 = bary[2 * (size_t)n_pad + i];
+    for (int k = 0; k < 3; ++k) {
+        float x1 = dv2 * e1[k], x2 = dv1 * e2[k];
+        R[k][0] = (x1 - x2) * rd;
+        x1 = du1 * e2[k];
+        x2 = du2 * e1[k];
+        R[k][1] = (x1 - x2) * rd;
+        R[k][2] = n[k] / len;
+        float y = b0 * a[k];
+        y = y + b1 * b[k];
+        t[k] = y + b2 * c[k];
+    }
+}
+
 int orc_decide_one(int i, int n_pad, int k, unsigned mask, const float *g0, const float *dg,
                    const float *psi, const float *fp, int W, int H, int TW, int TH,
-                   int32_t *rect, float *f32) {
+                   int32_t *rect, float *f32, const int32_t *faces, const float *face_uv,
+                   const int32_t *face_of, const float *bary, const float *verts) {
     int A = popcount14(mask);
     float v[NCH];
     int a = 0;
@@ -168,6 +229,17 @@ int orc_decide_one(int i, int n_pad, int k, unsigned mask, const float *g0, cons
     }
     rect[0] = rect[1] = rect[2] = rect[3] = 0;
     for (int j = 0; j < 8; ++j) f32[j] = 0.0f;
+    /* S1b tangent -> deformed space: x_c = fmaf(N_c, x2, fmaf(B_c, x1, fmaf(T_c, x0, t_c))) */
+    float Rt[3][3], tt[3];
+    const int bound = faces != NULL;
+    if (bound) {
+        tbn_spec(i, n_pad, faces, face_uv, face_of, bary, verts, Rt, tt);
+        float xd[3];
+        for (int c = 0; c < 3; ++c) xd[c] = fmaf(Rt[c][2], v[2], fmaf(Rt[c][1], v[1], fmaf(Rt[c][0], v[0], tt[c])));
+        v[0] = xd[0];
+        v[1] = xd[1];
+        v[2] = xd[2];
+    }
     /* S2 view transform p_j = fmaf(V_j2, x2, fmaf(V_j1, x1, fmaf(V_j0, x0, V_j3))) */
     float p[3];
     for (int j = 0; j < 3; ++j)
@@ -205,6 +277,17 @@ int orc_decide_one(int i, int n_pad, int k, unsigned mask, const float *g0, cons
     for (int ii = 0; ii < 3; ++ii)
         for (int jj = 0; jj < 3; ++jj)
             Sg[ii][jj] = fmaf(Mm[ii][2], R[jj][2], fmaf(Mm[ii][1], R[jj][1], Mm[ii][0] * R[jj][0]));
+    /* S6b (bound) deformed-space covariance Rt Sigma Rt^T with P = Rt Sigma:
+     *    P_ij = fmaf(Rt_i2, S_2j, fmaf(Rt_i1, S_1j, Rt_i0 * S_0j)); S_ij = fmaf(P_i2, Rt_j2, ...) */
+    if (bound) {
+        float P[3][3];
+        for (int ii = 0; ii < 3; ++ii)
+            for (int jj = 0; jj < 3; ++jj)
+                P[ii][jj] = fmaf(Rt[ii][2], Sg[2][jj], fmaf(Rt[ii][1], Sg[1][jj], Rt[ii][0] * Sg[0][jj]));
+        for (int ii = 0; ii < 3; ++ii)
+            for (int jj = 0; jj < 3; ++jj)
+                Sg[ii][jj] = fmaf(P[ii][2], Rt[jj][2], fmaf(P[ii][1], Rt[jj][1], P[ii][0] * Rt[jj][0]));
+    }
     /* S7 camera covariance C = W Sigma W^T with T = W Sigma:
      *    T_ij = fmaf(W_i2, S_2j, fmaf(W_i1, S_1j, W_i0 * S_0j)); C_ij = fmaf(T_i2, W_j2, ...)    */
     float Tm[3][3], Cm[3][3];
@@ -280,25 +363,71 @@ int orc_decide_one(int i, int n_pad, int k, unsigned mask, const float *g0, cons
 
 void orc_decide(int n, int n_pad, int k, unsigned mask, const float *g0, const float *dg,
                 const float *psi, const float *fp, int W, int H, int TW, int TH, int32_t *rect,
-                float *f32) {
+                float *f32, const int32_t *faces, const float *face_uv, const int32_t *face_of,
+                const float *bary, const float *verts) {
     for (int i = 0; i < n; ++i)
         orc_decide_one(i, n_pad, k, mask, g0, dg, psi, fp, W, H, TW, TH, rect + 4 * (size_t)i,
-                       f32 + 8 * (size_t)i);
+                       f32 + 8 * (size_t)i, faces, face_uv, face_of, bary, verts);
+}
+
+/* FP64 TBN matrix and barycentric point of Gaussian i (Alg. 1; same definitions as tbn_spec):
+ * out[0..8] = R row-major (columns T, B, N), out[9..11] = t.                                   */
+void orc_tbn(int i, int n_pad, const int32_t *faces, const float *face_uv, const int32_t *face_of,
+             const float *bary, const float *verts, double *out) {
+    int f = face_of[i];
+    double a[3], b[3], c[3], e1[3], e2[3];
+    for (int k = 0; k < 3; ++k) {
+        a[k] = verts[3 * (size_t)faces[3 * (size_t)f + 0] + k];
+        b[k] = verts[3 * (size_t)faces[3 * (size_t)f + 1] + k];
+        c[k] = verts[3 * (size_t)faces[3 * (size_t)f + 2] + k];
+        e1[k] = b[k] - a[k];
+        e2[k] = c[k] - a[k];
+    }
+    const float *uv = face_uv + 6 * (size_t)f;
+    double du1 = (double)uv[2] - uv[0], dv1 = (double)uv[3] - uv[1];
+    double du2 = (double)uv[4] - uv[0], dv2 = (double)uv[5] - uv[1];
+    double det = du1 * dv2 - dv1 * du2;
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                   e1[0] * e2[1] - e1[1] * e2[0]};
+    double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    double bb[3] = {bary[i], bary[(size_t)n_pad + i], bary[2 * (size_t)n_pad + i]};
+    for (int k = 0; k < 3; ++k) {
+        out[3 * k + 0] = (dv2 * e1[k] - dv1 * e2[k]) / det;
+        out[3 * k + 1] = (du1 * e2[k] - du2 * e1[k]) / det;
+        out[3 * k + 2] = n[k] / len;
+        out[9 + k] = bb[0] * a[k] + bb[1] * b[k] + bb[2] * c[k];
+    }
+}
+
+void orc_tbn_all(int n, int n_pad, const int32_t *faces, const float *face_uv, const int32_t *face_of,
+                 const float *bary, const float *verts, double *out) {
+    for (int i = 0; i < n; ++i) orc_tbn(i, n_pad, faces, face_uv, face_of, bary, verts, out + 12 * (size_t)i);
 }
 
 /* ============================================================================================
  * 3. FP64 projection (3DGS preprocess; EWA splatting of Zwicker et al. 2001).
  * ========================================================================================== */
 typedef struct {
-    double p[3], qn[4], qlen, s[3], R[3][3], Sig[3][3], Mc[3][3], J[2][3];
+    double p[3], qn[4], qlen, s[3], R[3][3], Sig[3][3], Mc[3][3], J[2][3], Rt[3][3];
+    int bound;
     double rx, ry;
     int clx, cly;
     double A, B, C, det, conic[3], u, v, o, col[3];
 } fwd64;
 
-static void project64(const double *g, const double *fp, int W, int H, fwd64 *f) {
+/* tbn (bound models): [12] = TBN matrix R row-major, then t (orc_tbn); NULL when unbound.      */
+static void project64(const double *g, const double *fp, int W, int H, const double *tbn, fwd64 *f) {
     const double *V = fp;
     double x[3] = {g[0], g[1], g[2]};
+    f->bound = tbn != NULL;
+    if (f->bound) { /* x^D = R x^T + t */
+        double xd[3];
+        for (int c = 0; c < 3; ++c) {
+            for (int k = 0; k < 3; ++k) f->Rt[c][k] = tbn[3 * c + k];
+            xd[c] = tbn[3 * c] * x[0] + tbn[3 * c + 1] * x[1] + tbn[3 * c + 2] * x[2] + tbn[9 + c];
+        }
+        for (int c = 0; c < 3; ++c) x[c] = xd[c];
+    }
     for (int j = 0; j < 3; ++j)
         f->p[j] = V[4 * j] * x[0] + V[4 * j + 1] * x[1] + V[4 * j + 2] * x[2] + V[4 * j + 3];
     /* activations applied after blending (Supp. A.3) */
@@ -324,6 +453,17 @@ static void project64(const double *g, const double *fp, int W, int H, fwd64 *f)
             for (int m = 0; m < 3; ++m) acc += R[i][m] * f->s[m] * f->s[m] * R[j][m];
             f->Sig[i][j] = acc;
         }
+    if (f->bound) { /* deformed-space covariance Rt Sigma Rt^T */
+        double S[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double acc = 0;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) acc += f->Rt[i][a] * f->Sig[a][b] * f->Rt[j][b];
+                S[i][j] = acc;
+            }
+        memcpy(f->Sig, S, sizeof(S));
+    }
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
             double acc = 0;
@@ -367,7 +507,7 @@ static void project64(const double *g, const double *fp, int W, int H, fwd64 *f)
 /* Per-Gaussian render record: out[n][12] = (u, v, conic a, b, c, opacity, r, g, b, depth, 0, 0)
  * for Gaussians kept by the decision spec (rect area > 0); zeros otherwise.                    */
 void orc_project(int n, int n_pad, const double *blended, const double *fp, int W, int H,
-                 const int32_t *rect, double *out) {
+                 const int32_t *rect, double *out, const double *tbn) {
     double g[NCH];
     for (int i = 0; i < n; ++i) {
         double *o = out + 12 * (size_t)i;
@@ -376,7 +516,7 @@ void orc_project(int n, int n_pad, const double *blended, const double *fp, int 
         if ((rc[2] - rc[0]) * (rc[3] - rc[1]) <= 0) continue;
         for (int ch = 0; ch < NCH; ++ch) g[ch] = blended[(size_t)ch * n_pad + i];
         fwd64 f;
-        project64(g, fp, W, H, &f);
+        project64(g, fp, W, H, tbn ? tbn + 12 * (size_t)i : NULL, &f);
         o[0] = f.u;
         o[1] = f.v;
         o[2] = f.conic[0];
@@ -393,7 +533,7 @@ void orc_project(int n, int n_pad, const double *blended, const double *fp, int 
 /* Chain rule of the projection: grad2d[n][9] = dL/d(u, v, conic a, b, c, opacity, r, g, b)
  * -> dG[14][n_pad], the gradient w.r.t. the blended (pre-activation) channels.                 */
 void orc_project_bwd(int n, int n_pad, const double *blended, const double *fp, int W, int H,
-                     const int32_t *rect, const double *grad2d, double *dG) {
+                     const int32_t *rect, const double *grad2d, double *dG, const double *tbn) {
     double g[NCH];
     for (int i = 0; i < n; ++i) {
         for (int ch = 0; ch < NCH; ++ch) dG[(size_t)ch * n_pad + i] = 0.0;
@@ -401,7 +541,7 @@ void orc_project_bwd(int n, int n_pad, const double *blended, const double *fp, 
         if ((rc[2] - rc[0]) * (rc[3] - rc[1]) <= 0) continue;
         for (int ch = 0; ch < NCH; ++ch) g[ch] = blended[(size_t)ch * n_pad + i];
         fwd64 f;
-        project64(g, fp, W, H, &f);
+        project64(g, fp, W, H, tbn ? tbn + 12 * (size_t)i : NULL, &f);
         const double *gg = grad2d + 9 * (size_t)i;
         double du = gg[0], dv = gg[1], dca = gg[2], dcb = gg[3], dcc = gg[4], dop = gg[5];
         /* opacity: o = sigmoid(logit) */
@@ -441,6 +581,17 @@ void orc_project_bwd(int n, int n_pad, const double *blended, const double *fp, 
                     for (int b = 0; b < 3; ++b) acc += V[4 * a + r] * dM[a][b] * V[4 * b + c];
                 dS[r][c] = acc;
             }
+        if (f.bound) { /* Sigma^D = Rt Sigma^T Rt^T:  dSigma^T = Rt^T dSigma^D Rt */
+            double dT[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) {
+                    double acc = 0;
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) acc += f.Rt[a][r] * dS[a][b] * f.Rt[b][c];
+                    dT[r][c] = acc;
+                }
+            memcpy(dS, dT, sizeof(dT));
+        }
         /* Sig = R diag(s^2) R^T:  dR = 2 dS R diag(s^2),  ds_m = 2 s_m (R^T dS R)_mm */
         double dR[3][3], ds[3];
         for (int r = 0; r < 3; ++r)
@@ -493,8 +644,11 @@ void orc_project_bwd(int n, int n_pad, const double *blended, const double *fp, 
         } else {
             dp[2] += dJ[1][2] * (fy * f.ry / (pz * pz));
         }
-        for (int c = 0; c < 3; ++c)
-            dG[(size_t)c * n_pad + i] = V[c] * dp[0] + V[4 + c] * dp[1] + V[8 + c] * dp[2];
+        double dxw[3];
+        for (int c = 0; c < 3; ++c) dxw[c] = V[c] * dp[0] + V[4 + c] * dp[1] + V[8 + c] * dp[2];
+        for (int c = 0; c < 3; ++c) /* x^D = Rt x^T + t:  dx^T = Rt^T dx^D */
+            dG[(size_t)c * n_pad + i] =
+                f.bound ? f.Rt[0][c] * dxw[0] + f.Rt[1][c] * dxw[1] + f.Rt[2][c] * dxw[2] : dxw[c];
     }
 }
 

@@ -94,6 +94,19 @@ def blended_channels(mask: int) -> list[int]:
 
 
 @dataclass
+class Binding:
+    """Tangent-space binding of a model's Gaussians to a triangle mesh with a UV atlas (Supp.
+    "Gaussian Transformation", Alg. 1). Each Gaussian stays on one triangle, at the barycentric
+    point of its UV sample; its mean (channels 0..2) and rotation live in that triangle's
+    tangent space (u, v, normal)."""
+    faces: np.ndarray    # int32 [F][3] vertex indices
+    face_uv: np.ndarray  # float32 [F][6] (u, v) of corners 0, 1, 2
+    face_of: np.ndarray  # int32 [n] triangle of each Gaussian
+    bary: np.ndarray     # float32 [3][n_pad] barycentric weights of each Gaussian's UV sample
+    n_verts: int
+
+
+@dataclass
 class Model:
     """One avatar: base Gaussians G0 and K blendshape deltas (Eq. 1)."""
     n: int
@@ -101,6 +114,7 @@ class Model:
     mask: int
     g0: np.ndarray      # float32 [14][n_pad]
     dg: np.ndarray      # float32 [k][A][n_pad]
+    binding: Binding | None = None
 
     @property
     def n_pad(self) -> int:
@@ -116,6 +130,7 @@ class Frame:
     model: int
     width: int
     height: int
+    verts: np.ndarray | None = None  # float32 [V][3]: this frame's deformed mesh (bound models)
 
 
 @dataclass
@@ -241,7 +256,7 @@ def reference_avatar(model: Model, seed: int) -> Model:
     n = model.n
     g0[11:14, :n] += (0.1 * Stream(seed, 40).normal(3 * n)).reshape(3, n).astype(np.float32)
     g0[0:3, :n] += (1e-3 * Stream(seed, 41).normal(3 * n)).reshape(3, n).astype(np.float32)
-    return Model(n=model.n, k=model.k, mask=model.mask, g0=g0, dg=model.dg.copy())
+    return Model(n=model.n, k=model.k, mask=model.mask, g0=g0, dg=model.dg.copy(), binding=model.binding)
 
 
 def make_targets(batch: Batch, seed: int) -> list[np.ndarray]:
@@ -256,6 +271,90 @@ def make_targets(batch: Batch, seed: int) -> list[np.ndarray]:
 
 # ---------------------------------------------------------------------------------------------
 # The five workloads (synthetic stand-ins for the paper's INSTA / GaussianBlendShapes captures).
+
+@dataclass
+class Mesh:
+    """A head mesh with a UV atlas and an expression basis (stands in for the tracked 3DMM mesh
+    of the paper, Sec. 3.1 and Supp. "Gaussian Transformation")."""
+    verts: np.ndarray    # float32 [V][3] neutral shape
+    faces: np.ndarray    # int32 [F][3]
+    face_uv: np.ndarray  # float32 [F][6]
+    dverts: np.ndarray   # float32 [E][V][3] expression displacement basis
+
+
+def make_head_mesh(seed: int, n_lat: int = 48, n_lon: int = 96, radii=(0.09, 0.12, 0.10),
+                   n_expr: int = 10, amp: float = 4e-3, theta=(0.06 * math.pi, 0.94 * math.pi)) -> Mesh:
+    """Ellipsoid head mesh (radii as the volume avatars) with a latitude-longitude UV atlas.
+
+    Vertex rows at polar angles theta_i in [theta0, theta1] from the +y axis, n_lon + 1 columns
+    at azimuth phi_j = 2 pi j / n_lon (the seam column is duplicated so UVs stay continuous):
+    position (rx sin th cos ph, ry cos th, rz sin th sin ph), UV (phi / 2 pi, (th - th0) /
+    (th1 - th0)); two triangles per grid quad. 48 x 96 gives 4,656 vertices and 9,024 triangles
+    (the FLAME head has 5,023 and 9,976). Expression basis: E smooth normal displacements
+    amp cos(k_e . x + phase_e) n(x), wave vectors with |k| U[20, 60] rad/m, random direction.
+    """
+    rx, ry, rz = radii
+    th = theta[0] + (theta[1] - theta[0]) * np.arange(n_lat) / (n_lat - 1)
+    ph = 2.0 * math.pi * np.arange(n_lon + 1) / n_lon
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    pos = np.stack([rx * np.sin(T) * np.cos(P), ry * np.cos(T), rz * np.sin(T) * np.sin(P)], -1)
+    uv = np.stack([P / (2.0 * math.pi), (T - theta[0]) / (theta[1] - theta[0])], -1)
+    pos = pos.reshape(-1, 3)
+    uv = uv.reshape(-1, 2)
+    cols = n_lon + 1
+    faces = []
+    for i in range(n_lat - 1):
+        for j in range(n_lon):
+            a = i * cols + j
+            b, c = a + 1, a + cols
+            faces.append((a, c, b))
+            faces.append((b, c, c + 1))
+    faces = np.asarray(faces, np.int32)
+    face_uv = uv[faces].reshape(-1, 6)
+    nrm = pos / np.asarray(radii) ** 2
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    st = Stream(seed, 40)
+    d = st.normal(3 * n_expr).reshape(n_expr, 3)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    kmag = 20.0 + 40.0 * st.uniform(n_expr)
+    phase = 2.0 * math.pi * st.uniform(n_expr)
+    dverts = np.stack([amp * np.cos(pos @ (kmag[e] * d[e]) + phase[e])[:, None] * nrm
+                       for e in range(n_expr)])
+    return Mesh(pos.astype(np.float32), faces, face_uv.astype(np.float32), dverts.astype(np.float32))
+
+
+def frame_verts(mesh: Mesh, seed: int, frame: int) -> np.ndarray:
+    """A frame's deformed mesh: neutral + sum_e w_e dverts_e with w ~ N(0, 1) per frame."""
+    w = Stream(seed, 1000 + frame).normal(mesh.dverts.shape[0])
+    return (mesh.verts.astype(np.float64) +
+            np.tensordot(w, mesh.dverts.astype(np.float64), 1)).astype(np.float32)
+
+
+def make_bound_model(seed: int, n: int, k: int, mesh: Mesh, mask: int = MASK_MEAN_SCALE_COLOR,
+                     sd_mean=(2e-3, 3e-3, 1e-3), log_scale_mu=math.log(4e-3), log_scale_sd=0.3) -> Model:
+    """Synthetic avatar in the tangent space of `mesh` (Sec. 3.1 "Initialization": positions
+    sampled across the UV map). Each Gaussian takes a uniformly random triangle (all triangles
+    of the grid atlas have the same UV area, so this is uniform over the UV map) and a uniform
+    point in it (barycentric weights 1 - sqrt(r1), sqrt(r1)(1 - r2), sqrt(r1) r2). Tangent-space
+    mean offsets N(0, sd_mean) in (u, v, normal) units, log-scales N(log 4e-3, 0.3) in the same
+    units; rotations, opacity, colours and deltas as make_model."""
+    m = make_model(seed, n, k, mask=mask, log_scale_mu=log_scale_mu, log_scale_sd=log_scale_sd)
+    npad = m.n_pad
+    st = Stream(seed, 50)
+    face_of = (st.uniform(n) * mesh.faces.shape[0]).astype(np.int32)
+    r1, r2 = st.uniform(n), st.uniform(n)
+    sq = np.sqrt(r1)
+    bary = np.zeros((3, npad), np.float32)
+    bary[0, :n] = 1.0 - sq
+    bary[1, :n] = sq * (1.0 - r2)
+    bary[2, :n] = sq * r2
+    g0 = m.g0.copy()
+    off = Stream(seed, 51).normal(3 * n).reshape(3, n)
+    for c in range(3):
+        g0[c, :n] = (sd_mean[c] * off[c]).astype(np.float32)
+    b = Binding(mesh.faces, mesh.face_uv, face_of, bary, mesh.verts.shape[0])
+    return Model(n=n, k=k, mask=mask, g0=g0, dg=m.dg, binding=b)
+
 
 def workload_single(seed: int = 1000) -> Batch:
     """N=10,000, K=20, one 128x128 frame, fx=fy=150, camera at z=-1 m, bg 0."""
@@ -275,6 +374,17 @@ def workload_batched(seed: int = 3000, n: int = 60_000, k: int = 32, frames: int
     m = make_model(seed, n, k)
     return make_batch([m], [Frame(0, res, res) for _ in range(frames)], seed,
                       jitter_deg=20.0, random_bg=True)
+
+
+def workload_tangent(seed: int = 6000, n: int = 60_000, k: int = 32, frames: int = 16,
+                     res: int = 512, n_lat: int = 48, n_lon: int = 96) -> Batch:
+    """The batched workload in tangent space: N Gaussians bound to a head mesh (48 x 96 grid:
+    9,024 triangles) whose expression changes per frame; K blendshapes, B frames, yaw/pitch
+    jitter U[-20,20] deg, random bg."""
+    mesh = make_head_mesh(seed, n_lat, n_lon)
+    m = make_bound_model(seed, n, k, mesh)
+    fr = [Frame(0, res, res, frame_verts(mesh, seed, f)) for f in range(frames)]
+    return make_batch([m], fr, seed, jitter_deg=20.0, random_bg=True)
 
 
 UNEVEN_N = (20_000, 35_000, 50_000, 65_000, 80_000, 90_000, 95_000, 100_000)
