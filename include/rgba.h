@@ -76,12 +76,29 @@ typedef struct {
     const float *dg;    /* device [k][A][n_pad], A = popcount(mask) */
     float *grad_g0;     /* device [14][n_pad] or NULL: dL/dG0, overwritten by the backward */
     float *grad_dg;     /* device [k][A][n_pad] or NULL: dL/ddG, overwritten by the backward */
+    /* Tangent-space binding (Supp. "Gaussian Transformation", Alg. 1), or n_faces == 0 (the
+     * pointers are then ignored and means/rotations are in world space). A bound Gaussian i
+     * sits on triangle face_of[i] at the barycentric point bary[.][i] of its UV sample; its
+     * mean and rotation channels are tangent-space (u, v, normal) coordinates. Per frame,
+     * with the triangle's corners v0..v2 from rgba_frame.verts and their UVs, the TBN matrix
+     * R = [T B N] (T = dx/du, B = dx/dv over the triangle, N the unit normal of
+     * (v1 - v0) x (v2 - v0)) and t = b0 v0 + b1 v1 + b2 v2 map it to deformed space:
+     * x = R x_T + t, covariance R Sigma_T R^T. No gradient flows to the mesh. A face or vertex
+     * index out of range culls the Gaussian and sets bit 1 of rgba_step_out.device_error. */
+    int32_t n_faces;            /* triangles of the mesh, 0 = unbound */
+    int32_t n_verts;            /* vertices of every frame mesh of this model */
+    const int32_t *faces;       /* device [n_faces][3] vertex indices */
+    const float *face_uv;       /* device [n_faces][6]: (u, v) of corners 0, 1, 2 */
+    const int32_t *face_of;     /* device [n]: triangle of each Gaussian */
+    const float *bary;          /* device [3][n_pad]: barycentric weights of each Gaussian */
 } rgba_model;
 
 typedef struct {
     int32_t model;      /* index into rgba_batch.models */
     int32_t width;      /* pixels, 1..RGBA_MAX_DIM */
     int32_t height;
+    const float *verts; /* device [n_verts][3]: this frame's deformed mesh if the model is
+                           bound, else NULL (Supp. "Gaussian Transformation") */
 } rgba_frame;
 
 typedef struct {

@@ -34,11 +34,14 @@ STAGES = ("upload", "preprocess", "scan", "scatter", "sort", "render_fwd", "rend
 class RgbaModel(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_pad", C.c_int32), ("k", C.c_int32), ("mask", C.c_uint32),
                 ("g0", C.c_void_p), ("dg", C.c_void_p), ("grad_g0", C.c_void_p),
-                ("grad_dg", C.c_void_p)]
+                ("grad_dg", C.c_void_p), ("n_faces", C.c_int32), ("n_verts", C.c_int32),
+                ("faces", C.c_void_p), ("face_uv", C.c_void_p), ("face_of", C.c_void_p),
+                ("bary", C.c_void_p)]
 
 
 class RgbaFrame(C.Structure):
-    _fields_ = [("model", C.c_int32), ("width", C.c_int32), ("height", C.c_int32)]
+    _fields_ = [("model", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
+                ("verts", C.c_void_p)]
 
 
 class RgbaBatch(C.Structure):

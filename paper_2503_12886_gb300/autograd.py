@@ -17,8 +17,9 @@ from .rasterizer import DeviceBatch, DeviceModel, Renderer, stream_ptr
 class _Frames:
     """Host description of a batch whose tensors come from autograd (no copies)."""
 
-    def __init__(self, frames, k_stride, tile, smem_batch):
+    def __init__(self, frames, k_stride, tile, smem_batch, verts=None):
         self.frames = [(int(m), int(w), int(h)) for m, w, h in frames]
+        self.verts = list(verts) if verts is not None else [None] * len(self.frames)
         self.k_stride = k_stride
         self.tile = tile
         self.smem_batch = smem_batch
@@ -29,6 +30,7 @@ def _device_batch(spec: _Frames, psi, fparams, models, grads: bool) -> DeviceBat
     db.device = psi.device
     db.models = models
     db.frames = spec.frames
+    db.verts = spec.verts
     db.k_stride = spec.k_stride
     db.psi = psi
     db.fparams = fparams
@@ -58,8 +60,9 @@ class RasterizeBlendFn(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, renderer: Renderer, spec: _Frames, model_meta, psi, fparams, *tensors):
-        models = [DeviceModel(n, k, mask, tensors[2 * i].contiguous(), tensors[2 * i + 1].contiguous())
-                  for i, (n, k, mask) in enumerate(model_meta)]
+        models = [DeviceModel(n, k, mask, tensors[2 * i].contiguous(), tensors[2 * i + 1].contiguous(),
+                              binding=bd)
+                  for i, (n, k, mask, bd) in enumerate(model_meta)]
         db = _device_batch(spec, psi.contiguous(), fparams.contiguous(), models, grads=False)
         img, T, n = renderer.forward(db)
         ctx.renderer, ctx.spec, ctx.model_meta = renderer, spec, model_meta
@@ -70,9 +73,10 @@ class RasterizeBlendFn(torch.autograd.Function):
     def backward(ctx, dl_dimg):
         T, n, psi, fparams, *tensors = ctx.saved_tensors
         models = []
-        for i, (nn, k, mask) in enumerate(ctx.model_meta):
+        for i, (nn, k, mask, bd) in enumerate(ctx.model_meta):
             g0, dg = tensors[2 * i].contiguous(), tensors[2 * i + 1].contiguous()
-            models.append(DeviceModel(nn, k, mask, g0, dg, torch.empty_like(g0), torch.empty_like(dg)))
+            models.append(DeviceModel(nn, k, mask, g0, dg, torch.empty_like(g0), torch.empty_like(dg),
+                                      binding=bd))
         db = _device_batch(ctx.spec, psi.contiguous(), fparams.contiguous(), models, grads=True)
         r: Renderer = ctx.renderer
         ws = r.ensure_workspace(db)
@@ -93,14 +97,18 @@ class RasterizeBlendFn(torch.autograd.Function):
         return (None, None, None, db.grad_psi, None, *grads)
 
 
-def rasterize(renderer: Renderer, frames, psi, fparams, models, tile=(16, 16), smem_batch=64):
+def rasterize(renderer: Renderer, frames, psi, fparams, models, tile=(16, 16), smem_batch=64,
+              bindings=None, verts=None):
     """Differentiable batched render.
 
     frames: list of (model index, width, height); psi [B][k_stride]; fparams [B][20];
-    models: list of (n, k, mask, g0, dg) with g0/dg CUDA float32 tensors (may require grad).
-    Returns one [3][H][W] view per frame of the concatenated output."""
-    spec = _Frames(frames, psi.shape[1], tile, smem_batch)
-    meta = [(n, k, mask) for n, k, mask, _, _ in models]
+    models: list of (n, k, mask, g0, dg) with g0/dg CUDA float32 tensors (may require grad);
+    bindings (optional): per model a rasterizer.DeviceBinding or None (tangent space, Supp.
+    "Gaussian Transformation"), with verts: per frame the deformed mesh [V][3] (CUDA float32)
+    or None. Returns one [3][H][W] view per frame of the concatenated output."""
+    spec = _Frames(frames, psi.shape[1], tile, smem_batch, verts)
+    bindings = bindings or [None] * len(models)
+    meta = [(n, k, mask, bd) for (n, k, mask, _, _), bd in zip(models, bindings)]
     flat = []
     for _, _, _, g0, dg in models:
         flat += [g0, dg]

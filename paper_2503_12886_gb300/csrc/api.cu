@@ -83,6 +83,15 @@ int make_plan(const rgba_batch *b, Plan &p) {
         int a = 0;
         for (int ch = 0; ch < kNch; ++ch)
             if ((src.mask >> ch) & 1u) mi.chans[a++] = ch;
+        if (src.n_faces < 0 || (src.n_faces > 0 && (src.n_verts < 3 || !src.faces || !src.face_uv ||
+                                                     (src.n > 0 && (!src.face_of || !src.bary)))))
+            return fail(RGBA_ERR_INVALID_ARG, "model " + std::to_string(m) + ": incomplete tangent-space binding");
+        mi.n_faces = src.n_faces;
+        mi.n_verts = src.n_faces > 0 ? src.n_verts : 0;
+        mi.faces = src.n_faces > 0 ? src.faces : nullptr;
+        mi.face_uv = src.n_faces > 0 ? src.face_uv : nullptr;
+        mi.face_of = src.n_faces > 0 ? src.face_of : nullptr;
+        mi.bary = src.n_faces > 0 ? src.bary : nullptr;
         mi.n_chunks = (src.n_pad + kBwdChunk - 1) / kBwdChunk;
         p.max_n = std::max(p.max_n, src.n_pad);
         p.max_chunks = std::max(p.max_chunks, mi.n_chunks);
@@ -98,7 +107,10 @@ int make_plan(const rgba_batch *b, Plan &p) {
             return fail(RGBA_ERR_INVALID_ARG, "frame " + std::to_string(f) + ": size out of range");
         const ModelInfo &mi = p.models[fr.model];
         if (mi.k > b->k_stride) return fail(RGBA_ERR_INVALID_ARG, "k_stride smaller than a model's k");
+        if (mi.n_faces > 0 && !fr.verts)
+            return fail(RGBA_ERR_INVALID_ARG, "frame " + std::to_string(f) + ": its model is bound to a mesh but verts is NULL");
         FrameInfo &fi = p.frames[f];
+        fi.verts = mi.n_faces > 0 ? fr.verts : nullptr;
         fi.model = fr.model;
         fi.W = fr.width;
         fi.H = fr.height;

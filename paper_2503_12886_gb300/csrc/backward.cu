@@ -26,9 +26,14 @@ struct Fwd {
     float A, B, C, det;
 };
 
-__device__ __forceinline__ void recompute(const float v[10], const float *V, int W, int H, Fwd &f) {
+// Rt: [12] = TBN matrix row-major (columns T, B, N), then t (the identity and zero for unbound
+// models); the Gaussian is mapped from tangent space by x = R x_T + t, covariance R Sigma R^T.
+__device__ __forceinline__ void recompute(const float v[10], const float *V, int W, int H, const float *Rt, Fwd &f) {
+    float xm[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) f.p[j] = V[4 * j] * v[0] + V[4 * j + 1] * v[1] + V[4 * j + 2] * v[2] + V[4 * j + 3];
+    for (int c = 0; c < 3; ++c) xm[c] = Rt[3 * c] * v[0] + Rt[3 * c + 1] * v[1] + Rt[3 * c + 2] * v[2] + Rt[9 + c];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) f.p[j] = V[4 * j] * xm[0] + V[4 * j + 1] * xm[1] + V[4 * j + 2] * xm[2] + V[4 * j + 3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) f.s[m] = __expf(v[7 + m]);
     f.il = rsqrtf(v[3] * v[3] + v[4] * v[4] + v[5] * v[5] + v[6] * v[6]);
@@ -54,6 +59,17 @@ __device__ __forceinline__ void recompute(const float v[10], const float *V, int
             for (int m = 0; m < 3; ++m) a += f.R[i][m] * f.s[m] * f.s[m] * f.R[j][m];
             Sg[i][j] = a;
         }
+    {
+        float P[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) P[i][j] = Rt[3 * i] * Sg[0][j] + Rt[3 * i + 1] * Sg[1][j] + Rt[3 * i + 2] * Sg[2][j];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Sg[i][j] = P[i][0] * Rt[3 * j] + P[i][1] * Rt[3 * j + 1] + P[i][2] * Rt[3 * j + 2];
+    }
     float Tm[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -97,9 +113,9 @@ __device__ __forceinline__ void recompute(const float v[10], const float *V, int
 
 // dG[14]: gradient w.r.t. the blended channels of one (frame, Gaussian).
 __device__ __forceinline__ void chain(const float v[10], float op, const float *V, int W, int H,
-                                      const float g2[9], float dG[kNch]) {
+                                      const float *Rt, const float g2[9], float dG[kNch]) {
     Fwd f;
-    recompute(v, V, W, H, f);
+    recompute(v, V, W, H, Rt, f);
     const float du = g2[0], dv = g2[1], dca = g2[2], dcb = g2[3], dcc = g2[4];
     dG[10] = g2[5] * op * (1.f - op);
     dG[11] = g2[6];
@@ -136,6 +152,16 @@ __device__ __forceinline__ void chain(const float v[10], float op, const float *
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) dS[r][c] = tmp[r][0] * V[c] + tmp[r][1] * V[4 + c] + tmp[r][2] * V[8 + c];
+    {  // Sigma = R Sigma_T R^T: dSigma_T = R^T dSigma R
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) tmp[r][c] = Rt[r] * dS[0][c] + Rt[3 + r] * dS[1][c] + Rt[6 + r] * dS[2][c];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dS[r][c] = tmp[r][0] * Rt[c] + tmp[r][1] * Rt[3 + c] + tmp[r][2] * Rt[6 + c];
+    }
     // Sigma = R diag(s^2) R^T
     float dSR[3][3];
 #pragma unroll
@@ -183,8 +209,49 @@ __device__ __forceinline__ void chain(const float v[10], float op, const float *
     } else {
         dp2 += dJ[1][2] * fy * f.ry * ipz2;
     }
+    float dxw[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dG[c] = V[c] * dp0 + V[4 + c] * dp1 + V[8 + c] * dp2;
+    for (int c = 0; c < 3; ++c) dxw[c] = V[c] * dp0 + V[4 + c] * dp1 + V[8 + c] * dp2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)  // x = R x_T + t: dx_T = R^T dx
+        dG[c] = Rt[c] * dxw[0] + Rt[3 + c] * dxw[1] + Rt[6 + c] * dxw[2];
+}
+
+// TBN matrix and barycentric point of Gaussian i in one frame (the same definitions as the
+// preprocess, fp32 without its fixed rounding order): out[12] as recompute() reads it.
+__device__ __forceinline__ bool tbn_fast(const ModelInfo &m, const float *__restrict__ verts, int i, float out[12]) {
+    const int f = __ldg(m.face_of + i);
+    if ((unsigned)f >= (unsigned)m.n_faces) return false;
+    const int i0 = __ldg(m.faces + 3 * f), i1 = __ldg(m.faces + 3 * f + 1), i2 = __ldg(m.faces + 3 * f + 2);
+    if ((unsigned)i0 >= (unsigned)m.n_verts || (unsigned)i1 >= (unsigned)m.n_verts ||
+        (unsigned)i2 >= (unsigned)m.n_verts)
+        return false;
+    float a[3], b[3], c[3], e1[3], e2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a[k] = __ldg(verts + 3 * i0 + k);
+        b[k] = __ldg(verts + 3 * i1 + k);
+        c[k] = __ldg(verts + 3 * i2 + k);
+        e1[k] = b[k] - a[k];
+        e2[k] = c[k] - a[k];
+    }
+    const float *uv = m.face_uv + 6 * f;
+    const float du1 = __ldg(uv + 2) - __ldg(uv), dv1 = __ldg(uv + 3) - __ldg(uv + 1);
+    const float du2 = __ldg(uv + 4) - __ldg(uv), dv2 = __ldg(uv + 5) - __ldg(uv + 1);
+    const float rd = __frcp_rn(du1 * dv2 - dv1 * du2);
+    const float n0 = e1[1] * e2[2] - e1[2] * e2[1], n1 = e1[2] * e2[0] - e1[0] * e2[2],
+                n2 = e1[0] * e2[1] - e1[1] * e2[0];
+    const float il = rsqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+    const float nn[3] = {n0 * il, n1 * il, n2 * il};
+    const float b0 = __ldg(m.bary + i), b1 = __ldg(m.bary + m.n_pad + i), b2 = __ldg(m.bary + 2 * m.n_pad + i);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        out[3 * k] = (dv2 * e1[k] - dv1 * e2[k]) * rd;
+        out[3 * k + 1] = (du1 * e2[k] - du2 * e1[k]) * rd;
+        out[3 * k + 2] = nn[k];
+        out[9 + k] = b0 * a[k] + b1 * b[k] + b2 * c[k];
+    }
+    return true;
 }
 
 // The backward of one model chunk. One CTA = 32 Gaussians (lane = Gaussian) of one model; the
@@ -233,6 +300,7 @@ k_gauss_bwd(Ctx c, int max_k) {
     float *s_psi = s_dG + kFG2 * kNch * kBwdChunk;        // [16][max_k]
     __shared__ long long s_rec[kFG2];
     __shared__ int s_wh[kFG2][2];
+    __shared__ const float *s_verts[kFG2];
     __shared__ float s_fp[kFG2][RGBA_FP_STRIDE];
     const ModelInfo &m = c.models[blockIdx.y];
     const int chunk = blockIdx.x;
@@ -250,6 +318,7 @@ k_gauss_bwd(Ctx c, int max_k) {
             s_rec[threadIdx.x] = f.rec_base;
             s_wh[threadIdx.x][0] = f.W;
             s_wh[threadIdx.x][1] = f.H;
+            s_verts[threadIdx.x] = f.verts;
         }
         for (int e = threadIdx.x; e < ng * RGBA_FP_STRIDE; e += kBwdThreads) {
             const int fl = e / RGBA_FP_STRIDE, q = e - fl * RGBA_FP_STRIDE;
@@ -299,7 +368,9 @@ k_gauss_bwd(Ctx c, int max_k) {
                 if (live[0]) {  // item u sits in slot 0 (a rolled loop keeps the code small)
                     const float v[10] = {c0[0].x, c0[0].y, c0[0].z, c0[0].w, c1[0].x, c1[0].y, c1[0].z, c1[0].w, c2[0].x, c2[0].y};
                     const float g2[9] = {ga[0].x, ga[0].y, ga[0].z, ga[0].w, gb[0].x, gb[0].y, gb[0].z, gb[0].w, gc[0].x};
-                    chain(v, op[0], s_fp[fl], s_wh[fl][0], s_wh[fl][1], g2, dG);
+                    float Rt[12] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f};
+                    if (m.n_faces == 0 || tbn_fast(m, s_verts[fl], i0 + li, Rt))
+                        chain(v, op[0], s_fp[fl], s_wh[fl][0], s_wh[fl][1], Rt, g2, dG);
                 }
 #pragma unroll
                 for (int q = 0; q < kNch; ++q) s_dG[(fl * kNch + q) * kBwdChunk + li] = dG[q];

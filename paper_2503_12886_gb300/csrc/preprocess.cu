@@ -80,8 +80,57 @@ __device__ __forceinline__ void blend14(const ModelInfo &m, const float *__restr
 // per-Gaussian spec would use, so staging them changes no bit.
 struct FrameConst {
     float limx, limy;
-    int tiles_x, tiles_y, tile_base, rec_base, pad_[2];
+    int tiles_x, tiles_y, tile_base, rec_base;
+    const float *verts;  // the frame's deformed mesh (bound models)
 };
+
+// The TBN matrix of Gaussian i's triangle (Supp. "Gaussian Transformation", Alg. 1) and the
+// barycentric point of its UV sample, as a fixed sequence of correctly rounded operations:
+// e1 = v1 - v0, e2 = v2 - v0; with UV differences (du1, dv1), (du2, dv2) and
+// det = du1 dv2 - dv1 du2: T = (dv2 e1 - dv1 e2) / det, B = (du1 e2 - du2 e1) / det (so that
+// e1 = du1 T + dv1 B and e2 = du2 T + dv2 B), N = (e1 x e2) / |e1 x e2|; t = (b0 v0 + b1 v1) +
+// b2 v2. R[c] = (T_c, B_c, N_c). False when an index is out of range.
+__device__ __forceinline__ bool tbn_spec(const ModelInfo &m, const float *__restrict__ verts, int i,
+                                         float R[3][3], float t[3]) {
+    const int f = __ldg(m.face_of + i);
+    if ((unsigned)f >= (unsigned)m.n_faces) return false;
+    const int i0 = __ldg(m.faces + 3 * f), i1 = __ldg(m.faces + 3 * f + 1), i2 = __ldg(m.faces + 3 * f + 2);
+    if ((unsigned)i0 >= (unsigned)m.n_verts || (unsigned)i1 >= (unsigned)m.n_verts ||
+        (unsigned)i2 >= (unsigned)m.n_verts)
+        return false;
+    float a[3], b[3], c[3], e1[3], e2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a[k] = __ldg(verts + 3 * i0 + k);
+        b[k] = __ldg(verts + 3 * i1 + k);
+        c[k] = __ldg(verts + 3 * i2 + k);
+        e1[k] = fsub(b[k], a[k]);
+        e2[k] = fsub(c[k], a[k]);
+    }
+    const float *uv = m.face_uv + 6 * f;
+    const float u0 = __ldg(uv), v0 = __ldg(uv + 1);
+    const float du1 = fsub(__ldg(uv + 2), u0), dv1 = fsub(__ldg(uv + 3), v0);
+    const float du2 = fsub(__ldg(uv + 4), u0), dv2 = fsub(__ldg(uv + 5), v0);
+    const float det = fsub(fmul(du1, dv2), fmul(dv1, du2));
+    const float rd = fdiv(1.0f, det);
+    float n[3];
+    n[0] = fsub(fmul(e1[1], e2[2]), fmul(e1[2], e2[1]));
+    n[1] = fsub(fmul(e1[2], e2[0]), fmul(e1[0], e2[2]));
+    n[2] = fsub(fmul(e1[0], e2[1]), fmul(e1[1], e2[0]));
+    float l2 = fmul(n[0], n[0]);
+    l2 = fadd(l2, fmul(n[1], n[1]));
+    l2 = fadd(l2, fmul(n[2], n[2]));
+    const float len = fsqrt(l2);
+    const float b0 = __ldg(m.bary + i), b1 = __ldg(m.bary + m.n_pad + i), b2 = __ldg(m.bary + 2 * m.n_pad + i);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        R[k][0] = fmul(fsub(fmul(dv2, e1[k]), fmul(dv1, e2[k])), rd);
+        R[k][1] = fmul(fsub(fmul(du1, e2[k]), fmul(du2, e1[k])), rd);
+        R[k][2] = fdiv(n[k], len);
+        t[k] = fadd(fadd(fmul(b0, a[k]), fmul(b1, b[k])), fmul(b2, c[k]));
+    }
+    return true;
+}
 
 __device__ __forceinline__ float sigmoid_spec(float x) { return fdiv(1.0f, fadd(1.0f, exp_spec(-x))); }
 
@@ -89,19 +138,32 @@ __device__ __forceinline__ float sigmoid_spec(float x) { return fdiv(1.0f, fadd(
 // opacity op: view transform, activations, EWA covariance, conic, radius, tile rectangle, depth.
 // Writes the render record, the rectangle and the backward cache, and counts the Gaussian in
 // every tile it touches.
-__device__ __forceinline__ void decide_and_write(const Ctx &c, const FrameConst &f, const float *V,
-                                                 const float v[kNch], float op, long long r) {
+__device__ __forceinline__ void decide_and_write(const Ctx &c, const ModelInfo &m, const FrameConst &f,
+                                                 const float *V, const float v[kNch], float op, int i,
+                                                 long long r) {
     c.cache[r * 3 + 0] = make_float4(v[0], v[1], v[2], v[3]);
     c.cache[r * 3 + 1] = make_float4(v[4], v[5], v[6], v[7]);
     c.cache[r * 3 + 2] = make_float4(v[8], v[9], 0.f, 0.f);
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     ushort4 rc = make_ushort4(0, 0, 0, 0);
     do {
+        // tangent space -> deformed space: x_c = fma(N_c, x2, fma(B_c, x1, fma(T_c, x0, t_c)))
+        const bool bound = m.n_faces > 0;
+        float Rt[3][3], xm[3] = {v[0], v[1], v[2]};
+        if (bound) {
+            float tt[3];
+            if (!tbn_spec(m, f.verts, i, Rt, tt)) {
+                atomicOr(&c.cnt->device_error, 2u);
+                break;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) xm[k] = ffma(Rt[k][2], v[2], ffma(Rt[k][1], v[1], ffma(Rt[k][0], v[0], tt[k])));
+        }
         // view transform
         float p[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j)
-            p[j] = ffma(V[4 * j + 2], v[2], ffma(V[4 * j + 1], v[1], ffma(V[4 * j + 0], v[0], V[4 * j + 3])));
+            p[j] = ffma(V[4 * j + 2], xm[2], ffma(V[4 * j + 1], xm[1], ffma(V[4 * j + 0], xm[0], V[4 * j + 3])));
         if (!(p[2] > V[16])) break;
         // scales
         float s[3];
@@ -138,6 +200,20 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const FrameConst 
 #pragma unroll
             for (int jj = 0; jj < 3; ++jj)
                 Sg[ii][jj] = ffma(Mm[ii][2], R[jj][2], ffma(Mm[ii][1], R[jj][1], fmul(Mm[ii][0], R[jj][0])));
+        // deformed-space covariance Rt Sigma Rt^T (P = Rt Sigma, then P Rt^T)
+        if (bound) {
+            float P[3][3];
+#pragma unroll
+            for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj)
+                    P[ii][jj] = ffma(Rt[ii][2], Sg[2][jj], ffma(Rt[ii][1], Sg[1][jj], fmul(Rt[ii][0], Sg[0][jj])));
+#pragma unroll
+            for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj)
+                    Sg[ii][jj] = ffma(P[ii][2], Rt[jj][2], ffma(P[ii][1], Rt[jj][1], fmul(P[ii][0], Rt[jj][0])));
+        }
         // camera covariance W Sigma W^T
         float Tm[3][3], Cm[3][3];
 #pragma unroll
@@ -331,7 +407,7 @@ k_preprocess(Ctx c, int max_k) {
             fc.tiles_y = f.tiles_y;
             fc.tile_base = f.tile_base;
             fc.rec_base = f.rec_base;
-            fc.pad_[0] = fc.pad_[1] = 0;
+            fc.verts = f.verts;
             s_fc[tid] = fc;
         }
         __syncthreads();
@@ -367,8 +443,8 @@ k_preprocess(Ctx c, int max_k) {
             for (int q = 0; q < kPreFB; ++q) {
                 if (f0 + q < nr) {
                     const FrameConst &fc = s_fc[f0 + q];
-                    decide_and_write(c, fc, s_fp + (f0 + q) * RGBA_FP_STRIDE, v[0],
-                                     op_blended ? sigmoid_spec(v[0][10]) : op0, fc.rec_base + i);
+                    decide_and_write(c, m, fc, s_fp + (f0 + q) * RGBA_FP_STRIDE, v[0],
+                                     op_blended ? sigmoid_spec(v[0][10]) : op0, i, fc.rec_base + i);
                 }
 #pragma unroll
                 for (int q2 = 0; q2 + 1 < kPreFB; ++q2)

@@ -40,7 +40,12 @@ struct ModelInfo {
     int n_chunks;    // ceil(n / kBwdChunk)
     long long dpsi_off;  // float offset of this model's [n_chunks][nb][k] dpsi partials
     int chans[kNch]; // blended channel ids, ascending (first A used)
-    int pad_[2];
+    int n_faces;     // tangent-space binding (0: unbound)
+    int n_verts;
+    const int *faces;      // [n_faces][3]
+    const float *face_uv;  // [n_faces][6]
+    const int *face_of;    // [n]
+    const float *bary;     // [3][n_pad]
 };
 
 // Per-frame table (device copy in the workspace).
@@ -49,6 +54,7 @@ struct FrameInfo {
     int tiles_y, tile_base, rec_base, n;
     long long pix_base;  // first pixel of this frame in the concatenated image arrays
     int n_pad, k;
+    const float *verts;  // [n_verts][3] deformed mesh (bound models) or nullptr
 };
 
 struct Counters {

@@ -1,6 +1,6 @@
 """Runs eager training steps of a named workload, for profilers (ncu) and quick timing.
 
-    python -m paper_2503_12886_gb300.profile_step [--workload batched|single|uneven]
+    python -m paper_2503_12886_gb300.profile_step [--workload batched|single|uneven|tangent]
         [--steps N] [--tile 16x16|8x32] [--smem-batch 64|128|256] [--train T]
 
 With --train T the avatar first fits images of its reference avatar (synth.reference_avatar)
@@ -30,6 +30,8 @@ def make(name: str):
         return synth.workload_single()
     if name == "uneven":
         return synth.workload_uneven()
+    if name == "tangent":
+        return synth.workload_tangent()
     raise ValueError(name)
 
 

@@ -14,6 +14,23 @@ from . import api, synth
 
 
 @dataclass
+class DeviceBinding:
+    """A model's tangent-space binding on the device (synth.Binding)."""
+    faces: torch.Tensor     # int32 [F][3]
+    face_uv: torch.Tensor   # float32 [F][6]
+    face_of: torch.Tensor   # int32 [n]
+    bary: torch.Tensor      # float32 [3][n_pad]
+    n_verts: int
+
+    @staticmethod
+    def of(b: synth.Binding | None, device) -> "DeviceBinding | None":
+        if b is None:
+            return None
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        return DeviceBinding(t(b.faces), t(b.face_uv), t(b.face_of), t(b.bary), b.n_verts)
+
+
+@dataclass
 class DeviceModel:
     n: int
     k: int
@@ -22,10 +39,21 @@ class DeviceModel:
     dg: torch.Tensor        # [k][A][n_pad]
     grad_g0: torch.Tensor | None = None
     grad_dg: torch.Tensor | None = None
+    binding: DeviceBinding | None = None
 
     @property
     def n_pad(self) -> int:
         return self.g0.shape[1]
+
+    def abi(self) -> api.RgbaModel:
+        b = self.binding
+        return api.RgbaModel(self.n, self.n_pad, self.k, self.mask, self.g0.data_ptr(),
+                             self.dg.data_ptr(),
+                             self.grad_g0.data_ptr() if self.grad_g0 is not None else None,
+                             self.grad_dg.data_ptr() if self.grad_dg is not None else None,
+                             b.faces.shape[0] if b else 0, b.n_verts if b else 0,
+                             b.faces.data_ptr() if b else None, b.face_uv.data_ptr() if b else None,
+                             b.face_of.data_ptr() if b else None, b.bary.data_ptr() if b else None)
 
 
 class DeviceBatch:
@@ -36,7 +64,8 @@ class DeviceBatch:
         self.device = torch.device(device)
         if models is None:
             models = [DeviceModel(m.n, m.k, m.mask, torch.from_numpy(m.g0).to(self.device),
-                                  torch.from_numpy(m.dg).to(self.device))
+                                  torch.from_numpy(m.dg).to(self.device),
+                                  binding=DeviceBinding.of(m.binding, self.device))
                       for m in batch.models]
         self.models = models
         if grads:
@@ -45,6 +74,10 @@ class DeviceBatch:
                     m.grad_g0 = torch.zeros_like(m.g0)
                     m.grad_dg = torch.zeros_like(m.dg)
         self.frames = [(f.model, f.width, f.height) for f in batch.frames]
+        # each frame's deformed mesh (bound models), one device tensor per frame
+        self.verts = [None if f.verts is None else
+                      torch.from_numpy(np.ascontiguousarray(f.verts, np.float32)).to(self.device)
+                      for f in batch.frames]
         self.k_stride = batch.k_stride
         self.psi = torch.from_numpy(np.ascontiguousarray(batch.psi)).to(self.device)
         self.fparams = torch.from_numpy(np.ascontiguousarray(batch.fparams)).to(self.device)
@@ -73,12 +106,11 @@ class DeviceBatch:
         """ABI descriptor; host arrays are kept alive on this object."""
         ms = (api.RgbaModel * max(1, len(self.models)))()
         for i, m in enumerate(self.models):
-            ms[i] = api.RgbaModel(m.n, m.n_pad, m.k, m.mask, m.g0.data_ptr(), m.dg.data_ptr(),
-                                  m.grad_g0.data_ptr() if m.grad_g0 is not None else None,
-                                  m.grad_dg.data_ptr() if m.grad_dg is not None else None)
+            ms[i] = m.abi()
         fs = (api.RgbaFrame * max(1, len(self.frames)))()
         for i, (mi, w, h) in enumerate(self.frames):
-            fs[i] = api.RgbaFrame(mi, w, h)
+            v = self.verts[i]
+            fs[i] = api.RgbaFrame(mi, w, h, v.data_ptr() if v is not None else None)
         b = api.RgbaBatch()
         b.n_models = len(self.models)
         b.models = C.cast(ms, C.POINTER(api.RgbaModel))

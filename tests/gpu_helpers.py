@@ -130,9 +130,15 @@ def grad_error(g: np.ndarray, ref: np.ndarray, axis_rows=True):
     return float((np.abs(gr - rows) / tol).max())
 
 
-def oracle_fwd_bwd(batch, targets, kind, tile=(16, 16)):
-    ores = oracle.forward(batch, tile=tile, eps=AMBIG_EPS, splat="spec")
+def oracle_fwd_bwd(batch, targets, kind, tile=(16, 16), drop_flagged=False):
+    """Oracle forward, loss and backward. With drop_flagged, dL/dimg is zeroed at the pixels
+    the oracle flags as ambiguous (a compositing cutoff within AMBIG_EPS / AMBIG_EPS_T): there
+    the fp32 path may legitimately take the other decision, and the gradient of that pixel is
+    discontinuous, so both backward passes then see the same, decision-stable dL/dimg."""
+    ores = oracle.forward(batch, tile=tile, eps=AMBIG_EPS, splat="spec", eps_t=AMBIG_EPS_T)
     L, dls = oracle.loss(batch, ores, targets, kind)
+    if drop_flagged:
+        dls = [np.where(r.flags[None] != 0, 0.0, d) for r, d in zip(ores, dls)]
     per_model, dpsi, g2s, dgbs = oracle.backward(batch, ores, dls, tile=tile)
     return ores, L, dls, per_model, dpsi, g2s
 

@@ -66,6 +66,11 @@ def test_workspace_size_grows_with_capacity(api):
     (lambda b, ms, fs: setattr(b, "psi", None), "psi"),
     (lambda b, ms, fs: setattr(ms[0], "g0", None), "g0"),
     (lambda b, ms, fs: setattr(ms[0], "g0", 0x1004), "aligned"),
+    (lambda b, ms, fs: setattr(ms[0], "n_faces", 5), "tangent-space binding"),
+    (lambda b, ms, fs: (setattr(ms[0], "n_faces", 5), setattr(ms[0], "n_verts", 9),
+                        setattr(ms[0], "faces", 0x5000), setattr(ms[0], "face_uv", 0x6000),
+                        setattr(ms[0], "face_of", 0x7000), setattr(ms[0], "bary", 0x8000)), "verts"),
+    (lambda b, ms, fs: setattr(ms[0], "n_faces", -1), "tangent-space binding"),
 ])
 def test_invalid_batches_rejected_on_host(api, mutate, msg):
     b, ms, fs = _batch(api)
@@ -74,6 +79,15 @@ def test_invalid_batches_rejected_on_host(api, mutate, msg):
         api.rgba_workspace_size(b, 100)
     assert e.value.code == api.RGBA_ERR_INVALID_ARG
     assert msg in str(e.value)
+
+
+def test_complete_binding_accepted(api):
+    b, ms, fs = _batch(api)
+    for k, v in (("n_faces", 5), ("n_verts", 9), ("faces", 0x5000), ("face_uv", 0x6000),
+                 ("face_of", 0x7000), ("bary", 0x8000)):
+        setattr(ms[0], k, v)
+    fs[0].verts = 0x9000
+    assert api.rgba_workspace_size(b, 100) == api.rgba_workspace_size(_batch(api)[0], 100)
 
 
 def test_null_arguments(api):

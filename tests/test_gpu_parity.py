@@ -70,6 +70,15 @@ def dense_batch():
     return synth.make_batch([m], [synth.Frame(0, 64, 64)], seed=93)
 
 
+def tangent_batch(mask=synth.MASK_MEAN_SCALE_COLOR, seed=81):
+    """Gaussians bound to a head mesh (tangent space, Supp. "Gaussian Transformation"), three
+    frames with different mesh expressions, jittered cameras, random background."""
+    mesh = synth.make_head_mesh(seed, 24, 48)
+    m = synth.make_bound_model(seed, 8000, 8, mesh, mask=mask)
+    fr = [synth.Frame(0, 192, 160, synth.frame_verts(mesh, seed, f)) for f in range(3)]
+    return synth.make_batch([m], fr, seed, jitter_deg=20, random_bg=True)
+
+
 CASES = {
     "single_128": (lambda: synth.workload_single(), (16, 16), 64),
     "gradcheck_64": (lambda: synth.workload_gradcheck(), (16, 16), 256),
@@ -79,6 +88,8 @@ CASES = {
     "uneven": (uneven_batch, (16, 16), 128),
     "depth_ties": (ties_batch, (16, 16), 128),
     "dense_lists": (dense_batch, (16, 16), 64),
+    "tangent": (tangent_batch, (16, 16), 64),
+    "tangent_paper_mask": (lambda: tangent_batch(synth.MASK_PAPER, 82), (8, 32), 128),
 }
 
 
@@ -107,12 +118,13 @@ def test_forward_pixels(renderer, case):
 
 @pytest.mark.parametrize("case", list(CASES))
 def test_backward_gradients(renderer, case):
-    """Same dL/dimg (the oracle's, from its own image) into both backward passes."""
+    """Same dL/dimg (the oracle's, from its own image, zero at the pixels it flags as
+    ambiguous) into both backward passes."""
     make, tile, sb = CASES[case]
     batch = make()
     kind = "l2" if case.startswith("gradcheck") else "l1"
     targets = synth.make_targets(batch, 99)
-    ores, L, dls, per_model, dpsi, g2s = oracle_fwd_bwd(batch, targets, kind, tile)
+    ores, L, dls, per_model, dpsi, g2s = oracle_fwd_bwd(batch, targets, kind, tile, drop_flagged=True)
     r, db, img, T, n = run_gpu_forward(batch, tile, sb, renderer)
     dl = db.pack_images([d.astype(np.float32) for d in dls])
     r.backward(db, dl, T, n)
@@ -168,3 +180,32 @@ def test_blend_matches_oracle(renderer):
                                 np.abs(m.dg.astype(np.float64)))
         bound = (m.k + 1) * 2.0 ** -24 * mag
         assert (np.abs(got[:, :m.n] - ref[:, :m.n]) <= bound[:, :m.n]).all()
+
+
+def test_identity_frames_match_the_unbound_path_bit_for_bit(renderer):
+    """Every Gaussian bound to a triangle whose tangent frame is the identity at the origin:
+    the CUDA path's decisions, lists, image, T and contributor counts equal the unbound run."""
+    import dataclasses
+    m = synth.make_model(91, 6000, 8)
+    n = m.n
+    bary = np.zeros((3, m.n_pad), np.float32)
+    bary[0, :n] = 1.0
+    verts = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    b = synth.Binding(np.array([[0, 1, 2]], np.int32), np.array([[0, 0, 1, 0, 0, 1]], np.float32),
+                      np.zeros(n, np.int32), bary, 3)
+    frames = [synth.Frame(0, 160, 128), synth.Frame(0, 96, 96)]
+    plain = synth.make_batch([m], frames, seed=91, jitter_deg=15, random_bg=True)
+    bound = synth.Batch([dataclasses.replace(m, binding=b)],
+                        [synth.Frame(0, f.width, f.height, verts) for f in frames],
+                        plain.psi, plain.fparams, plain.k_stride)
+    outs = []
+    for batch in (plain, bound):
+        r, db, img, T, nc = run_gpu_forward(batch, (16, 16), 64, renderer)
+        inter = read_intermediates(r, db)
+        outs.append((img.clone(), T.clone(), nc.clone(), inter["rects"].copy(),
+                     inter["sorted"].copy(), inter["records"].copy()))
+    for a, c in zip(*outs):
+        if isinstance(a, torch.Tensor):
+            assert torch.equal(a, c)
+        else:
+            np.testing.assert_array_equal(a, c)
