@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-per-frame", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-uneven", action="store_true")
+    p.add_argument("--no-tangent", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=10.0)
     return p.parse_args()
 
@@ -404,6 +405,7 @@ def run_ours(args, rank, world, local_rank):
 
     r.close()
     uneven = None if args.no_uneven else run_uneven(local_rank)
+    tangent = None if args.no_tangent else run_tangent(local_rank)
     serve = None if args.no_serve else run_serve(local_rank, args.serve_seconds)
 
     cpu = None
@@ -439,7 +441,7 @@ def run_ours(args, rank, world, local_rank):
                 "speedup_vs_per_frame": (value / per_frame["value"]) if per_frame else None,
                 "gpu_launches": launches_per_step * args.steps,
                 "launches_per_step": launches_per_step,
-                "serve": serve, "uneven": uneven,
+                "serve": serve, "uneven": uneven, "tangent": tangent,
                 "clocks": ck}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -527,6 +529,86 @@ def run_uneven(local_rank, steps=20):
             "img_per_s": len(batch.frames) * steps / t, "ms_per_step": 1e3 * t / steps,
             "pairs": pairs, "tuned": {"tile": list(tune.tile), "smem_batch": tune.smem_batch},
             "autotune_ms": tune.table}
+
+
+def run_tangent(local_rank, steps=50, anim_frames=64):
+    """The tangent-space path (Supp. "Gaussian Transformation", Alg. 1): N=60,000 Gaussians
+    bound to a 9,024-triangle head mesh whose expression changes per frame, K=32, B=16 at
+    512x512. Training: graph-replayed step with Adam against images of the reference avatar.
+    Animation (forward only, the paper's 'animation + rendering' path minus the 3DMM mesh and
+    the MLP, which are inputs here): one frame per call with its host sync, and 16 per call."""
+    import numpy as np
+    import torch
+    from paper_2503_12886_gb300 import api, synth
+    from paper_2503_12886_gb300.batching import GraphStep
+    from paper_2503_12886_gb300.optim import Adam
+    from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
+    dev = f"cuda:{local_rank}"
+    batch = synth.workload_tangent()
+    r = Renderer(local_rank)
+    ref = synth.Batch([synth.reference_avatar(batch.models[0], 6100)], batch.frames, batch.psi,
+                      batch.fparams, batch.k_stride)
+    timg, _, _ = r.forward(DeviceBatch(ref, dev, grads=False))
+    db = DeviceBatch(batch, dev)
+    gs = GraphStep(r, db, timg.clone(), optimizer=Adam(r, db), headroom=1.6)
+    for _ in range(3):
+        gs.replay()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        loss, pairs = gs.replay()
+    t_train = time.perf_counter() - t0
+    # animation: forward renders of the fitted avatar, new weights and mesh per frame
+    mesh_seed = 6000
+    mesh = synth.make_head_mesh(mesh_seed)
+    anim = synth.make_batch(batch.models, [synth.Frame(0, 512, 512, synth.frame_verts(mesh, mesh_seed, 100 + f))
+                                            for f in range(anim_frames)], 6200, jitter_deg=20.0,
+                            random_bg=True)
+    base = db.models
+
+    def run_calls(per_call):
+        calls = []
+        for f0 in range(0, anim_frames, per_call):
+            sub = synth.Batch(anim.models, anim.frames[f0:f0 + per_call], anim.psi[f0:f0 + per_call],
+                              anim.fparams[f0:f0 + per_call], anim.k_stride)
+            d = DeviceBatch(sub, dev, models=base, grads=False)
+            r.forward(d)  # sizes the workspace
+            calls.append((d, d.struct(), torch.empty(3 * d.total_pix, device=dev),
+                          torch.empty(d.total_pix, device=dev),
+                          torch.empty(d.total_pix, dtype=torch.int32, device=dev)))
+        ws = r.ws
+        s = torch.cuda.current_stream().cuda_stream
+        host = torch.zeros(24, dtype=torch.uint8).pin_memory()
+        lay = r.layout(calls[0][0])
+        lat = []
+        for rep in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for d, b, img, T, n in calls:
+                t1 = time.perf_counter()
+                api.rgba_preprocess(r.ctx, b, ws.data_ptr(), ws.numel(), s)
+                api.rgba_bin_sort(r.ctx, b, ws.data_ptr(), ws.numel(), s)
+                api.rgba_render_fwd(r.ctx, b, ws.data_ptr(), ws.numel(), img.data_ptr(), T.data_ptr(),
+                                    n.data_ptr(), s)
+                host.copy_(ws[lay.counters: lay.counters + 24], non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+                if host[:8].numpy().view(np.uint32)[1]:
+                    raise RuntimeError("animation render overflowed")
+                lat.append(time.perf_counter() - t1)
+            t = time.perf_counter() - t0
+        lat = np.asarray(lat[len(calls):]) * 1e3
+        return {"frames_per_s": anim_frames / t, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "frames_per_call": per_call}
+
+    one = run_calls(1)
+    many = run_calls(16)
+    r.close()
+    return {"workload": "N=60,000 Gaussians bound to a 9,024-triangle head mesh (expression per "
+                        "frame), K=32, B=16 at 512x512, tangent-space transform fused into the "
+                        "preprocess",
+            "train_img_per_s": len(batch.frames) * steps / t_train, "train_ms_per_step": 1e3 * t_train / steps,
+            "pairs": pairs, "last_loss": loss,
+            "animation_one_frame_per_call": one, "animation_16_frames_per_call": many}
 
 
 def run_serve(local_rank, seconds):
