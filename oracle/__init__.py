@@ -61,6 +61,7 @@ def lib():
             L.orc_project.argtypes = [i32, i32, P, P, i32, i32, P, P, P]
             L.orc_project_bwd.argtypes = [i32, i32, P, P, i32, i32, P, P, P, P]
             L.orc_tbn_all.argtypes = [i32, i32, P, P, P, P, P, P]
+            L.orc_color_accum.argtypes = [i32, i32, i32, i32, P, P, P, P, P]
             L.orc_bin.argtypes = [i32, P, P, i32, i32, P, P]
             L.orc_bin.restype = C.c_int64
             L.orc_render.argtypes = [i32, i32, i32, i32, P, P, P, P, P, f64, f64, P, P, P, P, P]
@@ -313,6 +314,40 @@ def backward(batch, res, dL_dimg, tile=(16, 16), tile_masks=None, params=None):
         for j, b in enumerate(fids):
             dpsi[b, :m.k] = dps[j]
     return per_model, dpsi, g2s, dgbs
+
+
+def color_accum(W, H, TW, TH, rec, tile_start, lst, target, n):
+    """Per Gaussian of one frame: [n][4] = (sum w, sum w I_r, sum w I_g, sum w I_b) over the
+    pixels that blend it, w = alpha T its splatting weight there, I the target (Eq. 3)."""
+    acc = np.zeros((n, 4), np.float64)
+    lst = np.ascontiguousarray(lst if len(lst) else np.zeros(1, np.int32), np.int32)
+    tg = np.ascontiguousarray(target, np.float64)
+    lib().orc_color_accum(W, H, TW, TH, _p(np.ascontiguousarray(rec, np.float64)), _p(tile_start),
+                          _p(lst), _p(tg), _p(acc))
+    return acc
+
+
+def color_init(batch, res, targets, done, delta=0.1, tile=(16, 16)):
+    """Colour initialisation (Sec. 3.2 "Initialization", Eq. 3) over one batch: for every model,
+    W_i and C_i = sums over all pixels of all its frames of w and w I; a Gaussian whose done flag
+    is clear and whose W_i exceeds delta gets colour C_i / W_i and its flag set (once only).
+    done: per model a bool array [n]. Returns per model (colour [3][n] or None where unchanged,
+    new done flags, W [n])."""
+    TW, TH = tile
+    out = []
+    for mi, m in enumerate(batch.models):
+        acc = np.zeros((m.n, 4), np.float64)
+        for b, fr in enumerate(batch.frames):
+            if fr.model != mi:
+                continue
+            r = res[b]
+            acc += color_accum(fr.width, fr.height, TW, TH, r.rec, r.tile_start, r.lst, targets[b], m.n)
+        W = acc[:, 0]
+        take = (~done[mi]) & (W > delta)
+        col = np.full((3, m.n), np.nan)
+        col[:, take] = (acc[take, 1:] / W[take, None]).T
+        out.append((col, done[mi] | take, W))
+    return out
 
 
 def decision_signature(res) -> int:

@@ -787,6 +787,40 @@ uint64_t orc_render(int W, int H, int TW, int TH, const double *rec, const int32
     return hash;
 }
 
+/* Colour initialisation (Sec. 3.2 "Initialization", Eq. 3), the sums of one frame: the same
+ * front-to-back compositing as orc_render, and for every Gaussian that a pixel blends, with its
+ * splatting weight w = alpha T at that pixel and the target colour I of the pixel,
+ *   acc[g][0] += w,  acc[g][1 + c] += w I_c        (target planar [3][H][W]).              */
+void orc_color_accum(int W, int H, int TW, int TH, const double *rec, const int32_t *tile_start,
+                     const int32_t *list, const double *target, double *acc) {
+    int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+    for (int ty = 0; ty < tiles_y; ++ty)
+        for (int tx = 0; tx < tiles_x; ++tx) {
+            int t = ty * tiles_x + tx;
+            for (int py = ty * TH; py < (ty + 1) * TH && py < H; ++py)
+                for (int px = tx * TW; px < (tx + 1) * TW && px < W; ++px) {
+                    size_t pix = (size_t)py * W + px;
+                    double T = 1.0;
+                    for (int32_t j = tile_start[t]; j < tile_start[t + 1]; ++j) {
+                        const double *g = rec + 12 * (size_t)list[j];
+                        double dx = px + 0.5 - g[0], dy = py + 0.5 - g[1];
+                        double power = -0.5 * (g[2] * dx * dx + g[4] * dy * dy) - g[3] * dx * dy;
+                        if (power > 0.0) continue;
+                        double araw = g[5] * exp(power);
+                        double alpha = araw < ALPHA_MAX ? araw : ALPHA_MAX;
+                        if (alpha < ALPHA_MIN) continue;
+                        double testT = T * (1.0 - alpha);
+                        if (testT < T_MIN) break;
+                        double w = alpha * T;
+                        double *a = acc + 4 * (size_t)list[j];
+                        a[0] += w;
+                        for (int c = 0; c < 3; ++c) a[1 + c] += w * target[(size_t)c * W * H + pix];
+                        T = testT;
+                    }
+                }
+        }
+}
+
 /* Exact derivative of the compositing above (reverse sweep over the contributors).
  * dL_dimg[3][H][W] -> grad2d[n][9] += dL/d(u, v, conic a, b, c, opacity, r, g, b).
  * The oracle keeps each pixel's contributors in a local list; the clamp at 0.99 passes no
