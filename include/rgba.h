@@ -251,6 +251,20 @@ int rgba_profile_enable(rgba_ctx_t ctx, int on);
 /* Waits for the recorded events, fills `out` (host) and resets the launch count. */
 int rgba_profile_read(rgba_ctx_t ctx, rgba_profile *out);
 
+/* Colour initialisation (Sec. 3.2 "Initialization", Eq. 3), synchronous. Renders the batch
+ * (preprocess, bin/sort, front-to-back compositing) and, for every Gaussian, sums over all
+ * pixels of all frames that render its model W = sum w and C = sum w I, with w the Gaussian's
+ * splatting weight alpha T at the pixel and I the pixel's colour in target (planar [3][H][W]
+ * per frame, frames concatenated as the images of rgba_render_fwd). A Gaussian whose done flag
+ * is 0 and whose W exceeds delta (the paper uses 0.1) gets base colour G0[11..13] = C / W and
+ * its flag set to 1; flags already set are never revisited, so each Gaussian is initialised
+ * once. done: host array [n_models] of device uint8[n] flag arrays (NULL skips a model).
+ * Writes models[m].g0 colour rows (cast from const). Uses the workspace's image regions and
+ * 2-D gradient slots as scratch. Returns like rgba_step (out->loss is 0). */
+int rgba_color_init(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
+                    const float *target, float delta, uint8_t *const *done, rgba_step_out *out,
+                    void *stream);
+
 /* Forward render that allocates nothing: for callers that cannot call cudaMalloc (code inside
  * another framework's memory pool, plugins whose host forbids device allocation, processes that
  * must not grow their device footprint). The paper has no counterpart; it is a deployment

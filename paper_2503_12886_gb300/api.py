@@ -25,7 +25,8 @@ RGBA_NCH = 14
 EXPORTS = ("rgba_last_error", "rgba_create", "rgba_destroy", "rgba_workspace_size",
            "rgba_workspace_layout", "rgba_blend", "rgba_preprocess", "rgba_bin_sort",
            "rgba_render_fwd", "rgba_render_bwd", "rgba_step", "rgba_step_async",
-           "rgba_profile_enable", "rgba_profile_read", "rgba_render_fwd_noalloc", "rgba_adam")
+           "rgba_profile_enable", "rgba_profile_read", "rgba_render_fwd_noalloc", "rgba_adam",
+           "rgba_color_init")
 RGBA_N_STAGES = 9
 STAGES = ("upload", "preprocess", "scan", "scatter", "sort", "render_fwd", "render_bwd",
           "gauss_bwd", "dpsi_reduce")
@@ -116,6 +117,8 @@ def lib() -> C.CDLL:
             L.rgba_adam.argtypes = [P, Bp, C.POINTER(RgbaAdamCfg), C.POINTER(RgbaAdamState), i32, P, P]
             L.rgba_adam.restype = i32
             L.rgba_render_fwd_noalloc.argtypes = [P, Bp, P, P, P, C.POINTER(RgbaStepOut), P]
+            L.rgba_color_init.argtypes = [P, Bp, P, sz, P, C.c_float, C.POINTER(P),
+                                          C.POINTER(RgbaStepOut), P]
             L.rgba_render_fwd_noalloc.restype = i32
             L.rgba_profile_enable.argtypes = [P, i32]
             L.rgba_profile_read.argtypes = [P, C.POINTER(RgbaProfile)]
@@ -187,6 +190,18 @@ def rgba_step(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream) -> tuple
     out = RgbaStepOut()
     rc = lib().rgba_step(ctx, C.byref(batch), ws, ws_bytes, target, loss_kind, img,
                          C.byref(out), stream)
+    if rc not in (RGBA_OK, RGBA_ERR_CAPACITY):
+        check(rc)
+    return rc, out
+
+
+def rgba_color_init(ctx, batch, ws, ws_bytes, target, delta, done, stream) -> tuple[int, RgbaStepOut]:
+    """done: per model a device pointer (uint8[n]) or None. Returns (status, out) like
+    rgba_step (RGBA_ERR_CAPACITY returned, not raised)."""
+    arr = (C.c_void_p * max(1, len(done)))(*done)
+    out = RgbaStepOut()
+    rc = lib().rgba_color_init(ctx, C.byref(batch), ws, ws_bytes, target, delta, arr,
+                               C.byref(out), stream)
     if rc not in (RGBA_OK, RGBA_ERR_CAPACITY):
         check(rc)
     return rc, out

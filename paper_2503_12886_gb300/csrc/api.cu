@@ -341,11 +341,12 @@ int do_bin_sort(rgba_ctx_t ctx, Call &k) {
     return RGBA_OK;
 }
 
-int do_render_fwd(rgba_ctx_t ctx, Call &k, float *img, float *T, int *n, const float *target, int loss_kind, float *dl) {
+int do_render_fwd(rgba_ctx_t ctx, Call &k, float *img, float *T, int *n, const float *target, int loss_kind, float *dl,
+                  const float *acc_target = nullptr) {
     int rc;
     if ((rc = memset_async(&k.c.cnt->next_fwd, 4, k.s, "memset fwd counter"))) return rc;
     StageScope sc(ctx, ST_FWD, k.s, 1);
-    cudaError_t e = launch_render_fwd(k.c, ctx->sms, k.p.L.smem_batch, img, T, n, target, loss_kind, dl, nullptr, k.s);
+    cudaError_t e = launch_render_fwd(k.c, ctx->sms, k.p.L.smem_batch, img, T, n, target, loss_kind, dl, acc_target, k.s);
     return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "render fwd");
 }
 
@@ -582,13 +583,8 @@ int rgba_step_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
     return do_render_bwd(ctx, k, dl, T, n);
 }
 
-int rgba_step(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *target,
-              int loss_kind, float *img, rgba_step_out *out, void *stream) {
-    if (!out) return fail(RGBA_ERR_INVALID_ARG, "out is NULL");
-    memset(out, 0, sizeof(*out));
-    int rc = rgba_step_async(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream);
-    if (rc) return rc;
-    if (batch->n_frames == 0) return RGBA_OK;
+// The one host synchronisation of a synchronous entry point: reads the counters into out.
+int read_out(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, rgba_step_out *out, void *stream) {
     Plan p;
     make_plan(batch, p);
     const long long cap = cap_for_bytes(p.L, ws_bytes);
@@ -607,8 +603,42 @@ int rgba_step(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes
         out->pairs_needed = h.pairs;
         return fail(RGBA_ERR_CAPACITY, "pair buffer too small: need " + std::to_string(h.pairs) + " pairs");
     }
-    if (h.device_error) return fail(RGBA_ERR_TIMEOUT, "device loop gave up");
+    if (h.device_error & 1u) return fail(RGBA_ERR_TIMEOUT, "device loop gave up");
+    if (h.device_error & 2u) return fail(RGBA_ERR_INVALID_ARG, "tangent-space binding index out of range");
     return RGBA_OK;
+}
+
+int rgba_step(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *target,
+              int loss_kind, float *img, rgba_step_out *out, void *stream) {
+    if (!out) return fail(RGBA_ERR_INVALID_ARG, "out is NULL");
+    memset(out, 0, sizeof(*out));
+    int rc = rgba_step_async(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream);
+    if (rc) return rc;
+    if (batch->n_frames == 0) return RGBA_OK;
+    return read_out(ctx, batch, ws, ws_bytes, out, stream);
+}
+
+int rgba_color_init(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *target,
+                    float delta, uint8_t *const *done, rgba_step_out *out, void *stream) {
+    if (!out) return fail(RGBA_ERR_INVALID_ARG, "out is NULL");
+    memset(out, 0, sizeof(*out));
+    Call k;
+    int rc = prologue(ctx, batch, ws, ws_bytes, stream, k);
+    if (rc || k.p.L.B == 0) return rc;
+    if (!target || !done) return fail(RGBA_ERR_INVALID_ARG, "target/done is NULL");
+    if (!(delta >= 0.f)) return fail(RGBA_ERR_INVALID_ARG, "delta must be >= 0");
+    const Layout &L = k.p.L;
+    if ((rc = do_preprocess(ctx, k))) return rc;
+    if ((rc = do_bin_sort(ctx, k))) return rc;
+    if ((rc = memset_async(k.ws + L.grad2d, sizeof(float) * kG2Floats * (size_t)L.R, k.s, "memset accumulators")))
+        return rc;
+    if ((rc = do_render_fwd(ctx, k, reinterpret_cast<float *>(k.ws + L.pix_img), reinterpret_cast<float *>(k.ws + L.pix_T),
+                            reinterpret_cast<int *>(k.ws + L.pix_n), nullptr, 0, nullptr, target)))
+        return rc;
+    ctx->launches += 1;
+    cudaError_t e = launch_color_finish(k.c, k.p.max_n, delta, done, (int)k.p.models.size(), k.s);
+    if (e != cudaSuccess) return cuda_fail(e, "colour finish");
+    return read_out(ctx, batch, ws, ws_bytes, out, stream);
 }
 
 }  // extern "C"

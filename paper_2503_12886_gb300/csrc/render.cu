@@ -79,9 +79,11 @@ struct PixF {
     bool inside, done;
 };
 
-// One list entry for one pixel (forward); marks the pixel done when it saturates.
+// One list entry for one pixel (forward); marks the pixel done when it saturates. w receives
+// the entry's splatting weight alpha T at the pixel (0 when it does not blend).
 __device__ __forceinline__ void composite(PixF &p, const float4 *s_a, const float2 *s_q,
-                                          const float4 *s_c, int j, int pos) {
+                                          const float4 *s_c, int j, int pos, float &w) {
+    w = 0.0f;
     const float4 A = s_a[j];
     const float2 Q = s_q[j];
     const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
@@ -95,6 +97,7 @@ __device__ __forceinline__ void composite(PixF &p, const float4 *s_a, const floa
         return;
     }
     const float wgt = alpha * p.T;
+    w = wgt;
     p.C0 = fmaf(Cc.y, wgt, p.C0);
     p.C1 = fmaf(Cc.z, wgt, p.C1);
     p.C2 = fmaf(Cc.w, wgt, p.C2);
@@ -163,6 +166,24 @@ __device__ __forceinline__ void commit(const Stage<S> &g, int lo, int hi, float4
     }
 }
 
+// Warp sum of v[0..3] as a reduce-scatter: lane l ends with the total of value (l >> 3) & 3.
+__device__ __forceinline__ float warp_reduce4(const float v[4], int lane) {
+    const unsigned F = 0xffffffffu;
+    const bool h16 = lane & 16, h8 = lane & 8;
+    float a[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = h16 ? v[i] : v[i + 2];
+        const float keep = h16 ? v[i + 2] : v[i];
+        a[i] = keep + __shfl_xor_sync(F, send, 16);
+    }
+    float m = (h8 ? a[1] : a[0]) + __shfl_xor_sync(F, h8 ? a[0] : a[1], 8);
+    m += __shfl_xor_sync(F, m, 4);
+    m += __shfl_xor_sync(F, m, 2);
+    m += __shfl_xor_sync(F, m, 1);
+    return m;
+}
+
 // Writes one finished pixel (colour over the background, T, contributor count) and, with a
 // target, its loss term and dL/dpixel.
 __device__ __forceinline__ void finish_pixel(const Ctx &c, const FrameInfo &f, int b, int px, int py,
@@ -200,19 +221,25 @@ __device__ __forceinline__ void finish_pixel(const Ctx &c, const FrameInfo &f, i
 
 // Items: the pixel blocks of the non-empty tiles (work list order, heaviest tiles first), then
 // one item per empty tile, which the warp fills with the background eight pixels per lane.
-template <int TW, int BATCH>
+// ACC (colour initialisation, Eq. 3): every blended entry also adds its splatting weight w and
+// w times the pixel's colour in acc_target to the record's first four 2-D gradient slots
+// (one warp reduction and four atomics per entry and pixel block).
+template <int TW, int BATCH, bool ACC>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *__restrict__ n_contrib,
-             const float *__restrict__ target, int loss_kind, float *__restrict__ dl_dimg) {
+             const float *__restrict__ target, int loss_kind, float *__restrict__ dl_dimg,
+             const float *__restrict__ acc_target) {
     constexpr int TH = kTilePix / TW, BH = 4, NBX = TW / 8, NB = NBX * (TH / BH), S = BATCH / 32;
     __shared__ float4 s_a[kWarpsPerCta][BATCH];
     __shared__ float2 s_q[kWarpsPerCta][BATCH];
     __shared__ float4 s_c[kWarpsPerCta][BATCH];
+    __shared__ unsigned s_idx[kWarpsPerCta][ACC ? BATCH : 1];
     __shared__ float s_red[kWarpsPerCta];
     if (c.cnt->overflow) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float4 *wa = s_a[wid], *wc = s_c[wid];
     float2 *wq = s_q[wid];
+    unsigned *widx = ACC ? s_idx[wid] : nullptr;
     const unsigned n_work = c.cnt->n_work, n_blocks = n_work * NB;
     const unsigned n_items = n_blocks + ((unsigned)c.T - n_work);
     float loss_acc = 0.0f;
@@ -248,6 +275,15 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
         const float bx0 = (float)bx + 0.5f, bx1 = (float)bx + 7.5f, by0 = (float)by + 0.5f, by1 = (float)by + 3.5f;
         PixF p{(float)px + 0.5f, (float)py + 0.5f, 1.f, 0.f, 0.f, 0.f, 0, px < f.W && py < f.H, false};
         p.done = !p.inside;
+        float I0 = 0.f, I1 = 0.f, I2 = 0.f;  // ACC: the pixel's target colour
+        if (ACC && p.inside) {
+            const long long hw = (long long)f.W * f.H;
+            const float *tg = acc_target + f.pix_base * 3 + (long long)py * f.W + px;
+            I0 = tg[0];
+            I1 = tg[hw];
+            I2 = tg[2 * hw];
+        }
+        float *acc = c.grad2d + (size_t)f.rec_base * kG2Floats;
         const unsigned st = c.tile_start[t];
         const int len = (int)(c.tile_start[t + 1] - st);
         const float4 *rec = c.records + (size_t)f.rec_base * 3;
@@ -260,7 +296,7 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
             if (__all_sync(0xffffffffu, p.done)) break;
             unsigned hit[S];
             __syncwarp();  // the previous batch's slots are no longer read
-            commit<S>(g, lo, len, wa, wq, wc, nullptr, bx0, bx1, by0, by1, hit);
+            commit<S>(g, lo, len, wa, wq, wc, widx, bx0, bx1, by0, by1, hit);
             load_rec<S>(rec, lo + BATCH, len, nidx, g);
             load_idx<S>(c, lo + 2 * BATCH, len, st, nidx);
             __syncwarp();
@@ -271,7 +307,13 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
                 while (hm) {
                     const int j = 32 * q + __ffs(hm) - 1;
                     hm &= hm - 1;
-                    if (!p.done) composite(p, wa, wq, wc, j, pos0 + j);
+                    float w = 0.0f;
+                    if (!p.done) composite(p, wa, wq, wc, j, pos0 + j, w);
+                    if (ACC && __any_sync(0xffffffffu, w > 0.0f)) {
+                        const float v[4] = {w, w * I0, w * I1, w * I2};
+                        const float mine = warp_reduce4(v, lane);
+                        if ((lane & 7) == 0) atomicAdd(acc + (size_t)widx[j] * kG2Floats + (lane >> 3), mine);
+                    }
                 }
             }
         }
@@ -481,13 +523,26 @@ int persistent_grid(K kernel, int sms_hint, int threads, int &cached) {
     return cached;
 }
 
-template <int TW, int BATCH>
+template <int TW, int BATCH, bool ACC>
 cudaError_t fwd_inst(const Ctx &c, int grid, float *img, float *T, int *n, const float *tg, int lk,
-                     float *dl, cudaStream_t s) {
+                     float *dl, const float *acc_tg, cudaStream_t s) {
     static int cached = 0;
-    const int g = persistent_grid(k_render_fwd<TW, BATCH>, grid, 32 * kWarpsPerCta, cached);
-    k_render_fwd<TW, BATCH><<<g, 32 * kWarpsPerCta, 0, s>>>(c, img, T, n, tg, lk, dl);
+    const int g = persistent_grid(k_render_fwd<TW, BATCH, ACC>, grid, 32 * kWarpsPerCta, cached);
+    k_render_fwd<TW, BATCH, ACC><<<g, 32 * kWarpsPerCta, 0, s>>>(c, img, T, n, tg, lk, dl, acc_tg);
     return cudaGetLastError();
+}
+
+template <bool ACC>
+cudaError_t fwd_dispatch(const Ctx &c, int grid, int sb, float *img, float *T, int *n, const float *tg,
+                         int lk, float *dl, const float *acc_tg, cudaStream_t s) {
+    if (c.tw == 16) {
+        if (sb == 64) return fwd_inst<16, 64, ACC>(c, grid, img, T, n, tg, lk, dl, acc_tg, s);
+        if (sb == 128) return fwd_inst<16, 128, ACC>(c, grid, img, T, n, tg, lk, dl, acc_tg, s);
+        return fwd_inst<16, 256, ACC>(c, grid, img, T, n, tg, lk, dl, acc_tg, s);
+    }
+    if (sb == 64) return fwd_inst<8, 64, ACC>(c, grid, img, T, n, tg, lk, dl, acc_tg, s);
+    if (sb == 128) return fwd_inst<8, 128, ACC>(c, grid, img, T, n, tg, lk, dl, acc_tg, s);
+    return fwd_inst<8, 256, ACC>(c, grid, img, T, n, tg, lk, dl, acc_tg, s);
 }
 
 constexpr int kBwdPixPerLane = 1;  // 8 x 4 blocks: twice the items of 8 x 8, fewer registers
@@ -505,15 +560,12 @@ cudaError_t bwd_inst(const Ctx &c, int grid, const float *dl, const float *T, co
 
 cudaError_t launch_render_fwd(const Ctx &c, int grid, int smem_batch, float *img, float *T_final,
                               int *n_contrib, const float *target, int loss_kind,
-                              float *dl_dimg, const long long *, cudaStream_t s) {
-    if (c.tw == 16) {
-        if (smem_batch == 64) return fwd_inst<16, 64>(c, grid, img, T_final, n_contrib, target, loss_kind, dl_dimg, s);
-        if (smem_batch == 128) return fwd_inst<16, 128>(c, grid, img, T_final, n_contrib, target, loss_kind, dl_dimg, s);
-        return fwd_inst<16, 256>(c, grid, img, T_final, n_contrib, target, loss_kind, dl_dimg, s);
-    }
-    if (smem_batch == 64) return fwd_inst<8, 64>(c, grid, img, T_final, n_contrib, target, loss_kind, dl_dimg, s);
-    if (smem_batch == 128) return fwd_inst<8, 128>(c, grid, img, T_final, n_contrib, target, loss_kind, dl_dimg, s);
-    return fwd_inst<8, 256>(c, grid, img, T_final, n_contrib, target, loss_kind, dl_dimg, s);
+                              float *dl_dimg, const float *acc_target, cudaStream_t s) {
+    if (acc_target)
+        return fwd_dispatch<true>(c, grid, smem_batch, img, T_final, n_contrib, target, loss_kind, dl_dimg,
+                                  acc_target, s);
+    return fwd_dispatch<false>(c, grid, smem_batch, img, T_final, n_contrib, target, loss_kind, dl_dimg,
+                               nullptr, s);
 }
 
 cudaError_t launch_render_bwd(const Ctx &c, int grid, int smem_batch, const float *dl_dimg,

@@ -119,7 +119,9 @@ cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s);
 cudaError_t launch_tile_sort(const Ctx &c, int sms, cudaStream_t s);
 cudaError_t launch_render_fwd(const Ctx &c, int grid, int smem_batch, float *img, float *T_final,
                               int *n_contrib, const float *target, int loss_kind,
-                              float *dl_dimg, const long long *pix_base_dummy, cudaStream_t s);
+                              float *dl_dimg, const float *acc_target, cudaStream_t s);
+cudaError_t launch_color_finish(const Ctx &c, int max_n, float delta, const uint8_t *const *done_host,
+                                int n_models, cudaStream_t s);
 cudaError_t launch_render_bwd(const Ctx &c, int grid, int smem_batch, const float *dl_dimg,
                               const float *T_final, const int *n_contrib, cudaStream_t s);
 cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_n, int max_k, cudaStream_t s);

@@ -206,6 +206,20 @@ class Renderer:
             self.ensure_workspace(db, int(cnt["pairs"] * 1.25) + 4096)
         raise api.RgbaError(api.RGBA_ERR_CAPACITY, "workspace growth did not converge")
 
+    def color_init(self, db: DeviceBatch, target: torch.Tensor, done: list, delta: float = 0.1):
+        """Colour initialisation (Eq. 3) of every model of the batch from the target images;
+        done: per model a CUDA uint8 tensor [n] of flags (or None), updated in place. Regrows the
+        workspace and retries on a pair overflow. Returns the pair count."""
+        ptrs = [d.data_ptr() if d is not None else None for d in done]
+        for _ in range(3):
+            ws = self.ensure_workspace(db)
+            rc, out = api.rgba_color_init(self.ctx, db.struct(), ws.data_ptr(), ws.numel(),
+                                          target.data_ptr(), float(delta), ptrs, stream_ptr())
+            if rc == api.RGBA_OK:
+                return int(out.pairs)
+            self.ensure_workspace(db, int(out.pairs_needed * 1.25) + 4096)
+        raise api.RgbaError(api.RGBA_ERR_CAPACITY, "workspace growth did not converge")
+
     def backward(self, db: DeviceBatch, dl_dimg: torch.Tensor, T: torch.Tensor, n: torch.Tensor):
         b = db.struct()
         api.rgba_render_bwd(self.ctx, b, self.ws.data_ptr(), self.ws.numel(),
