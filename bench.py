@@ -53,7 +53,8 @@ def parse():
     p.add_argument("--no-per-frame", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-uneven", action="store_true")
-    p.add_argument("--no-tangent", action="store_true")
+    p.add_argument("--no-tangent", action="store_true", help="skip the tangent-space and "
+                   "colour-initialisation sections")
     p.add_argument("--serve-seconds", type=float, default=10.0)
     return p.parse_args()
 
@@ -406,6 +407,7 @@ def run_ours(args, rank, world, local_rank):
     r.close()
     uneven = None if args.no_uneven else run_uneven(local_rank)
     tangent = None if args.no_tangent else run_tangent(local_rank)
+    color_init = None if args.no_tangent else run_color_init(local_rank)
     serve = None if args.no_serve else run_serve(local_rank, args.serve_seconds)
 
     cpu = None
@@ -441,7 +443,7 @@ def run_ours(args, rank, world, local_rank):
                 "speedup_vs_per_frame": (value / per_frame["value"]) if per_frame else None,
                 "gpu_launches": launches_per_step * args.steps,
                 "launches_per_step": launches_per_step,
-                "serve": serve, "uneven": uneven, "tangent": tangent,
+                "serve": serve, "uneven": uneven, "tangent": tangent, "color_init": color_init,
                 "clocks": ck}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -609,6 +611,40 @@ def run_tangent(local_rank, steps=50, anim_frames=64):
             "train_img_per_s": len(batch.frames) * steps / t_train, "train_ms_per_step": 1e3 * t_train / steps,
             "pairs": pairs, "last_loss": loss,
             "animation_one_frame_per_call": one, "animation_16_frames_per_call": many}
+
+
+def run_color_init(local_rank, reps=20):
+    """Colour initialisation (Eq. 3, delta 0.1) over the batched workload's 16 frames at
+    512x512: one rgba_color_init call per rep (render with weight accumulation + per-Gaussian
+    finish + its host sync), flags reset between reps so every call does the full work."""
+    import torch
+    from paper_2503_12886_gb300 import synth
+    from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
+    dev = f"cuda:{local_rank}"
+    batch = synth.workload_batched()
+    r = Renderer(local_rank)
+    ref = synth.Batch([synth.reference_avatar(batch.models[0], 3999)], batch.frames, batch.psi,
+                      batch.fparams, batch.k_stride)
+    timg, _, _ = r.forward(DeviceBatch(ref, dev, grads=False))
+    db = DeviceBatch(batch, dev, grads=False)
+    done = [torch.zeros(m.n_pad, dtype=torch.uint8, device=dev) for m in db.models]
+    g0 = db.models[0].g0.clone()
+    r.color_init(db, timg, done)
+    n_done = int(done[0].sum())
+    torch.cuda.synchronize()
+    t = 0.0
+    for _ in range(reps):
+        done[0].zero_()
+        db.models[0].g0.copy_(g0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r.color_init(db, timg, done)
+        t += time.perf_counter() - t0
+    r.close()
+    return {"workload": "batched workload (N=60,000, B=16 at 512x512), targets = reference-avatar "
+                        "images, delta = 0.1",
+            "ms_per_call": 1e3 * t / reps, "frames_per_s": len(batch.frames) * reps / t,
+            "initialised": n_done, "n": batch.models[0].n}
 
 
 def run_serve(local_rank, seconds):
