@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-per-frame", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-uneven", action="store_true")
+    p.add_argument("--no-online", action="store_true")
     p.add_argument("--no-tangent", action="store_true", help="skip the tangent-space and "
                    "colour-initialisation sections")
     p.add_argument("--serve-seconds", type=float, default=10.0)
@@ -408,6 +409,7 @@ def run_ours(args, rank, world, local_rank):
     uneven = None if args.no_uneven else run_uneven(local_rank)
     tangent = None if args.no_tangent else run_tangent(local_rank)
     color_init = None if args.no_tangent else run_color_init(local_rank)
+    online = None if args.no_online else run_online(local_rank)
     serve = None if args.no_serve else run_serve(local_rank, args.serve_seconds)
 
     cpu = None
@@ -444,6 +446,7 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": launches_per_step * args.steps,
                 "launches_per_step": launches_per_step,
                 "serve": serve, "uneven": uneven, "tangent": tangent, "color_init": color_init,
+                "online": online,
                 "clocks": ck}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -645,6 +648,84 @@ def run_color_init(local_rank, reps=20):
                         "images, delta = 0.1",
             "ms_per_call": 1e3 * t / reps, "frames_per_s": len(batch.frames) * reps / t,
             "initialised": n_done, "n": batch.models[0].n}
+
+
+def run_online(local_rank, seconds=10.0, fps=25.0, batch=16):
+    """Online reconstruction (Sec. 3.3, Alg. 2): frames of a 25 FPS stream (renders of the
+    reference avatar at new weights, poses and backgrounds, arriving in real time) enter the
+    local/global pools; every training step (graph-replayed, Adam) takes a batch of 16 with
+    eta = 0.7 from the pools. The stream starts with 16 frames already received."""
+    import numpy as np
+    import torch
+    from paper_2503_12886_gb300 import synth
+    from paper_2503_12886_gb300.batching import GraphStep
+    from paper_2503_12886_gb300.online import LocalGlobalSampler
+    from paper_2503_12886_gb300.optim import Adam
+    from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
+    dev = f"cuda:{local_rank}"
+    n_frames = int(seconds * fps) + batch
+    stream = synth.workload_batched(seed=7000, frames=n_frames)
+    model = stream.models[0]
+    ref = synth.reference_avatar(model, 7001)
+    r = Renderer(local_rank)
+    # the store: every frame's target (rendered when it arrives), weights and camera
+    px = 3 * RES * RES
+    store_tg = torch.empty(n_frames, px, device=dev)
+    store_psi = torch.from_numpy(stream.psi).to(dev)
+    store_fp = torch.from_numpy(stream.fparams).to(dev)
+    one = [synth.Batch([ref], [stream.frames[f]], stream.psi[f:f + 1], stream.fparams[f:f + 1],
+                       stream.k_stride) for f in range(n_frames)]
+    ref_dm = None
+
+    def receive(f):
+        nonlocal ref_dm
+        d = DeviceBatch(one[f], dev, grads=False, models=ref_dm)
+        ref_dm = d.models
+        img, _, _ = r.forward(d)
+        store_tg[f].copy_(img)
+        sampler.push(f)
+
+    sampler = LocalGlobalSampler(150, 1000, 0.7, seed=7002)
+    for f in range(batch):
+        receive(f)
+    step_batch = synth.Batch([model], stream.frames[:batch], stream.psi[:batch], stream.fparams[:batch],
+                             stream.k_stride)
+    db = DeviceBatch(step_batch, dev)
+    tg = torch.empty(batch * px, device=dev)
+
+    def load(idx):
+        it = torch.as_tensor(idx, device=dev)
+        tg.view(batch, px).copy_(store_tg.index_select(0, it))
+        db.psi.copy_(store_psi.index_select(0, it))
+        db.fparams.copy_(store_fp.index_select(0, it))
+
+    load(sampler.sample(batch))
+    gs = GraphStep(r, db, tg, optimizer=Adam(r, db), headroom=1.6)
+    received, steps, ages = batch, 0, []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        if now >= seconds:
+            break
+        while received < n_frames and received - batch < now * fps:
+            receive(received)
+            received += 1
+        idx = sampler.sample(batch)
+        ages.extend(received - 1 - np.asarray(idx))
+        load(idx)
+        loss, pairs = gs.replay()
+        steps += 1
+    t = time.perf_counter() - t0
+    r.close()
+    ages = np.asarray(ages)
+    return {"workload": "25 FPS stream of 512x512 frames (reference-avatar renders, new weights, "
+                        "poses, backgrounds), local pool 150 / global pool 1000, eta 0.7, "
+                        "B=16 per step, N=60,000, K=32",
+            "seconds": t, "frames_received": received, "steps": steps, "steps_per_s": steps / t,
+            "img_per_s": steps * batch / t, "steps_per_frame": steps / max(1, received - batch),
+            "sample_age_frames": {"median": float(np.median(ages)), "p90": float(np.percentile(ages, 90))},
+            "last_loss": loss}
 
 
 def run_serve(local_rank, seconds):
