@@ -119,3 +119,25 @@ def test_uneven_workload_sampled_frames(renderer):
         o = oracle.forward(sub, splat="spec", tile_masks={0: mask})
         s = compare_images(sub, o, _view_batch(db, b), img, T, n, tiles_only=[pix])
         assert s["max_err"] <= 1e-4 and s["n_mismatch"] == 0, (b, s)
+
+
+def test_tangent_workload_full_size(renderer):
+    """The bench's tangent-space workload (N=60,000 bound to a 9,024-triangle mesh, K=32,
+    B=16 at 512x512): every decision and list bit-exact, pixels of the densest tile block of
+    three frames."""
+    batch = synth.workload_tangent()
+    db = DeviceBatch(batch, "cuda:0", tile=(16, 16), smem_batch=64, grads=False)
+    img, T, n = renderer.forward(db)
+    torch.cuda.synchronize()
+    inter = read_intermediates(renderer, db)
+    ores = oracle.forward(batch, do_render=False)
+    st = compare_decisions(batch, ores, inter, db)
+    assert st["pairs"] > 3_000_000
+    for b in (0, 8, 15):
+        fr = batch.frames[b]
+        mask, pix, _ = _block_mask(fr, ores[b], 16, 16)
+        sub = synth.Batch(batch.models, [fr], batch.psi[b:b + 1], batch.fparams[b:b + 1], batch.k_stride)
+        o = oracle.forward(sub, splat="spec", tile_masks={0: mask})
+        s = compare_images(sub, o, _view_batch(db, b), img, T, n, tiles_only=[pix])
+        assert s["max_err"] <= 1e-4 and s["n_mismatch"] == 0, (b, s)
+        assert s["flagged"] <= 0.005 * s["pixels"]
