@@ -293,7 +293,9 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-__global__ void __launch_bounds__(kBwdThreads)
+// 3 CTAs per SM (80 registers, a few spills to L1) beat 2 CTAs without spills: the kernel
+// waits on memory and needs the warps.
+__global__ void __launch_bounds__(kBwdThreads, 3)
 k_gauss_bwd(Ctx c, int max_k) {
     extern __shared__ float smem[];
     float *s_dG = smem;                                   // [16][14][32]
