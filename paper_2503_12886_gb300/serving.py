@@ -63,6 +63,9 @@ class Server:
     def __init__(self, avatars: list[synth.Model], device: int = 0, hbm_budget: float = 40e9,
                  max_frames: int = 32, slots: int = 2, max_res: int = 1024, tile=(16, 16),
                  smem_batch: int = 64, pairs_per_gaussian: float = 4.0):
+        if any(m.binding is not None for m in avatars):
+            raise ValueError("the server renders world-space avatars; a tangent-space avatar "
+                             "needs a deformed mesh per request")
         self.device = device
         dev = f"cuda:{device}"
         self.r = Renderer(device)
