@@ -165,6 +165,7 @@ int make_plan(const rgba_batch *b, Plan &p) {
     L.tile_start = take(4 * (size_t)(T + 1));
     L.cursor = take(4 * (size_t)T * kSubCounters);
     L.work = take(4 * (size_t)T);
+    L.scan_aux = take(scan_aux_bytes(T));
     L.records = take(sizeof(float) * kRecFloats * (size_t)R);
     L.rects = take(8 * (size_t)R);
     L.cache = take(sizeof(float) * kCacheFloats * (size_t)R);
@@ -216,6 +217,7 @@ Ctx make_ctx(const Layout &L, unsigned char *ws, const rgba_batch *b) {
     c.tile_start = reinterpret_cast<unsigned *>(ws + L.tile_start);
     c.cursor = reinterpret_cast<unsigned *>(ws + L.cursor);
     c.work = reinterpret_cast<unsigned *>(ws + L.work);
+    c.scan_aux = ws + L.scan_aux;
     c.records = reinterpret_cast<float4 *>(ws + L.records);
     c.rects = reinterpret_cast<ushort4 *>(ws + L.rects);
     c.cache = reinterpret_cast<float4 *>(ws + L.cache);
@@ -328,7 +330,7 @@ int do_bin_sort(rgba_ctx_t ctx, Call &k) {
     cudaError_t e;
     int rc;
     {
-        StageScope sc(ctx, ST_SCAN, k.s, 2);
+        StageScope sc(ctx, ST_SCAN, k.s, 3);
         if ((e = launch_scan(k.c, k.s)) != cudaSuccess) return cuda_fail(e, "scan");
     }
     {

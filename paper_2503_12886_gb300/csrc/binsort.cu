@@ -3,96 +3,194 @@
 // tile of its rectangle and each (frame, tile) list is ordered by (depth bits, Gaussian index).
 //
 // Design: the per-tile counts come out of the preprocess kernel (atomics whose return values
-// give each Gaussian its slot in up to 8 tiles), one CTA scans them into list offsets and a
-// work list, a scatter kernel drops (depth << 32 | index) keys into their tile's segment (by
+// give each Gaussian its slot in up to 8 tiles), a three-phase scan (per-CTA partials, one CTA
+// over the partials, per-CTA writes) turns them into list offsets and a work list, a scatter
+// kernel drops (depth << 32 | index) keys into their tile's segment (by
 // slot, or by a cursor atomic for larger rectangles), and one CTA per non-empty tile sorts its
-// shared memory, or through L2 for long segments (a stable LSD radix sort on the key compressed
-// to (depth - segment minimum, index); a bitonic network when that key would need more than 64
-// bits). Because the key carries the index, the result is unique.
+// list in shared memory, or through L2 for long segments: a stable LSD radix sort over the
+// depth bits of the key compressed to (depth - segment minimum) << 32 | index, then a pass
+// that orders runs of equal depth by index. Because the key carries the index, the result is
+// unique.
 #include "rgba_internal.cuh"
 
 namespace rgba {
 namespace {
 
-constexpr int kScanThreads = 1024;
+constexpr int kScanTile = 1024;  // tiles per CTA of the three-phase scan
 
-// Per tile (one thread each, coalesced): the total count into tile_start (the scan below turns
-// it into the list start) and, for the larger rectangles, each sub-counter's fill offset
-// relative to the tile's start (after the ranked slots).
-__global__ void k_tile_totals(Ctx c) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= c.T) return;
-    const unsigned *sub = c.tile_count + c.T + t * kSubCounters;
-    unsigned v = c.tile_count[t];
+// Exclusive scan over the CTA (kScanTile threads) of one (u64 value, u32 count) pair per
+// thread: warp shuffles, then the 32 warp totals scanned by warp 0. Also returns the totals.
+__device__ __forceinline__ void block_scan(unsigned long long v, unsigned e, unsigned long long &ex_v,
+                                           unsigned &ex_e, unsigned long long &tot_v, unsigned &tot_e) {
+    __shared__ unsigned long long s_v[32];
+    __shared__ unsigned s_e[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long xv = v;
+    unsigned xe = e;
 #pragma unroll
-    for (int q = 0; q < kSubCounters; ++q) {
-        c.cursor[t * kSubCounters + q] = v;
-        v += sub[q];
-    }
-    c.tile_start[t] = v;
-}
-
-// Exclusive scan of the tile counts (frame-major), pair total and capacity check, and the work
-// list: non-empty tiles first, longest lists first (bucketed by floor(log2(length))), then the
-// empty tiles in tile order. The persistent kernels pull items in this order, so the heaviest
-// tiles start first and the tail of the launch is short.
-__global__ void __launch_bounds__(kScanThreads) k_scan(Ctx c) {
-    __shared__ unsigned long long s_sum[kScanThreads];
-    __shared__ unsigned s_ne[kScanThreads];
-    __shared__ unsigned s_hist[32];
-    const long long T = c.T;
-    const int tid = threadIdx.x;
-    const long long per = (T + kScanThreads - 1) / kScanThreads;
-    const long long lo = tid * per, hi = (lo + per < T) ? lo + per : T;
-    if (tid < 32) s_hist[tid] = 0;
-    __syncthreads();
-    unsigned long long sum = 0;
-    unsigned ne = 0;
-    for (long long t = lo; t < hi; ++t) {
-        unsigned v = c.tile_start[t];  // the tile's total (k_tile_totals)
-        sum += v;
-        ne += v > 0;
-        if (v > 0) atomicAdd(&s_hist[31 - __clz(v)], 1u);
-    }
-    s_sum[tid] = sum;
-    s_ne[tid] = ne;
-    __syncthreads();
-    // Hillis-Steele inclusive scan over the 1024 partials
-    for (int off = 1; off < kScanThreads; off <<= 1) {
-        unsigned long long a = tid >= off ? s_sum[tid - off] : 0ull;
-        unsigned b = tid >= off ? s_ne[tid - off] : 0u;
-        __syncthreads();
-        s_sum[tid] += a;
-        s_ne[tid] += b;
-        __syncthreads();
-    }
-    if (tid == 0) {  // bucket offsets, longest bucket first
-        unsigned off = 0;
-        for (int k = 31; k >= 0; --k) {
-            const unsigned h = s_hist[k];
-            s_hist[k] = off;
-            off += h;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long yv = __shfl_up_sync(0xffffffffu, xv, o);
+        const unsigned ye = __shfl_up_sync(0xffffffffu, xe, o);
+        if (lane >= o) {
+            xv += yv;
+            xe += ye;
         }
     }
-    __syncthreads();
-    const unsigned long long total = s_sum[kScanThreads - 1];
-    const unsigned n_ne = s_ne[kScanThreads - 1];
-    unsigned long long run = s_sum[tid] - sum;
-    unsigned ne_run = s_ne[tid] - ne;
-    unsigned e_run = (unsigned)lo - ne_run;  // empty tiles before lo
-    for (long long t = lo; t < hi; ++t) {
-        const unsigned v = c.tile_start[t];
-        unsigned st = run > 0xffffffffull ? 0xffffffffu : (unsigned)run;
-        c.tile_start[t] = st;
-        if (v > 0) c.work[atomicAdd(&s_hist[31 - __clz(v)], 1u)] = (unsigned)t;
-        else c.work[n_ne + e_run++] = (unsigned)t;
-        run += v;
+    if (lane == 31) {
+        s_v[warp] = xv;
+        s_e[warp] = xe;
     }
-    if (tid == 0) {
-        c.tile_start[T] = total > 0xffffffffull ? 0xffffffffu : (unsigned)total;
-        c.cnt->pairs = total > 0xffffffffull ? 0xffffffffu : (unsigned)total;
-        c.cnt->overflow = total > (unsigned long long)c.cap ? 1u : 0u;
-        c.cnt->n_work = n_ne;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long wv = s_v[lane];
+        unsigned we = s_e[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long yv = __shfl_up_sync(0xffffffffu, wv, o);
+            const unsigned ye = __shfl_up_sync(0xffffffffu, we, o);
+            if (lane >= o) {
+                wv += yv;
+                we += ye;
+            }
+        }
+        s_v[lane] = wv;
+        s_e[lane] = we;
+    }
+    __syncthreads();
+    ex_v = (warp ? s_v[warp - 1] : 0ull) + xv - v;
+    ex_e = (warp ? s_e[warp - 1] : 0u) + xe - e;
+    tot_v = s_v[31];
+    tot_e = s_e[31];
+    __syncthreads();  // s_v / s_e free for the next call
+}
+
+// The scan's per-CTA partials: [nb] sums, [nb] non-empty counts, [nb][32] bucket counts and
+// the [32] bucket offsets, in the workspace.
+struct ScanAux {
+    unsigned long long *bsum;
+    unsigned *bne, *bhist, *bucket;
+};
+
+__device__ __forceinline__ ScanAux scan_aux(const Ctx &c) {
+    const long long nb = (c.T + kScanTile - 1) / kScanTile;
+    ScanAux a;
+    a.bsum = reinterpret_cast<unsigned long long *>(c.scan_aux);
+    a.bne = reinterpret_cast<unsigned *>(a.bsum + nb);
+    a.bhist = a.bne + nb;
+    a.bucket = a.bhist + nb * 32;
+    return a;
+}
+
+__device__ __forceinline__ unsigned bucket_of(unsigned v) { return 31u - __clz(v); }
+
+// Phase 1, one thread per tile: the tile's total count (ranked slots plus sub-counters) into
+// tile_start, each sub-counter's fill offset into cursor, and per CTA the sum, the number of
+// non-empty tiles and the histogram of floor(log2(length)).
+__global__ void __launch_bounds__(kScanTile) k_scan_blocks(Ctx c) {
+    __shared__ unsigned s_hist[32];
+    const ScanAux a = scan_aux(c);
+    if (threadIdx.x < 32) s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    const long long t = (long long)blockIdx.x * kScanTile + threadIdx.x;
+    unsigned v = 0;
+    if (t < c.T) {
+        const unsigned *sub = c.tile_count + c.T + t * kSubCounters;
+        v = c.tile_count[t];
+#pragma unroll
+        for (int q = 0; q < kSubCounters; ++q) {
+            c.cursor[t * kSubCounters + q] = v;
+            v += sub[q];
+        }
+        c.tile_start[t] = v;
+        if (v) atomicAdd(&s_hist[bucket_of(v)], 1u);
+    }
+    unsigned long long ex, tot;
+    unsigned exe, tote;
+    block_scan(v, v > 0, ex, exe, tot, tote);
+    if (threadIdx.x == 0) {
+        a.bsum[blockIdx.x] = tot;
+        a.bne[blockIdx.x] = tote;
+    }
+    if (threadIdx.x < 32) a.bhist[blockIdx.x * 32 + threadIdx.x] = s_hist[threadIdx.x];
+}
+
+// Phase 2, one CTA: exclusive scans over the CTAs of phase 1 (sums, non-empty counts, and per
+// bucket the counts, warp w taking bucket w), the bucket offsets with the longest bucket first,
+// the pair total, the capacity check and the work-list length.
+__global__ void __launch_bounds__(kScanTile) k_scan_top(Ctx c) {
+    __shared__ unsigned s_btot[32];
+    const ScanAux a = scan_aux(c);
+    const long long nb = (c.T + kScanTile - 1) / kScanTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long carry = 0;
+    unsigned carry_e = 0;
+    for (long long b0 = 0; b0 < nb; b0 += kScanTile) {
+        const long long b = b0 + threadIdx.x;
+        const unsigned long long v = b < nb ? a.bsum[b] : 0ull;
+        const unsigned e = b < nb ? a.bne[b] : 0u;
+        unsigned long long ex, tot;
+        unsigned exe, tote;
+        block_scan(v, e, ex, exe, tot, tote);
+        if (b < nb) {
+            a.bsum[b] = carry + ex;
+            a.bne[b] = carry_e + exe;
+        }
+        carry += tot;
+        carry_e += tote;
+    }
+    {
+        unsigned run = 0;  // warp w: bucket w, lane = CTA within a chunk of 32
+        for (long long b0 = 0; b0 < nb; b0 += 32) {
+            const long long b = b0 + lane;
+            const unsigned h = b < nb ? a.bhist[b * 32 + warp] : 0u;
+            unsigned x = h;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (b < nb) a.bhist[b * 32 + warp] = run + x - h;
+            run += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) s_btot[warp] = run;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned off = 0;
+        for (int k = 31; k >= 0; --k) {
+            a.bucket[k] = off;
+            off += s_btot[k];
+        }
+        c.tile_start[c.T] = carry > 0xffffffffull ? 0xffffffffu : (unsigned)carry;
+        c.cnt->pairs = carry > 0xffffffffull ? 0xffffffffu : (unsigned)carry;
+        c.cnt->overflow = carry > (unsigned long long)c.cap ? 1u : 0u;
+        c.cnt->n_work = carry_e;
+    }
+}
+
+// Phase 3, one thread per tile: the list start (exclusive scan of the totals) and the tile's
+// place in the work list: non-empty tiles by bucket, longest bucket first (in any order within
+// a bucket), then the empty tiles in tile order.
+__global__ void __launch_bounds__(kScanTile) k_scan_write(Ctx c) {
+    __shared__ unsigned s_off[32];
+    const ScanAux a = scan_aux(c);
+    const long long t = (long long)blockIdx.x * kScanTile + threadIdx.x;
+    const unsigned v = t < c.T ? c.tile_start[t] : 0u;
+    if (threadIdx.x < 32) s_off[threadIdx.x] = a.bucket[threadIdx.x] + a.bhist[blockIdx.x * 32 + threadIdx.x];
+    const bool empty = t < c.T && v == 0;
+    unsigned long long ex, tot;
+    unsigned exe, tote;
+    block_scan(v, empty, ex, exe, tot, tote);  // its syncs also publish s_off
+    if (t < c.T) {
+        const unsigned long long st = a.bsum[blockIdx.x] + ex;
+        c.tile_start[t] = st > 0xffffffffull ? 0xffffffffu : (unsigned)st;
+        if (v) {
+            c.work[atomicAdd(&s_off[bucket_of(v)], 1u)] = (unsigned)t;
+        } else {
+            // empty tiles before this CTA: its first tile index minus the non-empty ones
+            const unsigned e0 = (unsigned)((long long)blockIdx.x * kScanTile) - a.bne[blockIdx.x];
+            c.work[c.cnt->n_work + e0 + exe] = (unsigned)t;
+        }
     }
 }
 
@@ -360,11 +458,19 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
 }  // namespace
 
 cudaError_t launch_scan(const Ctx &c, cudaStream_t s) {
-    k_tile_totals<<<(unsigned)((c.T + 255) / 256), 256, 0, s>>>(c);
+    const unsigned nb = (unsigned)((c.T + kScanTile - 1) / kScanTile);
+    k_scan_blocks<<<nb, kScanTile, 0, s>>>(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_scan<<<1, kScanThreads, 0, s>>>(c);
+    k_scan_top<<<1, kScanTile, 0, s>>>(c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_scan_write<<<nb, kScanTile, 0, s>>>(c);
     return cudaGetLastError();
+}
+
+size_t scan_aux_bytes(long long T) {
+    const long long nb = (T + kScanTile - 1) / kScanTile;
+    return (size_t)nb * 8 + (size_t)nb * 4 + (size_t)nb * 32 * 4 + 32 * 4;
 }
 
 cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s) {

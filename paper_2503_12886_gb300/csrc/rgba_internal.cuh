@@ -73,7 +73,7 @@ static_assert(sizeof(Counters) <= 256, "counters fit in one 256-byte block");
 struct Layout {
     size_t counters, models, frames, mframes, tile_count, tile_start, cursor, work;
     size_t records, rects, cache, grad2d, ranks, pix_T, pix_n, pix_dl, pix_img, dpsi_part;
-    size_t keys, keys2, sorted, total;
+    size_t keys, keys2, sorted, scan_aux, total;
     long long R, T, P;     // records, tiles, pixels
     long long dpsi_floats;
     long long cap;
@@ -94,6 +94,7 @@ struct Ctx {
     unsigned *tile_start;
     unsigned *cursor;      // [T][kSubCounters]: fill positions of the larger rectangles
     unsigned *work;
+    unsigned char *scan_aux;  // the tile scan's per-CTA partials
     float4 *records;   // [R][3]
     ushort4 *rects;    // [R]
     float4 *cache;     // [R][3]
@@ -115,6 +116,7 @@ cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t
 cudaError_t launch_preprocess(const Ctx &c, int max_n, int max_k, int max_rows, cudaStream_t s);
 cudaError_t launch_blend(const Ctx &c, int max_n, float *out, cudaStream_t s);
 cudaError_t launch_scan(const Ctx &c, cudaStream_t s);
+size_t scan_aux_bytes(long long T);
 cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s);
 cudaError_t launch_tile_sort(const Ctx &c, int sms, cudaStream_t s);
 cudaError_t launch_render_fwd(const Ctx &c, int grid, int smem_batch, float *img, float *T_final,
