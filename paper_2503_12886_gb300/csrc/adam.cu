@@ -38,6 +38,7 @@ __device__ __forceinline__ void adam4(float4 &p, const float4 g, float4 &m, floa
 
 __global__ void k_adam(AdamChunk ch, float b1, float b2, float eps, float ibc1, float ibc2,
                        const int *step_dev) {
+    pdl_enter();
     if (step_dev) {  // t = completed steps + 1, read from the device (graph replays advance it)
         // 1 - b^t = -expm1(t log1p(b - 1)): no cancellation when b^t is close to 1 (1 - b is
         // exact in binary32 for b in [0.5, 1])
@@ -80,7 +81,10 @@ __global__ void k_adam(AdamChunk ch, float b1, float b2, float eps, float ibc1, 
     }
 }
 
-__global__ void k_step_advance(int *step_dev) { *step_dev += 1; }
+__global__ void k_step_advance(int *step_dev) {
+    pdl_enter();
+    *step_dev += 1;
+}
 
 }  // namespace
 
@@ -114,14 +118,12 @@ cudaError_t launch_adam(const ModelInfo *models, int n_models, const rgba_adam_c
             for (int a = 0; a < mi.A; ++a) M.lrd[a] = cfg.lr_delta[mi.chans[a]];
         }
         dim3 grid(sms * 4, nm);
-        k_adam<<<grid, 256, 0, s>>>(ch, cfg.beta1, cfg.beta2, cfg.eps, (float)(1.0 / bc1),
-                                    (float)(1.0 / bc2), step_dev);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(k_adam, grid, dim3(256), 0, s, ch, cfg.beta1, cfg.beta2, cfg.eps,
+                                   (float)(1.0 / bc1), (float)(1.0 / bc2), (const int *)step_dev);
         if (e != cudaSuccess) return e;
     }
     if (step_dev) {
-        k_step_advance<<<1, 1, 0, s>>>(step_dev);
-        return cudaGetLastError();
+        return launch_pdl(k_step_advance, dim3(1), dim3(1), 0, s, step_dev);
     }
     return cudaSuccess;
 }

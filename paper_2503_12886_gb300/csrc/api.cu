@@ -328,7 +328,6 @@ int do_preprocess(rgba_ctx_t ctx, Call &k) {
 
 int do_bin_sort(rgba_ctx_t ctx, Call &k) {
     cudaError_t e;
-    int rc;
     {
         StageScope sc(ctx, ST_SCAN, k.s, 3);
         if ((e = launch_scan(k.c, k.s)) != cudaSuccess) return cuda_fail(e, "scan");
@@ -337,7 +336,6 @@ int do_bin_sort(rgba_ctx_t ctx, Call &k) {
         StageScope sc(ctx, ST_SCATTER, k.s, 1);
         if ((e = launch_scatter(k.c, k.p.max_n, k.s)) != cudaSuccess) return cuda_fail(e, "scatter");
     }
-    if ((rc = memset_async(&k.c.cnt->next_sort, 4, k.s, "memset sort counter"))) return rc;
     StageScope sc(ctx, ST_SORT, k.s, 1);
     if ((e = launch_tile_sort(k.c, ctx->sms, k.s)) != cudaSuccess) return cuda_fail(e, "tile sort");
     return RGBA_OK;
@@ -345,18 +343,19 @@ int do_bin_sort(rgba_ctx_t ctx, Call &k) {
 
 int do_render_fwd(rgba_ctx_t ctx, Call &k, float *img, float *T, int *n, const float *target, int loss_kind, float *dl,
                   const float *acc_target = nullptr) {
-    int rc;
-    if ((rc = memset_async(&k.c.cnt->next_fwd, 4, k.s, "memset fwd counter"))) return rc;
     StageScope sc(ctx, ST_FWD, k.s, 1);
     cudaError_t e = launch_render_fwd(k.c, ctx->sms, k.p.L.smem_batch, img, T, n, target, loss_kind, dl, acc_target, k.s);
     return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "render fwd");
 }
 
-int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, const int *n) {
+// g2_zeroed: the preprocess of the same call zeroed the 2-D gradients (the fused step); a
+// standalone backward clears them itself.
+int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, const int *n, bool g2_zeroed = false) {
     int rc;
     const Layout &L = k.p.L;
-    if ((rc = memset_async(&k.c.cnt->next_bwd, 4, k.s, "memset bwd counter"))) return rc;
-    if ((rc = memset_async(k.ws + L.grad2d, sizeof(float) * kG2Floats * (size_t)L.R, k.s, "memset grad2d"))) return rc;
+    if (!g2_zeroed &&
+        (rc = memset_async(k.ws + L.grad2d, sizeof(float) * kG2Floats * (size_t)L.R, k.s, "memset grad2d")))
+        return rc;
     cudaError_t e;
     {
         StageScope sc(ctx, ST_BWD, k.s, 1);
@@ -582,7 +581,7 @@ int rgba_step_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
     if ((rc = do_preprocess(ctx, k))) return rc;
     if ((rc = do_bin_sort(ctx, k))) return rc;
     if ((rc = do_render_fwd(ctx, k, im, T, n, target, loss_kind, dl))) return rc;
-    return do_render_bwd(ctx, k, dl, T, n);
+    return do_render_bwd(ctx, k, dl, T, n, true);
 }
 
 // The one host synchronisation of a synchronous entry point: reads the counters into out.
@@ -632,8 +631,7 @@ int rgba_color_init(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
     const Layout &L = k.p.L;
     if ((rc = do_preprocess(ctx, k))) return rc;
     if ((rc = do_bin_sort(ctx, k))) return rc;
-    if ((rc = memset_async(k.ws + L.grad2d, sizeof(float) * kG2Floats * (size_t)L.R, k.s, "memset accumulators")))
-        return rc;
+    // the accumulators (the records' 2-D gradient slots) were zeroed by the preprocess
     if ((rc = do_render_fwd(ctx, k, reinterpret_cast<float *>(k.ws + L.pix_img), reinterpret_cast<float *>(k.ws + L.pix_T),
                             reinterpret_cast<int *>(k.ws + L.pix_n), nullptr, 0, nullptr, target)))
         return rc;

@@ -303,6 +303,7 @@ k_gauss_bwd(Ctx c, int max_k) {
     __shared__ long long s_rec[kFG2];
     __shared__ int s_wh[kFG2][2];
     __shared__ const float *s_verts[kFG2];
+    pdl_enter();
     __shared__ float s_fp[kFG2][RGBA_FP_STRIDE];
     const ModelInfo &m = c.models[blockIdx.y];
     const int chunk = blockIdx.x;
@@ -464,6 +465,7 @@ constexpr int kDpsiThreads = 256;
 // a warp-shuffle and shared-memory sum.
 __global__ void __launch_bounds__(kDpsiThreads) k_dpsi_reduce(Ctx c) {
     __shared__ float s_w[kDpsiThreads / 32];
+    pdl_enter();
     const int kk = blockIdx.x, b = blockIdx.y;
     const FrameInfo &f = c.frames[b];
     const ModelInfo &m = c.models[f.model];
@@ -504,15 +506,13 @@ cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_n, int max_k,
         attr_device = dev;
     }
     dim3 g2(max_chunks, c.M);
-    k_gauss_bwd<<<g2, kBwdThreads, bytes(max_k), s>>>(c, max_k);
-    return cudaGetLastError();
+    return launch_pdl(k_gauss_bwd, g2, dim3(kBwdThreads), (size_t)bytes(max_k), s, c, max_k);
 }
 
 cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s) {
     (void)max_k;
     if (!c.grad_psi || c.B == 0 || c.k_stride == 0) return cudaSuccess;
-    k_dpsi_reduce<<<dim3(c.k_stride, c.B), kDpsiThreads, 0, s>>>(c);
-    return cudaGetLastError();
+    return launch_pdl(k_dpsi_reduce, dim3(c.k_stride, c.B), dim3(kDpsiThreads), 0, s, c);
 }
 
 }  // namespace rgba

@@ -88,6 +88,7 @@ __device__ __forceinline__ unsigned bucket_of(unsigned v) { return 31u - __clz(v
 // non-empty tiles and the histogram of floor(log2(length)).
 __global__ void __launch_bounds__(kScanTile) k_scan_blocks(Ctx c) {
     __shared__ unsigned s_hist[32];
+    pdl_enter();
     const ScanAux a = scan_aux(c);
     if (threadIdx.x < 32) s_hist[threadIdx.x] = 0;
     __syncthreads();
@@ -119,6 +120,7 @@ __global__ void __launch_bounds__(kScanTile) k_scan_blocks(Ctx c) {
 // the pair total, the capacity check and the work-list length.
 __global__ void __launch_bounds__(kScanTile) k_scan_top(Ctx c) {
     __shared__ unsigned s_btot[32];
+    pdl_enter();
     const ScanAux a = scan_aux(c);
     const long long nb = (c.T + kScanTile - 1) / kScanTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -173,6 +175,7 @@ __global__ void __launch_bounds__(kScanTile) k_scan_top(Ctx c) {
 // a bucket), then the empty tiles in tile order.
 __global__ void __launch_bounds__(kScanTile) k_scan_write(Ctx c) {
     __shared__ unsigned s_off[32];
+    pdl_enter();
     const ScanAux a = scan_aux(c);
     const long long t = (long long)blockIdx.x * kScanTile + threadIdx.x;
     const unsigned v = t < c.T ? c.tile_start[t] : 0u;
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(kScanTile) k_scan_write(Ctx c) {
 constexpr int kScatterThreads = 128;
 
 __global__ void __launch_bounds__(kScatterThreads) k_scatter(Ctx c) {
+    pdl_enter();
     if (c.cnt->overflow) return;
     const int b = blockIdx.y;
     const FrameInfo f = c.frames[b];
@@ -363,6 +367,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
     unsigned *s_cnt = reinterpret_cast<unsigned *>(s_keys + 2 * kRadixCap);
     unsigned short *s_rank = reinterpret_cast<unsigned short *>(s_cnt + kSortWarps * 256 + kSortWarps);
     __shared__ unsigned s_w, s_dmin, s_dmax, s_imax, s_long;
+    pdl_enter();
     if (c.cnt->overflow) return;
     const unsigned n_work = c.cnt->n_work;
     if (threadIdx.x == 0) {
@@ -453,19 +458,21 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
         }
         __syncthreads();
     }
+    // the last CTA out puts the work counter back to zero for the next launch
+    if (threadIdx.x == 0 && atomicAdd(&c.cnt->done_sort, 1u) == gridDim.x - 1) {
+        c.cnt->next_sort = 0u;
+        c.cnt->done_sort = 0u;
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_scan(const Ctx &c, cudaStream_t s) {
     const unsigned nb = (unsigned)((c.T + kScanTile - 1) / kScanTile);
-    k_scan_blocks<<<nb, kScanTile, 0, s>>>(c);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_scan_blocks, dim3(nb), dim3(kScanTile), 0, s, c);
     if (e != cudaSuccess) return e;
-    k_scan_top<<<1, kScanTile, 0, s>>>(c);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_scan_write<<<nb, kScanTile, 0, s>>>(c);
-    return cudaGetLastError();
+    if ((e = launch_pdl(k_scan_top, dim3(1), dim3(kScanTile), 0, s, c)) != cudaSuccess) return e;
+    return launch_pdl(k_scan_write, dim3(nb), dim3(kScanTile), 0, s, c);
 }
 
 size_t scan_aux_bytes(long long T) {
@@ -476,8 +483,7 @@ size_t scan_aux_bytes(long long T) {
 cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s) {
     if (c.B == 0 || max_n == 0) return cudaSuccess;
     dim3 grid((max_n + kScatterThreads - 1) / kScatterThreads, c.B);
-    k_scatter<<<grid, kScatterThreads, 0, s>>>(c);
-    return cudaGetLastError();
+    return launch_pdl(k_scatter, grid, dim3(kScatterThreads), 0, s, c);
 }
 
 cudaError_t launch_tile_sort(const Ctx &c, int sms, cudaStream_t s) {
@@ -495,8 +501,7 @@ cudaError_t launch_tile_sort(const Ctx &c, int sms, cudaStream_t s) {
         per_sm = per_sm < 1 ? 1 : per_sm;
         attr_device = dev;
     }
-    k_tile_sort<<<sms * per_sm, kSortThreads, smem, s>>>(c);
-    return cudaGetLastError();
+    return launch_pdl(k_tile_sort, dim3(sms * per_sm), dim3(kSortThreads), (size_t)smem, s, c);
 }
 
 }  // namespace rgba

@@ -54,6 +54,7 @@ struct UploadBlob {
 };
 
 __global__ void k_upload_param(uint4 *dst, UploadBlob blob, int n16) {
+    pdl_enter();  // the previous step's kernels may still read the tables
     int i = threadIdx.x;
     if (i < n16) dst[i] = blob.data[i];
 }
@@ -144,6 +145,10 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const ModelInfo &
     c.cache[r * 3 + 0] = make_float4(v[0], v[1], v[2], v[3]);
     c.cache[r * 3 + 1] = make_float4(v[4], v[5], v[6], v[7]);
     c.cache[r * 3 + 2] = make_float4(v[8], v[9], 0.f, 0.f);
+    {  // the record's 2-D gradient slots start at zero for the compositing backward's atomics
+        float4 *g = reinterpret_cast<float4 *>(c.grad2d + r * kG2Floats);
+        g[0] = g[1] = g[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     ushort4 rc = make_ushort4(0, 0, 0, 0);
     do {
@@ -345,6 +350,7 @@ k_preprocess(Ctx c, int max_k) {
     extern __shared__ float4 smem4[];
     __shared__ __align__(8) unsigned long long s_bar;
     __shared__ FrameConst s_fc[kPreRound];
+    pdl_enter();
     const ModelInfo &m = c.models[blockIdx.y];
     const int i0 = blockIdx.x * kPreG;
     if (i0 >= m.n || m.nb == 0) return;
@@ -508,8 +514,8 @@ cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t
         size_t n16 = (n + 15) / 16;
         memset(&blob, 0, sizeof(blob));
         memcpy(&blob, p + off, n);
-        k_upload_param<<<1, 256, 0, s>>>(reinterpret_cast<uint4 *>(d + off), blob, (int)n16);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(k_upload_param, dim3(1), dim3(256), 0, s, reinterpret_cast<uint4 *>(d + off),
+                                   blob, (int)n16);
         if (e != cudaSuccess) return e;
         off += n16 * 16;
     }
@@ -533,8 +539,7 @@ cudaError_t launch_preprocess(const Ctx &c, int max_n, int max_k, int max_rows, 
         attr_device = dev;
     }
     dim3 grid((max_n + kPreG - 1) / kPreG, c.M);
-    k_preprocess<<<grid, kPreBlock, preprocess_smem(max_k, max_rows), s>>>(c, max_k);
-    return cudaGetLastError();
+    return launch_pdl(k_preprocess, grid, dim3(kPreBlock), preprocess_smem(max_k, max_rows), s, c, max_k);
 }
 
 cudaError_t launch_blend(const Ctx &c, int max_n, float *out, cudaStream_t s) {

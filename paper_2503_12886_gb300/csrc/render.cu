@@ -235,6 +235,7 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
     __shared__ float4 s_c[kWarpsPerCta][BATCH];
     __shared__ unsigned s_idx[kWarpsPerCta][ACC ? BATCH : 1];
     __shared__ float s_red[kWarpsPerCta];
+    pdl_enter();
     if (c.cnt->overflow) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float4 *wa = s_a[wid], *wc = s_c[wid];
@@ -319,6 +320,11 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
         }
         if (p.inside)
             finish_pixel(c, f, b, px, py, p, img, T_final, n_contrib, target, loss_kind, dl_dimg, loss_acc);
+    }
+    // the last warp out puts the work counter back to zero for the next launch
+    if (lane == 0 && atomicAdd(&c.cnt->done_fwd, 1u) == gridDim.x * kWarpsPerCta - 1) {
+        c.cnt->next_fwd = 0u;
+        c.cnt->done_fwd = 0u;
     }
     if (target) {
         for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
@@ -414,6 +420,7 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
     __shared__ float2 s_q[kWarpsPerCta][BATCH];
     __shared__ float4 s_c[kWarpsPerCta][BATCH];
     __shared__ unsigned s_idx[kWarpsPerCta][BATCH];
+    pdl_enter();
     if (c.cnt->overflow) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float4 *wa = s_a[wid], *wc = s_c[wid];
@@ -505,6 +512,11 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
             }
         }
     }
+    // the last warp out puts the work counter back to zero for the next launch
+    if (lane == 0 && atomicAdd(&c.cnt->done_bwd, 1u) == gridDim.x * kWarpsPerCta - 1) {
+        c.cnt->next_bwd = 0u;
+        c.cnt->done_bwd = 0u;
+    }
 }
 
 // Persistent grid: every CTA the SMs can hold at once (occupancy query, cached by the caller
@@ -528,8 +540,8 @@ cudaError_t fwd_inst(const Ctx &c, int grid, float *img, float *T, int *n, const
                      float *dl, const float *acc_tg, cudaStream_t s) {
     static int cached = 0;
     const int g = persistent_grid(k_render_fwd<TW, BATCH, ACC>, grid, 32 * kWarpsPerCta, cached);
-    k_render_fwd<TW, BATCH, ACC><<<g, 32 * kWarpsPerCta, 0, s>>>(c, img, T, n, tg, lk, dl, acc_tg);
-    return cudaGetLastError();
+    return launch_pdl(k_render_fwd<TW, BATCH, ACC>, dim3(g), dim3(32 * kWarpsPerCta), 0, s, c, img, T, n, tg, lk, dl,
+                      acc_tg);
 }
 
 template <bool ACC>
@@ -552,8 +564,7 @@ cudaError_t bwd_inst(const Ctx &c, int grid, const float *dl, const float *T, co
                      cudaStream_t s) {
     static int cached = 0;
     const int g = persistent_grid(k_render_bwd<TW, BATCH, kBwdPixPerLane>, grid, 32 * kWarpsPerCta, cached);
-    k_render_bwd<TW, BATCH, kBwdPixPerLane><<<g, 32 * kWarpsPerCta, 0, s>>>(c, dl, T, n);
-    return cudaGetLastError();
+    return launch_pdl(k_render_bwd<TW, BATCH, kBwdPixPerLane>, dim3(g), dim3(32 * kWarpsPerCta), 0, s, c, dl, T, n);
 }
 
 }  // namespace

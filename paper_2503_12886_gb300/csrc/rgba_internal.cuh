@@ -66,7 +66,10 @@ struct Counters {
     unsigned next_sort;   // dynamic work counters of the persistent kernels
     unsigned next_fwd;
     unsigned next_bwd;
-    unsigned pad_[9];
+    unsigned done_sort;   // CTAs / warps of each persistent kernel that ran out of work: the
+    unsigned done_fwd;    // last one to leave puts its kernel's counters back to zero, so
+    unsigned done_bwd;    // every launch starts from zero without a memset
+    unsigned pad_[6];
 };
 static_assert(sizeof(Counters) <= 256, "counters fit in one 256-byte block");
 
@@ -107,6 +110,33 @@ struct Ctx {
     long long R, T, cap;
     int B, M, k_stride, tw, th;
 };
+
+// Programmatic dependent launch (Hopper/Blackwell): a kernel launched with launch_pdl may be
+// scheduled while the previous kernel in its stream drains; every kernel starts with pdl_wait(),
+// which returns once the previous grid has completed and its writes are visible (a no-op for
+// kernels launched without the attribute), then releases its own dependents (pdl_release).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+    pdl_wait();
+    pdl_release();
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // Records msg as the calling thread's rgba_last_error() text and returns code.
 int set_error(int code, const char *msg);
