@@ -387,14 +387,13 @@ def run_ours(args, rank, world, local_rank):
         host_in.append((tgs[dbs.index(db)].cpu().pin_memory(), db.psi.cpu().pin_memory(),
                         db.fparams.cpu().pin_memory()))
     h2d = sum(x.numel() * x.element_size() for x in host_in[0])
-    e2e_cnt = torch.zeros(24, dtype=torch.uint8).pin_memory()
     cs = torch.cuda.Stream(device=dev)  # copy stream: step i + 1's inputs travel during step i
     n_e2e = max(10, min(args.steps, 100))
     with torch.cuda.stream(s):
-        e2e_run(api, r, dbs, tgs, structs, host_in, ws, img, s, cs, 3, opt, lay, e2e_cnt)
+        e2e_run(dbs, tgs, host_in, s, cs, 3, cap, host_cnt, capture)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e2e_run(api, r, dbs, tgs, structs, host_in, ws, img, s, cs, n_e2e, opt, lay, e2e_cnt)
+        e2e_run(dbs, tgs, host_in, s, cs, n_e2e, cap, host_cnt, capture)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
     e2e_value = world * FRAMES * n_e2e / t_e2e
@@ -438,9 +437,10 @@ def run_ours(args, rank, world, local_rank):
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "img/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": 24, "steps": n_e2e,
-                        "path": "rgba_step_async + rgba_adam through the C ABI, every step's "
-                                "inputs copied from pinned host (on a copy stream, overlapping "
-                                "the previous step), counters read back, one sync per step"},
+                        "path": "captured step graphs (rgba_step_async + rgba_adam through the C "
+                                "ABI, one per input variant), every step's inputs copied from "
+                                "pinned host on a copy stream while the previous step computes, "
+                                "counters read back, one sync per step"},
                 "per_frame": per_frame,
                 "speedup_vs_per_frame": (value / per_frame["value"]) if per_frame else None,
                 "gpu_launches": launches_per_step * args.steps,
@@ -453,12 +453,13 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def e2e_run(api, r, dbs, tgs, structs, host_in, ws, img, s, cs, steps, opt, lay, cnt_host):
-    """`steps` training steps end to end: every step's inputs (targets, weights, cameras) are
-    copied from pinned host memory on the copy stream cs while the previous step computes on s
-    (the input variants rotate, so a buffer is refilled only after the step that read it has
-    been synchronised); each step then waits for its copies, runs rgba_step_async + Adam, reads
-    its counters back and synchronises once."""
+def e2e_run(dbs, tgs, host_in, s, cs, steps, cap, host_cnt, capture):
+    """`steps` training steps end to end through the captured step graphs (rgba_step_async +
+    rgba_adam + the counter read, one graph per input variant): every step's inputs (targets,
+    weights, cameras) are copied from pinned host memory on the copy stream cs while the
+    previous step computes on s (the variants rotate, so a variant's buffers are refilled only
+    after the step that read them has been synchronised); each step waits for its copies,
+    replays its graph and synchronises once to read its loss and pair count."""
     import numpy as np
     import torch
     nv = len(dbs)
@@ -479,13 +480,14 @@ def e2e_run(api, r, dbs, tgs, structs, host_in, ws, img, s, cs, steps, opt, lay,
         nxt = issue(i + 1) if i + 1 < steps else None
         j = i % nv
         s.wait_event(ready)
-        api.rgba_step_async(r.ctx, structs[j], ws.data_ptr(), ws.numel(), tgs[j].data_ptr(),
-                            api.RGBA_LOSS_L1, img.data_ptr(), s.cuda_stream)
-        opt.step(s.cuda_stream)
-        cnt_host.copy_(ws[lay.counters: lay.counters + 24], non_blocking=True)
-        s.synchronize()  # the step's one host synchronisation: its loss and pair count
-        if cnt_host[:8].numpy().view(np.uint32)[1]:
-            raise RuntimeError("e2e step overflowed")
+        while True:
+            cap["graphs"][j].replay()
+            s.synchronize()  # the step's one host synchronisation: its loss and pair count
+            u = host_cnt[j][:8].numpy().view(np.uint32)
+            if not u[1]:
+                break
+            cap["regrow"] += 1
+            capture(int(u[0] * 1.3) + 4096)
         ready = nxt
 
 
