@@ -338,8 +338,11 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
     }
 }
 
+// Backward state of one pixel: its dL/dcolour g, T_final times g . background (TB), the
+// transmittance T in front of the current entry and P = g . S, S the colour accumulated behind
+// it (only that dot product enters the alpha gradient).
 struct PixB {
-    float pxc, pyc, T, Tfin, g0, g1, g2, bgdot, S0, S1, S2;
+    float pxc, pyc, T, TB, g0, g1, g2, P;
     int last;
 };
 
@@ -351,10 +354,8 @@ __device__ __forceinline__ bool accumulate(PixB &p, int pos, const float4 &A, co
     const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
     const float power = power_of(dx, dy, A, Q);
     if (skip(power, Q.y)) return false;
-    const float4 Bv = make_float4(Q.x, Cc.x, Cc.y, Cc.z);  // -c/2, opacity, r, g
-    const float cb = Cc.w;
     const float G = __expf(power);
-    const float araw = __fmul_rn(Bv.y, G);
+    const float araw = __fmul_rn(Cc.x, G);
     const float alpha = fminf(kAlphaMax, araw);
     const float oma = 1.0f - alpha;
     const float inv = __fdividef(1.0f, oma);  // 1 - alpha >= 0.01
@@ -363,20 +364,20 @@ __device__ __forceinline__ bool accumulate(PixB &p, int pos, const float4 &A, co
     v[6] = fmaf(wgt, p.g0, v[6]);
     v[7] = fmaf(wgt, p.g1, v[7]);
     v[8] = fmaf(wgt, p.g2, v[8]);
-    float dalpha = p.T * (p.g0 * (Bv.z - p.S0) + p.g1 * (Bv.w - p.S1) + p.g2 * (cb - p.S2));
-    dalpha -= p.Tfin * inv * p.bgdot;
-    p.S0 = fmaf(alpha, Bv.z, oma * p.S0);
-    p.S1 = fmaf(alpha, Bv.w, oma * p.S1);
-    p.S2 = fmaf(alpha, cb, oma * p.S2);
+    // dL/dalpha = T (g . c - g . S) - T_final / (1 - alpha) g . bg, then S <- alpha c + (1-alpha) S
+    const float gc = fmaf(p.g2, Cc.w, fmaf(p.g1, Cc.z, p.g0 * Cc.y));
+    const float dalpha = fmaf(p.T, gc - p.P, -p.TB * inv);
+    p.P = fmaf(alpha, gc, oma * p.P);
     if (!(araw > kAlphaMax)) {
         v[5] = fmaf(dalpha, G, v[5]);
-        const float dpow = dalpha * Bv.y * G;
-        v[2] = fmaf(-0.5f * dx * dx, dpow, v[2]);
+        const float dpow = dalpha * araw;
+        const float hx = -0.5f * dx, hy = -0.5f * dy;
+        v[2] = fmaf(hx * dx, dpow, v[2]);
         v[3] = fmaf(-dx * dy, dpow, v[3]);
-        v[4] = fmaf(-0.5f * dy * dy, dpow, v[4]);
-        // conic a = -2 A.z, b = -A.w, c = -2 B.x
+        v[4] = fmaf(hy * dy, dpow, v[4]);
+        // conic a = -2 A.z, b = -A.w, c = -2 Q.x
         v[0] = fmaf(-dpow, 2.0f * A.z * dx + A.w * dy, v[0]);
-        v[1] = fmaf(-dpow, 2.0f * Bv.x * dy + A.w * dx, v[1]);
+        v[1] = fmaf(-dpow, 2.0f * Q.x * dy + A.w * dx, v[1]);
     }
     return true;
 }
@@ -453,17 +454,17 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
 #pragma unroll
         for (int h = 0; h < PXL; ++h) {
             const int py = py0 + h * 4;
-            p[h] = PixB{(float)px + 0.5f, (float)py + 0.5f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+            p[h] = PixB{(float)px + 0.5f, (float)py + 0.5f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
             if (px < f.W && py < f.H) {
                 const long long pix = (long long)py * f.W + px;
-                p[h].Tfin = T_final[f.pix_base + pix];
-                p[h].T = p[h].Tfin;
+                const float Tfin = T_final[f.pix_base + pix];
+                p[h].T = Tfin;
                 p[h].last = n_contrib[f.pix_base + pix];
                 const float *dl = dl_dimg + f.pix_base * 3 + pix;
                 p[h].g0 = dl[0];
                 p[h].g1 = dl[hw];
                 p[h].g2 = dl[2 * hw];
-                p[h].bgdot = p[h].g0 * bgp[0] + p[h].g1 * bgp[1] + p[h].g2 * bgp[2];
+                p[h].TB = Tfin * (p[h].g0 * bgp[0] + p[h].g1 * bgp[1] + p[h].g2 * bgp[2]);
                 m = max(m, p[h].last);
             }
         }
