@@ -1,5 +1,6 @@
 """Edge cases of the CUDA path through the C ABI: empty batches, empty models, everything
-culled, tiny and ragged images, the largest frame and K, and pair-buffer overflow with retry."""
+culled, tiny and ragged images, the largest frame and K, pair-buffer overflow with retry, and
+tangent-space bindings with degenerate triangles or out-of-range indices."""
 import ctypes as C
 import math
 
@@ -133,3 +134,56 @@ def test_pair_overflow_reports_and_retries(renderer):
     assert rc == api.RGBA_OK and out2.pairs == out.pairs_needed
     ref = Renderer(0).step(DeviceBatch(batch, "cuda:0"), tg, api.RGBA_LOSS_L1)
     assert abs(out2.loss - ref.loss) <= 1e-6 * ref.loss
+
+
+def _bound_batch(seed=301, n=2000):
+    import dataclasses
+    mesh = synth.make_head_mesh(seed, 12, 24)
+    m = synth.make_bound_model(seed, n, 4, mesh)
+    fr = [synth.Frame(0, 96, 80, synth.frame_verts(mesh, seed, f)) for f in range(2)]
+    return synth.make_batch([m], fr, seed, jitter_deg=10, random_bg=True), mesh, dataclasses
+
+
+def test_degenerate_triangles_cull_like_the_oracle(renderer):
+    """Gaussians on zero-area triangles (collapsed in the mesh) or on triangles with a
+    degenerate UV map get a non-finite frame and are culled, the same way by both paths."""
+    batch, mesh, dataclasses = _bound_batch()
+    m = batch.models[0]
+    faces = m.binding.faces
+    hit = np.unique(m.binding.face_of[:200])
+    uv = m.binding.face_uv.copy()
+    uv[hit[::2], 4:6] = uv[hit[::2], 0:2]         # UV triangle collapsed onto a segment
+    frames = []
+    for fr in batch.frames:
+        v = fr.verts.copy()
+        for f in hit[1::2]:
+            v[faces[f, 2]] = v[faces[f, 0]]           # a corner on top of another: zero area
+        frames.append(synth.Frame(fr.model, fr.width, fr.height, v))
+    mb = dataclasses.replace(m, binding=dataclasses.replace(m.binding, face_uv=uv))
+    b2 = synth.Batch([mb], frames, batch.psi, batch.fparams, batch.k_stride)
+    r, db, img, T, n = run_gpu_forward(b2, (16, 16), 64, renderer)
+    ores = oracle.forward(b2, do_render=False)
+    compare_decisions(b2, ores, read_intermediates(r, db), db)
+    culled = (ores[0].rect[:200, 2] <= ores[0].rect[:200, 0])
+    assert culled.sum() > 50
+
+
+def test_binding_index_out_of_range_is_reported(renderer):
+    """A face index past n_faces culls that Gaussian (the kernels check every index before
+    reading) and rgba_step reports RGBA_ERR_INVALID_ARG."""
+    batch, mesh, dataclasses = _bound_batch(seed=303)
+    m = batch.models[0]
+    face_of = m.binding.face_of.copy()
+    face_of[5] = m.binding.faces.shape[0] + 7
+    mb = dataclasses.replace(m, binding=dataclasses.replace(m.binding, face_of=face_of))
+    b2 = synth.Batch([mb], batch.frames, batch.psi, batch.fparams, batch.k_stride)
+    db = DeviceBatch(b2, "cuda:0")
+    ws = renderer.ensure_workspace(db)
+    tg = db.pack_images(synth.make_targets(b2, 3))
+    img = torch.empty(3 * db.total_pix, device="cuda:0")
+    with pytest.raises(api.RgbaError) as e:
+        api.rgba_step(renderer.ctx, db.struct(), ws.data_ptr(), ws.numel(), tg.data_ptr(),
+                      api.RGBA_LOSS_L1, img.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == api.RGBA_ERR_INVALID_ARG and "binding index" in str(e.value)
+    rects = read_intermediates(renderer, db)["rects"]
+    assert (rects[5] == 0).all() and (rects[db.rec_offsets[1] + 5] == 0).all()
