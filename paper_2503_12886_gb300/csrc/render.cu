@@ -2,12 +2,14 @@
 // its exact reverse. The binning tile (16x16 or 8x32 pixels) fixes the lists; the compositing
 // work is split finer: every warp is an independent persistent worker that takes (tile, pixel
 // block) items from one counter, so the few heavy tiles of a face-centred frame spread over
-// many warps and no warp ever waits at a CTA barrier. A block is 8 x 4 pixels, one per lane (the
-// backward kernel also builds for 8 x 8 blocks, two pixels per lane). A warp walks its tile's list in
-// steps of BATCH entries: each lane stages BATCH / 32 of them into the warp's shared-memory
-// slots together with the box of the entry's alpha >= 1/255 ellipse, a ballot marks the entries
-// whose box meets the warp's block, and only those are visited, in list order (in reverse in
-// the backward). The forward stops once every pixel of the block is saturated.
+// many warps and no warp ever waits at a CTA barrier. A block is 8 x 4 pixels, one per lane. A
+// warp walks its tile's list in steps of BATCH entries: each lane stages BATCH / 32 of them into
+// the warp's shared-memory slots together with the box of the entry's alpha >= 1/255 ellipse, a
+// ballot marks the entries whose box meets the warp's block, and only those are visited, in
+// list order (in reverse in the backward). A visit evaluates the power at every pixel, skips
+// the entry when no lane passes the cutoff, and otherwise runs the pixel step without branches
+// (lanes that do not take part keep their state). The forward stops once every pixel of the
+// block is saturated.
 //
 // Per pixel, with d = pixel centre - mean:
 //   power = -(a dx^2 + c dy^2) / 2 - b dx dy  (skip if > 0)
@@ -79,30 +81,26 @@ struct PixF {
     bool inside, done;
 };
 
-// One list entry for one pixel (forward); marks the pixel done when it saturates. w receives
-// the entry's splatting weight alpha T at the pixel (0 when it does not blend).
-__device__ __forceinline__ void composite(PixF &p, const float4 *s_a, const float2 *s_q,
-                                          const float4 *s_c, int j, int pos, float &w) {
-    w = 0.0f;
-    const float4 A = s_a[j];
-    const float2 Q = s_q[j];
-    const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
-    const float power = power_of(dx, dy, A, Q);
-    if (skip(power, Q.y)) return;
-    const float4 Cc = s_c[j];
+// One list entry for one pixel (forward), once the caller has evaluated the entry's power at
+// the pixel: live = the pixel is still compositing and the entry passes the alpha cutoff. A live
+// entry that would take T (1 - alpha) below 1e-4 marks the pixel done without blending;
+// otherwise it blends. Branch-free, so a warp whose lanes disagree runs it once: a lane that is
+// not live keeps its state whatever its exponential gives (alpha is capped at 0.99 and its
+// weight is 0). Returns the splatting weight alpha T at the pixel (0 when the entry does not
+// blend).
+__device__ __forceinline__ float composite(PixF &p, bool live, float power, const float4 &Cc, int pos) {
     const float alpha = fminf(kAlphaMax, __fmul_rn(Cc.x, __expf(power)));
     const float testT = p.T * (1.0f - alpha);
-    if (testT < kTMin) {
-        p.done = true;
-        return;
-    }
-    const float wgt = alpha * p.T;
-    w = wgt;
-    p.C0 = fmaf(Cc.y, wgt, p.C0);
-    p.C1 = fmaf(Cc.z, wgt, p.C1);
-    p.C2 = fmaf(Cc.w, wgt, p.C2);
-    p.T = testT;
-    p.last = pos;
+    const bool sat = testT < kTMin;
+    p.done = p.done || (live && sat);
+    const bool blend = live && !sat;
+    const float w = blend ? alpha * p.T : 0.0f;
+    p.C0 = fmaf(Cc.y, w, p.C0);
+    p.C1 = fmaf(Cc.z, w, p.C1);
+    p.C2 = fmaf(Cc.w, w, p.C2);
+    p.T = blend ? testT : p.T;
+    p.last = blend ? pos : p.last;
+    return w;
 }
 
 constexpr int kWarpsPerCta = 4;  // independent warps per CTA (they share nothing but the loss sum)
@@ -308,8 +306,13 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
                 while (hm) {
                     const int j = 32 * q + __ffs(hm) - 1;
                     hm &= hm - 1;
-                    float w = 0.0f;
-                    if (!p.done) composite(p, wa, wq, wc, j, pos0 + j, w);
+                    const float4 A = wa[j];
+                    const float2 Q = wq[j];
+                    const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
+                    const float power = power_of(dx, dy, A, Q);
+                    const bool live = !p.done && !skip(power, Q.y);
+                    if (!__any_sync(0xffffffffu, live)) continue;  // the colour is not even read
+                    const float w = composite(p, live, power, wc[j], pos0 + j);
                     if (ACC && __any_sync(0xffffffffu, w > 0.0f)) {
                         const float v[4] = {w, w * I0, w * I1, w * I2};
                         const float mine = warp_reduce4(v, lane);
@@ -346,40 +349,42 @@ struct PixB {
     int last;
 };
 
-// One list entry for one pixel, in reverse; adds this pixel's share of the entry's gradient
-// dL/d(u, v, conic a, b, c, opacity, r, g, b) into v. Returns whether the pixel blended it.
-__device__ __forceinline__ bool accumulate(PixB &p, int pos, const float4 &A, const float2 &Q,
-                                           const float4 &Cc, float v[9]) {
-    if (pos > p.last) return false;
-    const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
-    const float power = power_of(dx, dy, A, Q);
-    if (skip(power, Q.y)) return false;
-    const float G = __expf(power);
+// One list entry for one pixel, in reverse, once the caller has evaluated the entry's power at
+// the pixel: live = the pixel blended the entry (its position is within the pixel's contributor
+// count and the power passes the cutoff). Writes this pixel's share of the entry's gradient
+// dL/d(u, v, conic a, b, c, opacity, r, g, b) into v (zeros when not live) and, when live,
+// steps T and P back past the entry. Branch-free, like the forward step: a lane that is not
+// live keeps its state and computes with its power clamped to 0, so that no infinite
+// exponential times a zero factor puts a NaN into the warp's sums.
+__device__ __forceinline__ void accumulate(PixB &p, bool live, float dx, float dy, float power, const float4 &A,
+                                           const float2 &Q, const float4 &Cc, float v[9]) {
+    const float G = __expf(fminf(power, 0.0f));
     const float araw = __fmul_rn(Cc.x, G);
     const float alpha = fminf(kAlphaMax, araw);
     const float oma = 1.0f - alpha;
     const float inv = __fdividef(1.0f, oma);  // 1 - alpha >= 0.01
-    p.T = p.T * inv;  // transmittance in front of this Gaussian
-    const float wgt = alpha * p.T;
-    v[6] = fmaf(wgt, p.g0, v[6]);
-    v[7] = fmaf(wgt, p.g1, v[7]);
-    v[8] = fmaf(wgt, p.g2, v[8]);
+    const float T = p.T * inv;                // transmittance in front of this Gaussian
     // dL/dalpha = T (g . c - g . S) - T_final / (1 - alpha) g . bg, then S <- alpha c + (1-alpha) S
     const float gc = fmaf(p.g2, Cc.w, fmaf(p.g1, Cc.z, p.g0 * Cc.y));
-    const float dalpha = fmaf(p.T, gc - p.P, -p.TB * inv);
-    p.P = fmaf(alpha, gc, oma * p.P);
-    if (!(araw > kAlphaMax)) {
-        v[5] = fmaf(dalpha, G, v[5]);
-        const float dpow = dalpha * araw;
-        const float hx = -0.5f * dx, hy = -0.5f * dy;
-        v[2] = fmaf(hx * dx, dpow, v[2]);
-        v[3] = fmaf(-dx * dy, dpow, v[3]);
-        v[4] = fmaf(hy * dy, dpow, v[4]);
-        // conic a = -2 A.z, b = -A.w, c = -2 Q.x
-        v[0] = fmaf(-dpow, 2.0f * A.z * dx + A.w * dy, v[0]);
-        v[1] = fmaf(-dpow, 2.0f * Q.x * dy + A.w * dx, v[1]);
-    }
-    return true;
+    const float dalpha = fmaf(T, gc - p.P, -p.TB * inv);
+    const float P = fmaf(alpha, gc, oma * p.P);
+    const float wgt = live ? alpha * T : 0.0f;
+    p.T = live ? T : p.T;
+    p.P = live ? P : p.P;
+    v[6] = wgt * p.g0;
+    v[7] = wgt * p.g1;
+    v[8] = wgt * p.g2;
+    // the clamp alpha = 0.99 passes no gradient to the opacity, conic or mean
+    const float dcl = (live && !(araw > kAlphaMax)) ? dalpha : 0.0f;
+    v[5] = dcl * G;
+    const float dpow = dcl * araw;
+    const float hx = -0.5f * dx, hy = -0.5f * dy;
+    v[2] = hx * dx * dpow;
+    v[3] = -dx * dy * dpow;
+    v[4] = hy * dy * dpow;
+    // conic a = -2 A.z, b = -A.w, c = -2 Q.x
+    v[0] = -dpow * (2.0f * A.z * dx + A.w * dy);
+    v[1] = -dpow * (2.0f * Q.x * dy + A.w * dx);
 }
 
 // Warp sum of v[0..8] as a reduce-scatter: three halving exchanges leave lane l with the partial
@@ -412,11 +417,11 @@ __device__ __forceinline__ void warp_reduce9(const float v[9], int lane, float &
     v8 = x;
 }
 
-template <int TW, int BATCH, int PXL>
+template <int TW, int BATCH>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__ T_final,
              const int *__restrict__ n_contrib) {
-    constexpr int TH = kTilePix / TW, BH = 4 * PXL, NBX = TW / 8, NB = NBX * (TH / BH), S = BATCH / 32;
+    constexpr int TH = kTilePix / TW, NBX = TW / 8, NB = NBX * (TH / 4), S = BATCH / 32;
     __shared__ float4 s_a[kWarpsPerCta][BATCH];
     __shared__ float2 s_q[kWarpsPerCta][BATCH];
     __shared__ float4 s_c[kWarpsPerCta][BATCH];
@@ -439,35 +444,28 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
         const FrameInfo &f = c.frames[b];
         const int lt = (int)(t - f.tile_base);
         const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
-        // the block: 8 x BH pixels; lane l owns column l % 8 of rows l / 8 + 4 h, h < PXL
-        const int bx = tx * TW + (int)(blk % NBX) * 8, by = ty * TH + (int)(blk / NBX) * BH;
-        const int px = bx + (lane & 7), py0 = by + (lane >> 3);
-        const float bx0 = (float)bx + 0.5f, bx1 = (float)bx + 7.5f, by0 = (float)by + 0.5f,
-                    by1 = (float)by + (float)BH - 0.5f;
+        // the block: 8 x 4 pixels; lane l owns column l % 8 of row l / 8
+        const int bx = tx * TW + (int)(blk % NBX) * 8, by = ty * TH + (int)(blk / NBX) * 4;
+        const int px = bx + (lane & 7), py = by + (lane >> 3);
+        const float bx0 = (float)bx + 0.5f, bx1 = (float)bx + 7.5f, by0 = (float)by + 0.5f, by1 = (float)by + 3.5f;
         const unsigned st = c.tile_start[t], list_len = c.tile_start[t + 1] - st;
         const float4 *rec = c.records + (size_t)f.rec_base * 3;
         float *g2 = c.grad2d + (size_t)f.rec_base * kG2Floats;
         const float *bgp = c.fparams + (size_t)b * RGBA_FP_STRIDE + 17;
         const long long hw = (long long)f.W * f.H;
-        PixB p[PXL];
-        int m = 0;
-#pragma unroll
-        for (int h = 0; h < PXL; ++h) {
-            const int py = py0 + h * 4;
-            p[h] = PixB{(float)px + 0.5f, (float)py + 0.5f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
-            if (px < f.W && py < f.H) {
-                const long long pix = (long long)py * f.W + px;
-                const float Tfin = T_final[f.pix_base + pix];
-                p[h].T = Tfin;
-                p[h].last = n_contrib[f.pix_base + pix];
-                const float *dl = dl_dimg + f.pix_base * 3 + pix;
-                p[h].g0 = dl[0];
-                p[h].g1 = dl[hw];
-                p[h].g2 = dl[2 * hw];
-                p[h].TB = Tfin * (p[h].g0 * bgp[0] + p[h].g1 * bgp[1] + p[h].g2 * bgp[2]);
-                m = max(m, p[h].last);
-            }
+        PixB p{(float)px + 0.5f, (float)py + 0.5f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+        if (px < f.W && py < f.H) {
+            const long long pix = (long long)py * f.W + px;
+            const float Tfin = T_final[f.pix_base + pix];
+            p.T = Tfin;
+            p.last = n_contrib[f.pix_base + pix];
+            const float *dl = dl_dimg + f.pix_base * 3 + pix;
+            p.g0 = dl[0];
+            p.g1 = dl[hw];
+            p.g2 = dl[2 * hw];
+            p.TB = Tfin * (p.g0 * bgp[0] + p.g1 * bgp[1] + p.g2 * bgp[2]);
         }
+        int m = p.last;
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         // n_contrib comes from the caller: entries past the list's end do not exist
         const int top = min(m, (int)list_len);
@@ -494,21 +492,19 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
                     hm &= ~(1u << bit);
                     const int j = 32 * q + bit;
                     const int pos = begin + j + 1;
-                    const float4 A = wa[j], Cc = wc[j];
+                    const float4 A = wa[j];
                     const float2 Q = wq[j];
+                    const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
+                    const float power = power_of(dx, dy, A, Q);
+                    const bool live = pos <= p.last && !skip(power, Q.y);
+                    if (!__any_sync(0xffffffffu, live)) continue;  // the colour is not even read
                     float v[9];
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) v[k] = 0.f;
-                    bool any = false;
-#pragma unroll
-                    for (int h = 0; h < PXL; ++h) any |= accumulate(p[h], pos, A, Q, Cc, v);
-                    if (__any_sync(0xffffffffu, any)) {
-                        float mine, v8;
-                        warp_reduce9(v, lane, mine, v8);
-                        float *dst = g2 + (size_t)widx[j] * kG2Floats;
-                        if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), mine);
-                        if (lane == 0) atomicAdd(dst + 8, v8);
-                    }
+                    accumulate(p, live, dx, dy, power, A, Q, wc[j], v);
+                    float mine, v8;
+                    warp_reduce9(v, lane, mine, v8);
+                    float *dst = g2 + (size_t)widx[j] * kG2Floats;
+                    if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), mine);
+                    if (lane == 0) atomicAdd(dst + 8, v8);
                 }
             }
         }
@@ -558,14 +554,12 @@ cudaError_t fwd_dispatch(const Ctx &c, int grid, int sb, float *img, float *T, i
     return fwd_inst<8, 256, ACC>(c, grid, img, T, n, tg, lk, dl, acc_tg, s);
 }
 
-constexpr int kBwdPixPerLane = 1;  // 8 x 4 blocks: twice the items of 8 x 8, fewer registers
-
 template <int TW, int BATCH>
 cudaError_t bwd_inst(const Ctx &c, int grid, const float *dl, const float *T, const int *n,
                      cudaStream_t s) {
     static int cached = 0;
-    const int g = persistent_grid(k_render_bwd<TW, BATCH, kBwdPixPerLane>, grid, 32 * kWarpsPerCta, cached);
-    return launch_pdl(k_render_bwd<TW, BATCH, kBwdPixPerLane>, dim3(g), dim3(32 * kWarpsPerCta), 0, s, c, dl, T, n);
+    const int g = persistent_grid(k_render_bwd<TW, BATCH>, grid, 32 * kWarpsPerCta, cached);
+    return launch_pdl(k_render_bwd<TW, BATCH>, dim3(g), dim3(32 * kWarpsPerCta), 0, s, c, dl, T, n);
 }
 
 }  // namespace
