@@ -51,7 +51,8 @@ typedef enum {
     RGBA_ERR_INVALID_ARG = 1,  /* bad pointer, size, layout or mask; nothing was enqueued */
     RGBA_ERR_CAPACITY = 2,     /* tile-pair buffer too small; rgba_step_out.pairs_needed set */
     RGBA_ERR_CUDA = 3,         /* a CUDA runtime call failed; see rgba_last_error() */
-    RGBA_ERR_TIMEOUT = 4,      /* a bounded device loop gave up; the results are invalid */
+    RGBA_ERR_TIMEOUT = 4,      /* a bounded device wait gave up; the results are invalid (reserved:
+                                  no kernel of this library waits on another's progress) */
     RGBA_ERR_UNSUPPORTED = 5   /* valid request outside what this build supports */
 } rgba_status;
 
@@ -60,6 +61,11 @@ typedef enum {
 #define RGBA_MAX_FRAMES 4096
 #define RGBA_MAX_MODELS 256
 #define RGBA_MAX_K 64
+/* Two common channel masks (any other valid mask works too; these two run a blend specialised at
+ * compile time when every model of a batch uses the same one): mean + log-scale + colour, and
+ * the paper's mean + rotation + colour (Supp. A.3). */
+#define RGBA_MASK_MEAN_SCALE_COLOR 0x3B87u
+#define RGBA_MASK_MEAN_ROT_COLOR 0x387Fu
 #define RGBA_MAX_DIM 4096
 
 /* Loss kinds for rgba_step (Sec. 3.2 "Loss Function" uses L1). Each frame's loss is the mean
@@ -120,7 +126,8 @@ typedef struct {
     int64_t pair_capacity;      /* pairs the workspace could hold */
     int64_t pairs_needed;       /* == pairs; set on RGBA_ERR_CAPACITY */
     uint32_t overflow;          /* 1 when pairs > pair_capacity */
-    uint32_t device_error;      /* non-zero when a bounded device loop gave up */
+    uint32_t device_error;      /* bit 0: a bounded device wait gave up (reserved); bit 1: a
+                                   tangent-space binding index was out of range */
 } rgba_step_out;
 
 /* Byte offsets of the workspace regions, for tests and debugging tools that read the

@@ -321,8 +321,12 @@ int do_preprocess(rgba_ctx_t ctx, Call &k) {
         return rc;
     StageScope sc(ctx, ST_PRE, k.s, 1);
     int max_rows = 0;
-    for (const ModelInfo &m : k.p.models) max_rows = std::max(max_rows, kNch + m.k * m.A);
-    cudaError_t e = launch_preprocess(k.c, k.p.max_n, k.p.max_k, max_rows, k.s);
+    unsigned common_mask = k.p.models.empty() ? 0u : k.p.models[0].mask;
+    for (const ModelInfo &m : k.p.models) {
+        max_rows = std::max(max_rows, kNch + m.k * m.A);
+        if (m.mask != common_mask) common_mask = 0u;
+    }
+    cudaError_t e = launch_preprocess(k.c, k.p.max_n, k.p.max_k, max_rows, common_mask, k.s);
     return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "preprocess");
 }
 

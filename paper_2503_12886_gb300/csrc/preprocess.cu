@@ -3,7 +3,7 @@
 // standalone Eq. 1 blend.
 //
 // The base Gaussians and blendshapes are read from HBM once per step: a CTA stages its chunk's
-// rows in shared memory with bulk asynchronous copies and blends every frame of the model from
+// rows in shared memory with asynchronous copies and blends every frame of the model from
 // there.
 //
 // Every value that decides a discrete outcome (cull, tile rectangle, depth key) is computed by
@@ -316,73 +316,52 @@ constexpr int kPreFB = 2;         // frames per thread per round (register block
 constexpr int kPreRound = kPreSlots * kPreFB;
 constexpr int kPreBlock = kPreG * kPreSlots;
 
+__host__ __device__ constexpr int popcount_c(unsigned x) { return x ? (int)(x & 1u) + popcount_c(x >> 1) : 0; }
+
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-// Bulk asynchronous copy global -> shared completing on an mbarrier (16-byte aligned, size a
-// multiple of 16).
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-
-// Bounded wait for phase `phase` of the mbarrier; false after max_iter polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned phase, int max_iter) {
-    for (int it = 0; it < max_iter; ++it) {
-        unsigned done;
-        asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(smem_u32(bar)), "r"(phase) : "memory");
-        if (done) return true;
-    }
-    return false;
+// Asynchronous 16-byte copy global -> shared (both addresses 16-byte aligned), completed by
+// cp.async.wait_all.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
 // One CTA = kPreG (32) Gaussians of one model and every frame that renders it. The model's G0
-// rows and blendshape rows for the chunk arrive once in shared memory by bulk async copies
-// (39 KB at K = 32 with 9 blended channels, so several CTAs share an SM); its kPreSlots (8)
+// rows and blendshape rows for the chunk arrive once in shared memory by 16-byte asynchronous
+// copies from all threads (39 KB at K = 32 with 9 blended channels, so several CTAs share an
+// SM; 128-byte bulk copies issued by one warp were 20 % slower); its kPreSlots (8)
 // thread slots per Gaussian then each blend kPreFB (2) frames at a time from shared memory
 // (each blendshape value read once per 2 frames) and run the decision spec per frame.
+// MASK != 0: every model of the batch blends exactly the channels in MASK, so the channel
+// selection of the blend loop is resolved at compile time (a runtime mask costs a test, a
+// branch and an index update per channel and blendshape); MASK = 0 reads each model's mask.
+template <unsigned MASK>
 __global__ void __launch_bounds__(kPreBlock, 3)
 k_preprocess(Ctx c, int max_k) {
     extern __shared__ float4 smem4[];
-    __shared__ __align__(8) unsigned long long s_bar;
     __shared__ FrameConst s_fc[kPreRound];
     pdl_enter();
     const ModelInfo &m = c.models[blockIdx.y];
     const int i0 = blockIdx.x * kPreG;
     if (i0 >= m.n || m.nb == 0) return;
-    const int K = m.k, A = m.A, rows = kNch + K * A;
-    const unsigned mask = m.mask;
-    float *s_rows = reinterpret_cast<float *>(smem4);      // [rows][64]: G0 then blendshapes
+    const unsigned mask = MASK ? MASK : m.mask;
+    const int K = m.k, A = MASK ? popcount_c(MASK) : m.A, rows = kNch + K * A;
+    float *s_rows = reinterpret_cast<float *>(smem4);      // [rows][kPreG]: G0 then blendshapes
     float *s_psi = s_rows + (size_t)rows * kPreG;          // [16][max_k]
     float *s_fp = s_psi + kPreRound * max_k;               // [16][20]
     const int tid = threadIdx.x;
     const int cols = min(kPreG, m.n_pad - i0);
-    const unsigned row_bytes = (unsigned)cols * 4u;
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_bar)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (tid < 32) {
-        if (tid == 0)
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         :: "r"(smem_u32(&s_bar)), "r"(row_bytes * (unsigned)rows) : "memory");
-        __syncwarp();
-        for (int rr = tid; rr < rows; rr += 32) {
-            const float *src = rr < kNch ? m.g0 + (size_t)rr * m.n_pad + i0
-                                         : m.dg + (size_t)(rr - kNch) * m.n_pad + i0;
-            bulk_g2s(s_rows + (size_t)rr * kPreG, src, row_bytes, &s_bar);
+    {  // 16-byte asynchronous copies of the chunk's rows by every thread, then one wait
+        const int per_row = cols >> 2;  // n_pad and i0 are multiples of 4
+        for (int e = tid; e < rows * per_row; e += kPreBlock) {
+            const int rr = e / per_row, q = e - rr * per_row;
+            const float *src = (rr < kNch ? m.g0 + (size_t)rr * m.n_pad : m.dg + (size_t)(rr - kNch) * m.n_pad) + i0 + 4 * q;
+            cp_async16(s_rows + (size_t)rr * kPreG + 4 * q, src);
         }
-    }
-    if (!mbar_wait(&s_bar, 0, 1 << 22)) {
-        // the copies never landed: report and give them one more bounded wait before leaving
-        if (tid == 0) atomicExch(&c.cnt->device_error, 1u);
-        mbar_wait(&s_bar, 0, 1 << 20);
-        return;
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
     }
     const int g = tid % kPreG, slot = tid / kPreG;
     const int i = i0 + g;
@@ -526,20 +505,32 @@ int preprocess_smem(int max_k, int max_rows) {
     return (max_rows * kPreG + kPreRound * max_k + kPreRound * RGBA_FP_STRIDE) * (int)sizeof(float);
 }
 
-cudaError_t launch_preprocess(const Ctx &c, int max_n, int max_k, int max_rows, cudaStream_t s) {
-    if (c.B == 0 || max_n == 0) return cudaSuccess;
+namespace {
+template <unsigned MASK>
+cudaError_t preprocess_inst(const Ctx &c, int max_n, int max_k, int max_rows, cudaStream_t s) {
     static int attr_device = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (attr_device != dev) {  // once, at the largest size (K = 64, 13 blended channels)
-        e = cudaFuncSetAttribute(k_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_preprocess<MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  preprocess_smem(RGBA_MAX_K, kNch + RGBA_MAX_K * 13));
         if (e != cudaSuccess) return e;
         attr_device = dev;
     }
     dim3 grid((max_n + kPreG - 1) / kPreG, c.M);
-    return launch_pdl(k_preprocess, grid, dim3(kPreBlock), preprocess_smem(max_k, max_rows), s, c, max_k);
+    return launch_pdl(k_preprocess<MASK>, grid, dim3(kPreBlock), preprocess_smem(max_k, max_rows), s, c, max_k);
+}
+}  // namespace
+
+cudaError_t launch_preprocess(const Ctx &c, int max_n, int max_k, int max_rows, unsigned common_mask,
+                              cudaStream_t s) {
+    if (c.B == 0 || max_n == 0) return cudaSuccess;
+    if (common_mask == RGBA_MASK_MEAN_SCALE_COLOR)
+        return preprocess_inst<RGBA_MASK_MEAN_SCALE_COLOR>(c, max_n, max_k, max_rows, s);
+    if (common_mask == RGBA_MASK_MEAN_ROT_COLOR)
+        return preprocess_inst<RGBA_MASK_MEAN_ROT_COLOR>(c, max_n, max_k, max_rows, s);
+    return preprocess_inst<0u>(c, max_n, max_k, max_rows, s);
 }
 
 cudaError_t launch_blend(const Ctx &c, int max_n, float *out, cudaStream_t s) {

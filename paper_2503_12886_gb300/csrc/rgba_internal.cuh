@@ -143,7 +143,10 @@ int set_error(int code, const char *msg);
 
 // Launch wrappers (each returns the cudaError_t of its launch).
 cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t s);
-cudaError_t launch_preprocess(const Ctx &c, int max_n, int max_k, int max_rows, cudaStream_t s);
+// common_mask: the channel mask every model of the batch shares (0 when they differ); the two
+// masks of the RGBA_MASK_* constants run a blend specialised at compile time.
+cudaError_t launch_preprocess(const Ctx &c, int max_n, int max_k, int max_rows, unsigned common_mask,
+                              cudaStream_t s);
 cudaError_t launch_blend(const Ctx &c, int max_n, float *out, cudaStream_t s);
 cudaError_t launch_scan(const Ctx &c, cudaStream_t s);
 size_t scan_aux_bytes(long long T);
