@@ -373,7 +373,9 @@ int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, cons
     }
     {
         StageScope sc(ctx, ST_GBWD, k.s, 1);
-        if ((e = launch_gauss_bwd(k.c, k.p.max_chunks, k.p.max_n, k.p.max_k, k.s)) != cudaSuccess)
+        int max_ka = 0;
+        for (const ModelInfo &m : k.p.models) max_ka = std::max(max_ka, m.k * m.A);
+        if ((e = launch_gauss_bwd(k.c, k.p.max_chunks, k.p.max_k, max_ka, k.s)) != cudaSuccess)
             return cuda_fail(e, "gauss bwd");
     }
     if (k.c.grad_psi) {

@@ -255,12 +255,21 @@ __device__ __forceinline__ bool tbn_fast(const ModelInfo &m, const float *__rest
 }
 
 // The backward of one model chunk. One CTA = 32 Gaussians (lane = Gaussian) of one model; the
-// frames that render it go 16 at a time. First the chain rule per (frame, Gaussian) turns the
-// 2-D gradients into dL/dG_b over the 14 channels, straight into shared memory; then the
-// adjoint of Eq. 1 reduces them over the frames. A warp takes two adjacent
+// frames that render it go 16 at a time. The chunk's blendshape rows are copied to shared
+// memory asynchronously at the start. Meanwhile the chain rule per (frame, Gaussian) turns the
+// 2-D gradients into dL/dG_b over the 14 channels, straight into shared memory (each item
+// reads only its cache and 2-D gradients: the cache carries the opacity and whether the
+// Gaussian was kept); then the adjoint of Eq. 1 reduces them over the frames. A warp takes two adjacent
 // blendshapes k, k+1 at a time with the 16 frames' weights psi_b[k], psi_b[k+1] in registers,
 // so each dG_b value read from shared memory feeds four FMAs; its dpsi partials (16 frames x 2
 // blendshapes per lane) are summed over the warp by a shuffle reduce-scatter.
+// Asynchronous 16-byte copy global -> shared (both addresses 16-byte aligned), completed by
+// cp.async.wait_all.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))), "l"(src) : "memory");
+}
+
 constexpr int kFG2 = 16;
 constexpr int kWarps = kBwdThreads / 32;
 
@@ -300,6 +309,7 @@ k_gauss_bwd(Ctx c, int max_k) {
     extern __shared__ float smem[];
     float *s_dG = smem;                                   // [16][14][32]
     float *s_psi = s_dG + kFG2 * kNch * kBwdChunk;        // [16][max_k]
+    float *s_dgc = s_psi + kFG2 * max_k;                  // [k][A][32]: the chunk's blendshapes
     __shared__ long long s_rec[kFG2];
     __shared__ int s_wh[kFG2][2];
     __shared__ const float *s_verts[kFG2];
@@ -314,6 +324,13 @@ k_gauss_bwd(Ctx c, int max_k) {
     const bool valid = i < m.n;      // real Gaussian
     const bool in_pad = i < m.n_pad; // row slot (padding slots receive zeros)
     const int K = m.k, A = m.A;
+    {  // the chunk's blendshape rows travel to shared memory while the chain rule runs
+        const int per_row = min(kBwdChunk, m.n_pad - i0) >> 2;  // n_pad, i0 multiples of 4
+        for (int e = threadIdx.x; e < K * A * per_row; e += kBwdThreads) {
+            const int rr = e / per_row, q = e - rr * per_row;
+            cp_async16(s_dgc + rr * kBwdChunk + 4 * q, m.dg + (size_t)rr * m.n_pad + i0 + 4 * q);
+        }
+    }
     for (int g0 = 0; g0 < m.nb; g0 += kFG2) {
         const int ng = min(kFG2, m.nb - g0);
         if (threadIdx.x < ng) {
@@ -338,7 +355,6 @@ k_gauss_bwd(Ctx c, int max_k) {
         {
             constexpr int kItems = kFG2 * kBwdChunk / kBwdThreads;
             float4 c0[kItems], c1[kItems], c2[kItems], ga[kItems], gb[kItems], gc[kItems];
-            float op[kItems];
             bool live[kItems];
 #pragma unroll
             for (int u = 0; u < kItems; ++u) {  // every load of both items in flight at once
@@ -347,18 +363,14 @@ k_gauss_bwd(Ctx c, int max_k) {
                 live[u] = fl < ng && gi < m.n;
                 const long long r = live[u] ? s_rec[fl] + gi : 0;
                 c0[u] = c1[u] = c2[u] = ga[u] = gb[u] = gc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                op[u] = 0.f;
                 if (live[u]) {
-                    const ushort4 rc = c.rects[r];
-                    live[u] = rc.z > rc.x && rc.w > rc.y;
                     c0[u] = c.cache[r * 3 + 0];
                     c1[u] = c.cache[r * 3 + 1];
-                    c2[u] = c.cache[r * 3 + 2];
+                    c2[u] = c.cache[r * 3 + 2];  // (log-scale z, -, opacity, kept)
                     const float4 *gp = reinterpret_cast<const float4 *>(c.grad2d + r * kG2Floats);
                     ga[u] = gp[0];
                     gb[u] = gp[1];
                     gc[u] = gp[2];
-                    op[u] = c.records[r * 3 + 1].y;
                 }
             }
 #pragma unroll 1
@@ -368,12 +380,12 @@ k_gauss_bwd(Ctx c, int max_k) {
                 float dG[kNch];
 #pragma unroll
                 for (int q = 0; q < kNch; ++q) dG[q] = 0.f;
-                if (live[0]) {  // item u sits in slot 0 (a rolled loop keeps the code small)
+                if (live[0] && c2[0].w != 0.f) {  // item u sits in slot 0 (a rolled loop keeps the code small)
                     const float v[10] = {c0[0].x, c0[0].y, c0[0].z, c0[0].w, c1[0].x, c1[0].y, c1[0].z, c1[0].w, c2[0].x, c2[0].y};
                     const float g2[9] = {ga[0].x, ga[0].y, ga[0].z, ga[0].w, gb[0].x, gb[0].y, gb[0].z, gb[0].w, gc[0].x};
                     float Rt[12] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f};
                     if (m.n_faces == 0 || tbn_fast(m, s_verts[fl], i0 + li, Rt))
-                        chain(v, op[0], s_fp[fl], s_wh[fl][0], s_wh[fl][1], Rt, g2, dG);
+                        chain(v, c2[0].z, s_fp[fl], s_wh[fl][0], s_wh[fl][1], Rt, g2, dG);
                 }
 #pragma unroll
                 for (int q = 0; q < kNch; ++q) s_dG[(fl * kNch + q) * kBwdChunk + li] = dG[q];
@@ -385,11 +397,11 @@ k_gauss_bwd(Ctx c, int max_k) {
                     ga[w] = ga[w + 1];
                     gb[w] = gb[w + 1];
                     gc[w] = gc[w + 1];
-                    op[w] = op[w + 1];
                     live[w] = live[w + 1];
                 }
             }
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
         // dG0[ch][i] = sum_b dG_b[ch][i]
         if (m.gg0 && in_pad) {
@@ -411,20 +423,13 @@ k_gauss_bwd(Ctx c, int max_k) {
                 s0[fl] = 0.f;
                 s1[fl] = 0.f;
             }
-            // the blendshape values of channel a + 1 are loaded while channel a is summed
-            const float *dgp0 = m.dg + (size_t)kk * A * m.n_pad + i;
-            const float *dgp1 = dgp0 + (size_t)A * m.n_pad;
-            float nx0 = valid ? __ldg(dgp0) : 0.f;
-            float nx1 = (valid && two) ? __ldg(dgp1) : 0.f;
             for (int a = 0; a < A; ++a) {
                 const int ch = m.chans[a];
                 const size_t off0 = ((size_t)kk * A + a) * m.n_pad + i;
                 const size_t off1 = off0 + (size_t)A * m.n_pad;
-                const float dg0 = nx0, dg1 = nx1;
-                if (a + 1 < A) {
-                    nx0 = valid ? __ldg(dgp0 + (size_t)(a + 1) * m.n_pad) : 0.f;
-                    nx1 = (valid && two) ? __ldg(dgp1 + (size_t)(a + 1) * m.n_pad) : 0.f;
-                }
+                // padding columns hold whatever the caller left there: zero them
+                const float dg0 = valid ? s_dgc[(kk * A + a) * kBwdChunk + lane] : 0.f;
+                const float dg1 = (valid && two) ? s_dgc[((kk + 1) * A + a) * kBwdChunk + lane] : 0.f;
                 float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
                 for (int fl = 0; fl < kFG2; ++fl) {
@@ -490,10 +495,9 @@ __global__ void __launch_bounds__(kDpsiThreads) k_dpsi_reduce(Ctx c) {
 
 }  // namespace
 
-cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_n, int max_k, cudaStream_t s) {
-    (void)max_n;
+cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_k, int max_ka, cudaStream_t s) {
     if (c.M == 0 || max_chunks == 0) return cudaSuccess;
-    auto bytes = [](int k) { return (kFG2 * kNch * kBwdChunk + kFG2 * k) * (int)sizeof(float); };
+    auto bytes = [](int k, int ka) { return (kFG2 * kNch * kBwdChunk + kFG2 * k + ka * kBwdChunk) * (int)sizeof(float); };
     // set once, at the largest size any batch can ask for, so no attribute call happens while
     // a stream is being captured
     static int attr_device = -1;
@@ -501,12 +505,13 @@ cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_n, int max_k,
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (attr_device != dev) {
-        e = cudaFuncSetAttribute(k_gauss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes(RGBA_MAX_K));
+        e = cudaFuncSetAttribute(k_gauss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes(RGBA_MAX_K, RGBA_MAX_K * 13));
         if (e != cudaSuccess) return e;
         attr_device = dev;
     }
     dim3 g2(max_chunks, c.M);
-    return launch_pdl(k_gauss_bwd, g2, dim3(kBwdThreads), (size_t)bytes(max_k), s, c, max_k);
+    return launch_pdl(k_gauss_bwd, g2, dim3(kBwdThreads), (size_t)bytes(max_k, max_ka), s, c, max_k);
 }
 
 cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s) {

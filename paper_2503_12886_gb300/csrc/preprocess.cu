@@ -144,7 +144,6 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const ModelInfo &
                                                  long long r) {
     c.cache[r * 3 + 0] = make_float4(v[0], v[1], v[2], v[3]);
     c.cache[r * 3 + 1] = make_float4(v[4], v[5], v[6], v[7]);
-    c.cache[r * 3 + 2] = make_float4(v[8], v[9], 0.f, 0.f);
     {  // the record's 2-D gradient slots start at zero for the compositing backward's atomics
         float4 *g = reinterpret_cast<float4 *>(c.grad2d + r * kG2Floats);
         g[0] = g[1] = g[2] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -307,6 +306,9 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const ModelInfo &
     c.records[r * 3 + 1] = r1;
     c.records[r * 3 + 2] = r2;
     c.rects[r] = rc;
+    // the cache's last slot also carries the activated opacity and whether the Gaussian was
+    // kept (1) or culled (0), so the backward reads one array per (frame, Gaussian)
+    c.cache[r * 3 + 2] = make_float4(v[8], v[9], op, rc.z > rc.x && rc.w > rc.y ? 1.f : 0.f);
 }
 
 constexpr int kPreThreads = 128;  // standalone blend

@@ -20,7 +20,7 @@ namespace rgba {
 
 constexpr int kNch = 14;
 constexpr int kRecFloats = 12;   // render record: u, v, a, b, c, o, r, g, b, depth, -, -
-constexpr int kCacheFloats = 12; // backward cache: mean(3), quat(4), log-scale(3), -, -
+constexpr int kCacheFloats = 12; // backward cache: mean(3), quat(4), log-scale(3), opacity, kept
 constexpr int kG2Floats = 12;    // 2-D gradient: du, dv, da, db, dc, dopacity, dr, dg, db, -
 constexpr int kTilePix = 256;    // pixels per screen tile (16x16 or 8x32)
 constexpr int kBwdChunk = 32;    // Gaussians per CTA in the fused preprocess/blend backward
@@ -159,7 +159,8 @@ cudaError_t launch_color_finish(const Ctx &c, int max_n, float delta, const uint
                                 int n_models, cudaStream_t s);
 cudaError_t launch_render_bwd(const Ctx &c, int grid, int smem_batch, const float *dl_dimg,
                               const float *T_final, const int *n_contrib, cudaStream_t s);
-cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_n, int max_k, cudaStream_t s);
+// max_ka: the largest k * A over the models (rows of blendshapes a chunk stages).
+cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_k, int max_ka, cudaStream_t s);
 cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s);
 cudaError_t launch_adam(const ModelInfo *models, int n_models, const rgba_adam_cfg &cfg,
                         const rgba_adam_state *st, int step, int *step_dev, int sms, cudaStream_t s);
