@@ -355,13 +355,80 @@ __device__ unsigned long long *radix_sort(unsigned long long *a, unsigned long l
 
 constexpr int kTieRun = 32;  // longest run of equal depths the tie pass orders by itself
 
+constexpr int kBucketBits = 11;  // buckets of the one-pass shared-memory sort
+
+// Sort of L <= kRadixCap compressed keys (depth - d0) << 32 | index in shared memory by the
+// top kBucketBits bits of the db-bit depth spread, then each bucket by the full key: one
+// shared-memory atomic per key gives its bucket and its rank in it, an exclusive scan of the
+// bucket counts the bucket starts, a scatter puts every key in its bucket (in any order
+// inside), and one thread per bucket orders the bucket's keys by insertion (buckets are short:
+// L keys over 2^kBucketBits buckets). A bucket longer than kTieRun sets *s_long and is left
+// unordered for the caller's fallback. Returns the buffer holding the result.
+__device__ unsigned long long *bucket_sort(unsigned long long *a, unsigned long long *b, int L, int db,
+                                           unsigned *s_hist /* >= 2^kBucketBits + kSortWarps */,
+                                           unsigned short *s_rank, unsigned *s_long) {
+    constexpr int NB = 1 << kBucketBits, PER = NB / kSortThreads;
+    static_assert(NB % kSortThreads == 0, "whole buckets per thread");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int shift = 32 + max(0, db - kBucketBits);
+    unsigned *wsum = s_hist + NB;
+    for (int i = tid; i < NB; i += kSortThreads) s_hist[i] = 0u;
+    __syncthreads();
+    for (int e = tid; e < L; e += kSortThreads)
+        s_rank[e] = (unsigned short)atomicAdd(&s_hist[(unsigned)(a[e] >> shift)], 1u);
+    __syncthreads();
+    {  // exclusive scan of the bucket counts; thread t owns buckets [t PER, (t+1) PER)
+        unsigned v[PER], run = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            v[q] = run;
+            run += s_hist[tid * PER + q];
+        }
+        unsigned x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        unsigned off = x - run;
+#pragma unroll
+        for (int q = 0; q < kSortWarps; ++q) off += q < warp ? wsum[q] : 0u;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) s_hist[tid * PER + q] = off + v[q];
+    }
+    __syncthreads();
+    for (int e = tid; e < L; e += kSortThreads) {
+        const unsigned long long k = a[e];
+        b[s_hist[(unsigned)(k >> shift)] + s_rank[e]] = k;
+    }
+    __syncthreads();
+    for (int bk = tid; bk < NB; bk += kSortThreads) {
+        const int lo = (int)s_hist[bk], hi = bk + 1 < NB ? (int)s_hist[bk + 1] : L;
+        if (hi - lo > kTieRun) {
+            *s_long = 1u;
+            continue;
+        }
+        for (int i = lo + 1; i < hi; ++i) {
+            const unsigned long long k = b[i];
+            int j = i;
+            for (; j > lo && b[j - 1] > k; --j) b[j] = b[j - 1];
+            b[j] = k;
+        }
+    }
+    __syncthreads();
+    return b;
+}
+
 // Persistent: CTAs take (frame, tile) segments from the LPT-ordered work list. A key is
-// (depth, Gaussian index); it is compressed to (depth - min depth) << 32 | index and
-// radix-sorted on the depth bits only (in shared memory up to kRadixCap keys, else in place in
-// global memory, mostly L2), which leaves runs of equal depth in list order. A tie pass then
-// orders each such run by index (insertion sort by the run's first thread); if any run is
-// longer than kTieRun the segment is instead sorted again on the index bits and then on the
-// depth bits, the full key. The next work item is claimed while the current one is sorted.
+// (depth, Gaussian index); it is compressed to (depth - min depth) << 32 | index. A segment of
+// up to kRadixCap keys is sorted in shared memory by bucket_sort (one bucket pass, then each
+// bucket by the full key). A longer one is radix-sorted in place in global memory (mostly L2)
+// on the depth bits only, which leaves runs of equal depth in list order, and a tie pass orders
+// each such run by index (insertion sort by the run's first thread). Either way, a bucket or
+// run longer than kTieRun sends the segment to a full-key sort: radix passes on the index bits,
+// then on the depth bits. The next work item is claimed while the current one is sorted.
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
     extern __shared__ unsigned long long s_keys[];  // [kRadixCap] x 2, counts, ranks
     unsigned *s_cnt = reinterpret_cast<unsigned *>(s_keys + 2 * kRadixCap);
@@ -386,9 +453,11 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
         const unsigned t = c.work[w];
         const unsigned st = c.tile_start[t], L = c.tile_start[t + 1] - st;
         const unsigned long long *g = c.keys + st;
+        const bool in_smem = L <= (unsigned)kRadixCap;
         unsigned dmin = 0xffffffffu, dmax = 0u, imax = 0u;
         for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
             const unsigned long long k = g[e];
+            if (in_smem) s_keys[e] = k;  // read once; compressed in place below
             const unsigned d = (unsigned)(k >> 32), i = (unsigned)k;
             dmin = min(dmin, d);
             dmax = max(dmax, d);
@@ -408,44 +477,50 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
         const unsigned d0 = s_dmin;
         const int ib = 32 - __clz(s_imax);       // bits of the largest index (0 if 0)
         const int db = 32 - __clz(s_dmax - d0);  // bits of the depth spread
-        const bool in_smem = L <= (unsigned)kRadixCap;
         unsigned long long *a = in_smem ? s_keys : c.keys2 + st;
         unsigned long long *bb = in_smem ? s_keys + kRadixCap : c.keys + st;
         for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
-            const unsigned long long k = g[e];
+            const unsigned long long k = in_smem ? a[e] : g[e];
             a[e] = ((unsigned long long)((unsigned)(k >> 32) - d0) << 32) | (unsigned)k;
         }
         __syncthreads();
-        unsigned long long *res =
-            in_smem ? radix_sort<true>(a, bb, (int)L, 32, 32 + db, s_cnt, s_rank)
-                    : radix_sort<false>(a, bb, (int)L, 32, 32 + db, s_cnt, nullptr);
-        // ties: a run keeps its depth under any reordering, so run starts found by other
-        // threads do not change while a run is being ordered
-        for (unsigned e = threadIdx.x; e + 1 < L; e += blockDim.x) {
-            const unsigned dep = (unsigned)(res[e] >> 32);
-            if ((unsigned)(res[e + 1] >> 32) != dep || (e > 0 && (unsigned)(res[e - 1] >> 32) == dep))
-                continue;
-            unsigned end = e + 2;
-            while (end < L && end - e <= (unsigned)kTieRun && (unsigned)(res[end] >> 32) == dep) ++end;
-            if (end - e > (unsigned)kTieRun) {
-                s_long = 1u;
-                continue;
+        unsigned long long *res;
+        if (in_smem) {
+            res = bucket_sort(a, bb, (int)L, db, s_cnt, s_rank, &s_long);
+            if (s_long) {  // a bucket too crowded for the fix-up: the full key by radix passes
+                unsigned long long *other = res == a ? bb : a;
+                res = radix_sort<true>(res, other, (int)L, 0, ib, s_cnt, s_rank);
+                other = res == a ? bb : a;
+                res = radix_sort<true>(res, other, (int)L, 32, 32 + db, s_cnt, s_rank);
             }
-            for (unsigned i = e + 1; i < end; ++i) {
-                const unsigned long long k = res[i];
-                unsigned j = i;
-                for (; j > e && res[j - 1] > k; --j) res[j] = res[j - 1];
-                res[j] = k;
+        } else {
+            res = radix_sort<false>(a, bb, (int)L, 32, 32 + db, s_cnt, nullptr);
+            // ties: a run keeps its depth under any reordering, so run starts found by other
+            // threads do not change while a run is being ordered
+            for (unsigned e = threadIdx.x; e + 1 < L; e += blockDim.x) {
+                const unsigned dep = (unsigned)(res[e] >> 32);
+                if ((unsigned)(res[e + 1] >> 32) != dep || (e > 0 && (unsigned)(res[e - 1] >> 32) == dep))
+                    continue;
+                unsigned end = e + 2;
+                while (end < L && end - e <= (unsigned)kTieRun && (unsigned)(res[end] >> 32) == dep) ++end;
+                if (end - e > (unsigned)kTieRun) {
+                    s_long = 1u;
+                    continue;
+                }
+                for (unsigned i = e + 1; i < end; ++i) {
+                    const unsigned long long k = res[i];
+                    unsigned j = i;
+                    for (; j > e && res[j - 1] > k; --j) res[j] = res[j - 1];
+                    res[j] = k;
+                }
             }
-        }
-        __syncthreads();
-        if (s_long) {
-            unsigned long long *other = res == a ? bb : a;
-            res = in_smem ? radix_sort<true>(res, other, (int)L, 0, ib, s_cnt, s_rank)
-                          : radix_sort<false>(res, other, (int)L, 0, ib, s_cnt, nullptr);
-            other = res == a ? bb : a;
-            res = in_smem ? radix_sort<true>(res, other, (int)L, 32, 32 + db, s_cnt, s_rank)
-                          : radix_sort<false>(res, other, (int)L, 32, 32 + db, s_cnt, nullptr);
+            __syncthreads();
+            if (s_long) {
+                unsigned long long *other = res == a ? bb : a;
+                res = radix_sort<false>(res, other, (int)L, 0, ib, s_cnt, nullptr);
+                other = res == a ? bb : a;
+                res = radix_sort<false>(res, other, (int)L, 32, 32 + db, s_cnt, nullptr);
+            }
         }
         for (unsigned e = threadIdx.x; e < L; e += blockDim.x) c.sorted[st + e] = (unsigned)res[e];
         __syncthreads();
