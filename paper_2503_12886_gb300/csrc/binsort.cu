@@ -355,15 +355,19 @@ __device__ unsigned long long *radix_sort(unsigned long long *a, unsigned long l
 
 constexpr int kTieRun = 32;  // longest run of equal depths the tie pass orders by itself
 
-constexpr int kBucketBits = 11;  // buckets of the one-pass shared-memory sort
+constexpr int kBucketBits = 12;  // buckets of the one-pass shared-memory sort
+constexpr int kBucketRun = 64;   // longest bucket the rank placement orders by itself
+static_assert((1 << kBucketBits) + kSortWarps <= kSortWarps * 256 + kSortWarps, "bucket counts fit the count area");
 
 // Sort of L <= kRadixCap compressed keys (depth - d0) << 32 | index in shared memory by the
 // top kBucketBits bits of the db-bit depth spread, then each bucket by the full key: one
-// shared-memory atomic per key gives its bucket and its rank in it, an exclusive scan of the
+// shared-memory atomic per key gives its bucket and its slot in it, an exclusive scan of the
 // bucket counts the bucket starts, a scatter puts every key in its bucket (in any order
-// inside), and one thread per bucket orders the bucket's keys by insertion (buckets are short:
-// L keys over 2^kBucketBits buckets). A bucket longer than kTieRun sets *s_long and is left
-// unordered for the caller's fallback. Returns the buffer holding the result.
+// inside), and every key then counts the smaller keys of its bucket and moves to that rank
+// (keys are distinct: the index differs). Buckets are short (L keys over 2^kBucketBits
+// buckets), so the count costs little and is the same for every key of a bucket. A bucket
+// longer than kBucketRun sets *s_long and the keys are returned grouped by bucket for the
+// caller's fallback. Returns the buffer holding the result.
 __device__ unsigned long long *bucket_sort(unsigned long long *a, unsigned long long *b, int L, int db,
                                            unsigned *s_hist /* >= 2^kBucketBits + kSortWarps */,
                                            unsigned short *s_rank, unsigned *s_long) {
@@ -404,21 +408,20 @@ __device__ unsigned long long *bucket_sort(unsigned long long *a, unsigned long 
         b[s_hist[(unsigned)(k >> shift)] + s_rank[e]] = k;
     }
     __syncthreads();
-    for (int bk = tid; bk < NB; bk += kSortThreads) {
-        const int lo = (int)s_hist[bk], hi = bk + 1 < NB ? (int)s_hist[bk + 1] : L;
-        if (hi - lo > kTieRun) {
+    for (int p = tid; p < L; p += kSortThreads) {
+        const unsigned long long k = b[p];
+        const unsigned bk = (unsigned)(k >> shift);
+        const int lo = (int)s_hist[bk], hi = bk + 1 < (unsigned)NB ? (int)s_hist[bk + 1] : L;
+        if (hi - lo > kBucketRun) {
             *s_long = 1u;
             continue;
         }
-        for (int i = lo + 1; i < hi; ++i) {
-            const unsigned long long k = b[i];
-            int j = i;
-            for (; j > lo && b[j - 1] > k; --j) b[j] = b[j - 1];
-            b[j] = k;
-        }
+        int rank = 0;
+        for (int q = lo; q < hi; ++q) rank += b[q] < k;
+        a[lo + rank] = k;
     }
     __syncthreads();
-    return b;
+    return *s_long ? b : a;  // b still holds every key for the fallback
 }
 
 // Persistent: CTAs take (frame, tile) segments from the LPT-ordered work list. A key is
@@ -426,9 +429,10 @@ __device__ unsigned long long *bucket_sort(unsigned long long *a, unsigned long 
 // up to kRadixCap keys is sorted in shared memory by bucket_sort (one bucket pass, then each
 // bucket by the full key). A longer one is radix-sorted in place in global memory (mostly L2)
 // on the depth bits only, which leaves runs of equal depth in list order, and a tie pass orders
-// each such run by index (insertion sort by the run's first thread). Either way, a bucket or
-// run longer than kTieRun sends the segment to a full-key sort: radix passes on the index bits,
-// then on the depth bits. The next work item is claimed while the current one is sorted.
+// each such run by index (insertion sort by the run's first thread). A bucket longer than
+// kBucketRun or a run longer than kTieRun sends the segment to a full-key sort: radix passes on
+// the index bits, then on the depth bits. The next work item is claimed while the current one
+// is sorted.
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
     extern __shared__ unsigned long long s_keys[];  // [kRadixCap] x 2, counts, ranks
     unsigned *s_cnt = reinterpret_cast<unsigned *>(s_keys + 2 * kRadixCap);
