@@ -314,11 +314,36 @@ int memset_async(void *p, size_t bytes, cudaStream_t s, const char *what) {
 
 int do_preprocess(rgba_ctx_t ctx, Call &k) {
     int rc;
-    if ((rc = upload_tables(ctx, k))) return rc;
-    if ((rc = memset_async(k.ws + k.p.L.counters, 256, k.s, "memset counters"))) return rc;
-    if ((rc = memset_async(k.ws + k.p.L.tile_count, 4 * (size_t)k.p.L.T * (1 + kSubCounters), k.s,
-                           "memset tile counts")))
-        return rc;
+    const size_t count_bytes = 4 * (size_t)k.p.L.T * (1 + kSubCounters);
+    {  // tables, counters and tile counts in one launch when the tables fit its parameters
+        const Layout &L = k.p.L;
+        PrologueArgs a{};
+        const void *src[3] = {k.p.models.data(), k.p.frames.data(), k.p.mframes.data()};
+        const size_t bytes[3] = {sizeof(ModelInfo) * k.p.models.size(), sizeof(FrameInfo) * k.p.frames.size(),
+                                 sizeof(int) * k.p.mframes.size()};
+        const size_t off[3] = {L.models, L.frames, L.mframes};
+        for (int t = 0; t < 3; ++t) {
+            a.dst[t] = reinterpret_cast<uint4 *>(k.ws + off[t]);
+            a.nbytes[t] = (int)std::min(bytes[t], (size_t)1 << 30);
+            a.n16[t] = (int)((bytes[t] + 15) / 16);
+        }
+        a.zero_a = reinterpret_cast<uint4 *>(k.ws + L.counters);
+        a.zero_a16 = 256 / 16;
+        a.zero_b = reinterpret_cast<uint4 *>(k.ws + L.tile_count);  // regions are 256-byte aligned
+        a.zero_b16 = (long long)((count_bytes + 15) / 16);
+        if ((bytes[0] + 15) / 16 + (bytes[1] + 15) / 16 + (bytes[2] + 15) / 16 <= (size_t)kPrologueBlob16) {
+            cudaError_t e;
+            {
+                StageScope sc(ctx, ST_UPLOAD, k.s, 1);
+                e = launch_prologue(a, src, k.s);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "step prologue");
+        } else {
+            if ((rc = upload_tables(ctx, k))) return rc;
+            if ((rc = memset_async(k.ws + L.counters, 256, k.s, "memset counters"))) return rc;
+            if ((rc = memset_async(k.ws + L.tile_count, count_bytes, k.s, "memset tile counts"))) return rc;
+        }
+    }
     StageScope sc(ctx, ST_PRE, k.s, 1);
     int max_rows = 0;
     unsigned common_mask = k.p.models.empty() ? 0u : k.p.models[0].mask;

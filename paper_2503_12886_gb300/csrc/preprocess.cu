@@ -10,6 +10,7 @@
 // a fixed sequence of correctly rounded binary32 operations written with explicit-rounding
 // intrinsics, so the compiler can neither contract nor reorder them: any other IEEE-754
 // implementation of the same sequence reproduces the tile lists bit for bit.
+#include <algorithm>
 #include <cstring>
 
 #include "rgba_internal.cuh"
@@ -52,6 +53,23 @@ __device__ float exp_spec(float x) {
 struct UploadBlob {
     uint4 data[240];  // 3840 bytes per launch
 };
+
+// The step's prologue in one launch: CTA 0 copies up to three host tables (packed in the blob
+// at 16-byte offsets) to the workspace and zeroes the counters; every CTA zeroes its share of
+// the per-tile counts, which the preprocess then counts into.
+__global__ void k_prologue(PrologueArgs a, UploadBlob blob) {
+    pdl_enter();  // the previous step's kernels may still read the tables and counts
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    if (blockIdx.x == 0) {
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+            for (int i = threadIdx.x; i < a.n16[t]; i += blockDim.x) a.dst[t][i] = blob.data[a.src16[t] + i];
+        for (int i = threadIdx.x; i < a.zero_a16; i += blockDim.x) a.zero_a[i] = z;
+    }
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.zero_b16;
+         i += (long long)gridDim.x * blockDim.x)
+        a.zero_b[i] = z;
+}
 
 __global__ void k_upload_param(uint4 *dst, UploadBlob blob, int n16) {
     pdl_enter();  // the previous step's kernels may still read the tables
@@ -482,6 +500,23 @@ k_blend(BlendChunk ch) {
 }
 
 }  // namespace
+
+cudaError_t launch_prologue(const PrologueArgs &a0, const void *const src[3], cudaStream_t s) {
+    static_assert(sizeof(UploadBlob) == 16 * kPrologueBlob16, "one blob per prologue");
+    PrologueArgs a = a0;
+    UploadBlob blob;
+    memset(&blob, 0, sizeof(blob));
+    int at = 0;
+    for (int t = 0; t < 3; ++t) {
+        if (at + a.n16[t] > kPrologueBlob16) return cudaErrorInvalidValue;
+        if (a.nbytes[t]) memcpy(&blob.data[at], src[t], (size_t)a.nbytes[t]);  // the blob is zeroed
+        a.src16[t] = at;
+        at += a.n16[t];
+    }
+    const long long per = 256LL * 8;  // uint4 stores per CTA
+    const unsigned grid = (unsigned)std::max(1LL, std::min((a.zero_b16 + per - 1) / per, 1024LL));
+    return launch_pdl(k_prologue, dim3(grid), dim3(256), 0, s, a, blob);
+}
 
 cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t s) {
     // src is host memory: it travels as kernel parameters (captured by value in graphs).

@@ -143,6 +143,21 @@ int set_error(int code, const char *msg);
 
 // Launch wrappers (each returns the cudaError_t of its launch).
 cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t s);
+// One launch for the start of a step: n16[t] 16-byte units of table t from host src[t] to dst[t]
+// (src16 is filled in), zero_a16 units zeroed at zero_a and zero_b16 at zero_b. The tables
+// travel as kernel parameters, at most kPrologueBlob16 units in all.
+constexpr int kPrologueBlob16 = 240;
+struct PrologueArgs {
+    uint4 *dst[3];
+    int nbytes[3];  // table sizes; n16 = ceil(nbytes / 16)
+    int n16[3];
+    int src16[3];
+    uint4 *zero_a;
+    int zero_a16;
+    uint4 *zero_b;
+    long long zero_b16;
+};
+cudaError_t launch_prologue(const PrologueArgs &a, const void *const src[3], cudaStream_t s);
 // common_mask: the channel mask every model of the batch shares (0 when they differ); the two
 // masks of the RGBA_MASK_* constants run a blend specialised at compile time.
 cudaError_t launch_preprocess(const Ctx &c, int max_n, int max_k, int max_rows, unsigned common_mask,
