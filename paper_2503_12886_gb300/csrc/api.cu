@@ -171,6 +171,7 @@ int make_plan(const rgba_batch *b, Plan &p) {
     L.cache = take(sizeof(float) * kCacheFloats * (size_t)R);
     L.grad2d = take(sizeof(float) * kG2Floats * (size_t)R);
     L.ranks = take(4 * kRankSlots * (size_t)R);
+    L.depth = take(4 * (size_t)R);
     L.pix_T = take(4 * (size_t)P);
     L.pix_n = take(4 * (size_t)P);
     L.pix_dl = take(12 * (size_t)P);
@@ -227,6 +228,7 @@ Ctx make_ctx(const Layout &L, unsigned char *ws, const rgba_batch *b) {
     c.sorted = reinterpret_cast<unsigned *>(ws + L.sorted);
     c.dpsi_part = reinterpret_cast<float *>(ws + L.dpsi_part);
     c.ranks = reinterpret_cast<unsigned *>(ws + L.ranks);
+    c.depth = reinterpret_cast<float *>(ws + L.depth);
     c.R = L.R;
     c.T = L.T;
     c.cap = L.cap;

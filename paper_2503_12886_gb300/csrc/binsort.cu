@@ -7,8 +7,9 @@
 // over the partials, per-CTA writes) turns them into list offsets and a work list, a scatter
 // kernel drops (depth << 32 | index) keys into their tile's segment (by
 // slot, or by a cursor atomic for larger rectangles), and one CTA per non-empty tile sorts its
-// list in shared memory, or through L2 for long segments: a stable LSD radix sort over the
-// depth bits of the key compressed to (depth - segment minimum) << 32 | index, then a pass
+// list, with the key compressed to (depth - segment minimum) << 32 | index: in shared memory by
+// one bucket pass on the top depth bits and a placement of every key by its rank in its bucket,
+// or, for long segments, through L2 by a stable LSD radix sort over the depth bits and a pass
 // that orders runs of equal depth by index. Because the key carries the index, the result is
 // unique.
 #include "rgba_internal.cuh"
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(Ctx c) {
     const long long r = f.rec_base + i;
     const ushort4 rc = c.rects[r];
     if (rc.z <= rc.x || rc.w <= rc.y) return;
-    const unsigned bits = __float_as_uint(c.records[r * 3 + 2].y);
+    const unsigned bits = __float_as_uint(c.depth[r]);
     const unsigned long long key = ((unsigned long long)bits << 32) | (unsigned)i;
     const int w = rc.z - rc.x, area = w * (rc.w - rc.y);
     if (area <= kRankSlots) {  // slots recorded by the preprocess: no atomics

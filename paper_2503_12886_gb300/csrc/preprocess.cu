@@ -324,6 +324,7 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const ModelInfo &
     c.records[r * 3 + 1] = r1;
     c.records[r * 3 + 2] = r2;
     c.rects[r] = rc;
+    c.depth[r] = r2.y;  // compact copy for the scatter (0 when culled; never read then)
     // the cache's last slot also carries the activated opacity and whether the Gaussian was
     // kept (1) or culled (0), so the backward reads one array per (frame, Gaussian)
     c.cache[r * 3 + 2] = make_float4(v[8], v[9], op, rc.z > rc.x && rc.w > rc.y ? 1.f : 0.f);

@@ -75,7 +75,7 @@ static_assert(sizeof(Counters) <= 256, "counters fit in one 256-byte block");
 
 struct Layout {
     size_t counters, models, frames, mframes, tile_count, tile_start, cursor, work;
-    size_t records, rects, cache, grad2d, ranks, pix_T, pix_n, pix_dl, pix_img, dpsi_part;
+    size_t records, rects, cache, grad2d, ranks, depth, pix_T, pix_n, pix_dl, pix_img, dpsi_part;
     size_t keys, keys2, sorted, scan_aux, total;
     long long R, T, P;     // records, tiles, pixels
     long long dpsi_floats;
@@ -107,6 +107,7 @@ struct Ctx {
     unsigned *sorted;
     float *dpsi_part;
     unsigned *ranks;   // [R][kRankSlots]: slot of the Gaussian in each tile of its rectangle
+    float *depth;      // [R]: view-space depth of each kept record (the scatter's sort key)
     long long R, T, cap;
     int B, M, k_stride, tw, th;
 };
