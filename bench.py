@@ -369,8 +369,12 @@ def run_ours(args, rank, world, local_rank):
     # HBM-bound stages, algorithmic bytes
     R = dbs[0].total_rec
     A, K = 9, K_BASES
-    pre_bytes = 4 * N_GAUSS * (14 + K * A) + R * (48 + 8 + 48)
-    gbwd_bytes = 4 * N_GAUSS * (14 + 2 * K * A) + R * (48 + 48 + 8 + 12) + FRAMES * K * 4
+    # preprocess: bases once; per record the render record, rectangle, backward cache, zeroed
+    # 2-D gradient slots, tile slots and depth key
+    pre_bytes = 4 * N_GAUSS * (14 + K * A) + R * (48 + 8 + 48 + 48 + 32 + 4)
+    # Gaussian backward: bases for the weight gradients and both gradient arrays; per record the
+    # cache and the 2-D gradients; the weight partials
+    gbwd_bytes = 4 * N_GAUSS * (14 + 2 * K * A) + R * (48 + 48) + FRAMES * K * 4
     stages = {k: {"ms": v} for k, v in stage_ms.items()}
     stages["preprocess"]["GB/s"] = pre_bytes / (stage_ms["preprocess"] / 1e3) / 1e9
     stages["preprocess"]["frac_hbm"] = stages["preprocess"]["GB/s"] / peaks["hbm_gbs"]

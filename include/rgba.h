@@ -241,6 +241,20 @@ typedef struct {
 int rgba_adam(rgba_ctx_t ctx, const rgba_batch *batch, const rgba_adam_cfg *cfg,
               const rgba_adam_state *states, int step, int32_t *step_dev, void *stream);
 
+/* One training step with the Adam update fused into the backward: rgba_step_async followed by
+ * rgba_adam (same arguments, same meaning), with results equal to those two calls bit for bit.
+ * When every model of the batch is rendered by 1 to 16 of its frames and there are at most 16
+ * models, the update is applied at the end of the projection/blend backward, from the
+ * gradients it reduced in shared memory: the gradient arrays grad_g0 / grad_dg are neither
+ * written nor needed (grad_psi is written as usual), so a training loop needs no memory for
+ * them. (On the batched training workload it takes about as long as the two calls.) Other
+ * batches run the two calls, and then need grad_g0 / grad_dg wherever the matching moments are
+ * given (RGBA_ERR_INVALID_ARG otherwise, before anything is enqueued). Capturable, like
+ * rgba_step_async; no host synchronisation. */
+int rgba_step_adam_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
+                         const float *target, int loss_kind, float *img, const rgba_adam_cfg *cfg,
+                         const rgba_adam_state *states, int step, int32_t *step_dev, void *stream);
+
 /* Per-stage device timing with CUDA events on the call's stream (off by default). Stages, in
  * launch order: 0 table upload, 1 preprocess (fused blend + projection), 2 tile-count scan,
  * 3 pair scatter, 4 per-tile depth sort, 5 compositing forward (+ fused loss), 6 compositing

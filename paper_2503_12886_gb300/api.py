@@ -26,7 +26,7 @@ EXPORTS = ("rgba_last_error", "rgba_create", "rgba_destroy", "rgba_workspace_siz
            "rgba_workspace_layout", "rgba_blend", "rgba_preprocess", "rgba_bin_sort",
            "rgba_render_fwd", "rgba_render_bwd", "rgba_step", "rgba_step_async",
            "rgba_profile_enable", "rgba_profile_read", "rgba_render_fwd_noalloc", "rgba_adam",
-           "rgba_color_init")
+           "rgba_step_adam_async", "rgba_color_init")
 RGBA_N_STAGES = 9
 STAGES = ("upload", "preprocess", "scan", "scatter", "sort", "render_fwd", "render_bwd",
           "gauss_bwd", "dpsi_reduce")
@@ -116,6 +116,9 @@ def lib() -> C.CDLL:
             L.rgba_step_async.argtypes = [P, Bp, P, sz, P, i32, P, P]
             L.rgba_adam.argtypes = [P, Bp, C.POINTER(RgbaAdamCfg), C.POINTER(RgbaAdamState), i32, P, P]
             L.rgba_adam.restype = i32
+            L.rgba_step_adam_async.argtypes = [P, Bp, P, sz, P, i32, P, C.POINTER(RgbaAdamCfg),
+                                               C.POINTER(RgbaAdamState), i32, P, P]
+            L.rgba_step_adam_async.restype = i32
             L.rgba_render_fwd_noalloc.argtypes = [P, Bp, P, P, P, C.POINTER(RgbaStepOut), P]
             L.rgba_color_init.argtypes = [P, Bp, P, sz, P, C.c_float, C.POINTER(P),
                                           C.POINTER(RgbaStepOut), P]
@@ -233,6 +236,13 @@ def rgba_render_fwd_noalloc(ctx, batch, img, T_final, n_contrib, stream) -> tupl
     if rc not in (RGBA_OK, RGBA_ERR_CAPACITY):
         check(rc)
     return rc, out
+
+
+def rgba_step_adam_async(ctx, batch, ws, ws_bytes, target, loss_kind, img, cfg: RgbaAdamCfg, states,
+                         step: int, step_dev, stream) -> int:
+    """rgba_step_async + rgba_adam with the update fused into the backward (see rgba.h)."""
+    return check(lib().rgba_step_adam_async(ctx, C.byref(batch), ws, ws_bytes, target, loss_kind, img,
+                                            C.byref(cfg), states, step, step_dev, stream))
 
 
 def rgba_adam(ctx, batch, cfg: RgbaAdamCfg, states, step: int, step_dev, stream) -> int:

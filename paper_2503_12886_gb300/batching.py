@@ -29,9 +29,11 @@ class GraphStep:
 
     def __init__(self, renderer: Renderer, db: DeviceBatch, target: torch.Tensor,
                  loss_kind: int = api.RGBA_LOSS_L1, img: torch.Tensor | None = None,
-                 headroom: float = 1.1, optimizer=None):
+                 headroom: float = 1.1, optimizer=None, fused: bool = False):
         self.r, self.db, self.target, self.loss_kind = renderer, db, target, loss_kind
         self.opt = optimizer  # optim.Adam: its update becomes part of the captured step
+        # fused: the update runs inside the backward (rgba_step_adam_async), else after it
+        self.fused = fused and optimizer is not None
         self.img = img if img is not None else torch.empty(
             3 * db.total_pix, dtype=torch.float32, device=target.device)
         self.headroom = headroom
@@ -55,11 +57,15 @@ class GraphStep:
             self.stream.synchronize()
             self.graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(self.graph, stream=self.stream):
-                api.rgba_step_async(r.ctx, b, self.ws.data_ptr(), self.ws.numel(),
-                                    self.target.data_ptr(), self.loss_kind, self.img.data_ptr(),
-                                    self.stream.cuda_stream)
-                if self.opt is not None:
-                    self.opt.step(self.stream.cuda_stream)
+                if self.fused:
+                    self.opt.train_step(self.ws, self.target, self.loss_kind, self.img,
+                                        self.stream.cuda_stream)
+                else:
+                    api.rgba_step_async(r.ctx, b, self.ws.data_ptr(), self.ws.numel(),
+                                        self.target.data_ptr(), self.loss_kind, self.img.data_ptr(),
+                                        self.stream.cuda_stream)
+                    if self.opt is not None:
+                        self.opt.step(self.stream.cuda_stream)
                 c0 = self.layout.counters
                 self.host.copy_(self.ws[c0: c0 + 24], non_blocking=True)
         torch.cuda.synchronize()

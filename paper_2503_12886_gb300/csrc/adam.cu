@@ -26,11 +26,7 @@ __device__ __forceinline__ void adam4(float4 &p, const float4 g, float4 &m, floa
     const float gs[4] = {g.x, g.y, g.z, g.w};
     float ps[4] = {p.x, p.y, p.z, p.w}, ms[4] = {m.x, m.y, m.z, m.w}, vs[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        ms[q] = fmaf(b1, ms[q], (1.f - b1) * gs[q]);
-        vs[q] = fmaf(b2, vs[q], (1.f - b2) * gs[q] * gs[q]);
-        ps[q] -= lr * (ms[q] * ibc1) / (sqrtf(vs[q] * ibc2) + eps);
-    }
+    for (int q = 0; q < 4; ++q) adam_update(ps[q], gs[q], ms[q], vs[q], lr, b1, b2, eps, ibc1, ibc2);
     p = make_float4(ps[0], ps[1], ps[2], ps[3]);
     m = make_float4(ms[0], ms[1], ms[2], ms[3]);
     v = make_float4(vs[0], vs[1], vs[2], vs[3]);
@@ -40,11 +36,8 @@ __global__ void k_adam(AdamChunk ch, float b1, float b2, float eps, float ibc1, 
                        const int *step_dev) {
     pdl_enter();
     if (step_dev) {  // t = completed steps + 1, read from the device (graph replays advance it)
-        // 1 - b^t = -expm1(t log1p(b - 1)): no cancellation when b^t is close to 1 (1 - b is
-        // exact in binary32 for b in [0.5, 1])
-        const float t = (float)(*step_dev + 1);
-        ibc1 = -1.0f / expm1f(t * log1pf(-(1.0f - b1)));
-        ibc2 = -1.0f / expm1f(t * log1pf(-(1.0f - b2)));
+        ibc1 = adam_ibc(step_dev, b1);
+        ibc2 = adam_ibc(step_dev, b2);
     }
     const AdamModel &M = ch.m[blockIdx.y];
     const long long rows0 = kNch, rowsd = (long long)M.k * M.A;
@@ -88,9 +81,45 @@ __global__ void k_step_advance(int *step_dev) {
 
 }  // namespace
 
+// 1 / (1 - b^step) on the host, for updates without a device step counter.
+static float host_ibc(float b, int step) { return (float)(1.0 / (1.0 - pow((double)b, step))); }
+
+bool make_fused_adam(const ModelInfo *models, int n_models, const rgba_adam_cfg &cfg, const rgba_adam_state *st,
+                     int step, const int *step_dev, FusedAdam &fa) {
+    if (n_models > kFusedAdamModels) return false;
+    memset(&fa, 0, sizeof(fa));
+    for (int j = 0; j < n_models; ++j) {
+        const ModelInfo &mi = models[j];
+        FusedAdamModel &M = fa.m[j];
+        if (st[j].m_g0 && st[j].v_g0) {
+            M.p0 = const_cast<float *>(mi.g0);
+            M.m0 = st[j].m_g0;
+            M.v0 = st[j].v_g0;
+        }
+        if (mi.A > 0 && st[j].m_dg && st[j].v_dg) {
+            M.pd = const_cast<float *>(mi.dg);
+            M.md = st[j].m_dg;
+            M.vd = st[j].v_dg;
+        }
+        for (int c = 0; c < kNch; ++c) M.lr0[c] = cfg.lr[c];
+        for (int a = 0; a < mi.A; ++a) M.lrd[a] = cfg.lr_delta[mi.chans[a]];
+    }
+    fa.b1 = cfg.beta1;
+    fa.b2 = cfg.beta2;
+    fa.eps = cfg.eps;
+    fa.ibc1 = host_ibc(cfg.beta1, step < 1 ? 1 : step);
+    fa.ibc2 = host_ibc(cfg.beta2, step < 1 ? 1 : step);
+    fa.step_dev = step_dev;
+    return true;
+}
+
+cudaError_t launch_step_advance(int *step_dev, cudaStream_t s) {
+    return launch_pdl(k_step_advance, dim3(1), dim3(1), 0, s, step_dev);
+}
+
 cudaError_t launch_adam(const ModelInfo *models, int n_models, const rgba_adam_cfg &cfg,
                         const rgba_adam_state *st, int step, int *step_dev, int sms, cudaStream_t s) {
-    const double bc1 = 1.0 - pow((double)cfg.beta1, step), bc2 = 1.0 - pow((double)cfg.beta2, step);
+    const float ibc1 = host_ibc(cfg.beta1, step), ibc2 = host_ibc(cfg.beta2, step);
     for (int m0 = 0; m0 < n_models; m0 += kAdamModels) {
         const int nm = n_models - m0 < kAdamModels ? n_models - m0 : kAdamModels;
         AdamChunk ch;
@@ -118,13 +147,11 @@ cudaError_t launch_adam(const ModelInfo *models, int n_models, const rgba_adam_c
             for (int a = 0; a < mi.A; ++a) M.lrd[a] = cfg.lr_delta[mi.chans[a]];
         }
         dim3 grid(sms * 4, nm);
-        cudaError_t e = launch_pdl(k_adam, grid, dim3(256), 0, s, ch, cfg.beta1, cfg.beta2, cfg.eps,
-                                   (float)(1.0 / bc1), (float)(1.0 / bc2), (const int *)step_dev);
+        cudaError_t e = launch_pdl(k_adam, grid, dim3(256), 0, s, ch, cfg.beta1, cfg.beta2, cfg.eps, ibc1, ibc2,
+                                   (const int *)step_dev);
         if (e != cudaSuccess) return e;
     }
-    if (step_dev) {
-        return launch_pdl(k_step_advance, dim3(1), dim3(1), 0, s, step_dev);
-    }
+    if (step_dev) return launch_step_advance(step_dev, s);
     return cudaSuccess;
 }
 

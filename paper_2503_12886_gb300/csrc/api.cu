@@ -381,7 +381,8 @@ int do_render_fwd(rgba_ctx_t ctx, Call &k, float *img, float *T, int *n, const f
 
 // g2_zeroed: the preprocess of the same call zeroed the 2-D gradients (the fused step); a
 // standalone backward clears them itself.
-int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, const int *n, bool g2_zeroed = false) {
+int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, const int *n, bool g2_zeroed = false,
+                  const FusedAdam *fa = nullptr) {
     int rc;
     const Layout &L = k.p.L;
     if (!g2_zeroed &&
@@ -402,12 +403,17 @@ int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, cons
         StageScope sc(ctx, ST_GBWD, k.s, 1);
         int max_ka = 0;
         for (const ModelInfo &m : k.p.models) max_ka = std::max(max_ka, m.k * m.A);
-        if ((e = launch_gauss_bwd(k.c, k.p.max_chunks, k.p.max_k, max_ka, k.s)) != cudaSuccess)
+        if ((e = launch_gauss_bwd(k.c, k.p.max_chunks, k.p.max_k, max_ka, fa, k.s)) != cudaSuccess)
             return cuda_fail(e, "gauss bwd");
     }
     if (k.c.grad_psi) {
         StageScope sc(ctx, ST_DPSI, k.s, 1);
         if ((e = launch_dpsi_reduce(k.c, k.p.max_k, k.s)) != cudaSuccess) return cuda_fail(e, "dpsi reduce");
+    }
+    if (fa && fa->step_dev) {  // after every reader of the step count
+        ctx->launches += 1;
+        if ((e = launch_step_advance(const_cast<int *>(fa->step_dev), k.s)) != cudaSuccess)
+            return cuda_fail(e, "step advance");
     }
     return RGBA_OK;
 }
@@ -615,6 +621,48 @@ int rgba_step_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
     if ((rc = do_bin_sort(ctx, k))) return rc;
     if ((rc = do_render_fwd(ctx, k, im, T, n, target, loss_kind, dl))) return rc;
     return do_render_bwd(ctx, k, dl, T, n, true);
+}
+
+int rgba_step_adam_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *target,
+                         int loss_kind, float *img, const rgba_adam_cfg *cfg, const rgba_adam_state *states,
+                         int step, int32_t *step_dev, void *stream) {
+    if (!ctx || !cfg || !states) return fail(RGBA_ERR_INVALID_ARG, "ctx/cfg/states is NULL");
+    if (!step_dev && step < 1) return fail(RGBA_ERR_INVALID_ARG, "Adam step count starts at 1");
+    if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps > 0.f))
+        return fail(RGBA_ERR_INVALID_ARG, "Adam betas must lie in [0, 1) and eps be positive");
+    Call k;
+    int rc = prologue(ctx, batch, ws, ws_bytes, stream, k);
+    if (rc || k.p.L.B == 0) return rc;
+    if (!target) return fail(RGBA_ERR_INVALID_ARG, "target is NULL");
+    if (loss_kind != RGBA_LOSS_L1 && loss_kind != RGBA_LOSS_L2) return fail(RGBA_ERR_INVALID_ARG, "bad loss kind");
+    for (size_t m = 0; m < k.p.models.size(); ++m) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(states[m].m_g0) | reinterpret_cast<uintptr_t>(states[m].v_g0) |
+                            reinterpret_cast<uintptr_t>(states[m].m_dg) | reinterpret_cast<uintptr_t>(states[m].v_dg);
+        if (a & 15) return fail(RGBA_ERR_INVALID_ARG, "Adam moment buffers must be 16-byte aligned");
+    }
+    // fused when every model is rendered by 1..16 frames (one frame group in the backward)
+    bool fuse = true;
+    for (const ModelInfo &m : k.p.models) fuse = fuse && m.nb >= 1 && m.nb <= 16;
+    FusedAdam fa;
+    fuse = fuse && make_fused_adam(k.p.models.data(), (int)k.p.models.size(), *cfg, states, step, step_dev, fa);
+    if (!fuse) {  // the two calls; the separate update reads the gradient arrays
+        for (const ModelInfo &m : k.p.models)
+            if ((states[&m - k.p.models.data()].m_g0 && !m.gg0) || (m.A > 0 && states[&m - k.p.models.data()].m_dg && !m.gdg))
+                return fail(RGBA_ERR_INVALID_ARG,
+                            "this batch cannot fuse the update (a model rendered by 0 or more than 16 frames, "
+                            "or more than 16 models): grad_g0 / grad_dg are needed");
+        if ((rc = rgba_step_async(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream))) return rc;
+        return rgba_adam(ctx, batch, cfg, states, step, step_dev, stream);
+    }
+    const Layout &L = k.p.L;
+    float *im = img ? img : reinterpret_cast<float *>(k.ws + L.pix_img);
+    float *T = reinterpret_cast<float *>(k.ws + L.pix_T);
+    int *n = reinterpret_cast<int *>(k.ws + L.pix_n);
+    float *dl = reinterpret_cast<float *>(k.ws + L.pix_dl);
+    if ((rc = do_preprocess(ctx, k))) return rc;
+    if ((rc = do_bin_sort(ctx, k))) return rc;
+    if ((rc = do_render_fwd(ctx, k, im, T, n, target, loss_kind, dl))) return rc;
+    return do_render_bwd(ctx, k, dl, T, n, true, &fa);
 }
 
 // The one host synchronisation of a synchronous entry point: reads the counters into out.

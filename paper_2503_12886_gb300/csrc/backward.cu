@@ -10,6 +10,8 @@
 //                dpsi_b[k]     partial = sum_{a, i in chunk} dG_k[a][i] dG_b[ch_a][i]
 // The reduction over frames happens in registers in a fixed order, so dG0 and ddG are
 // deterministic; dpsi partials go to a [frame][k][chunk] buffer that a second kernel sums.
+#include <type_traits>
+
 #include "rgba_internal.cuh"
 
 namespace rgba {
@@ -304,12 +306,28 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
 
 // 3 CTAs per SM (80 registers, a few spills to L1) beat 2 CTAs without spills: the kernel
 // waits on memory and needs the warps.
+// ADAM: the fused Adam update of rgba_step_adam_async; every model is rendered by at most kFG2
+// frames, so the reductions below are complete after one group. Their results are parked in
+// shared memory (G0's in s_g0, the blendshapes' in the slots of the staged rows, whose values
+// are read again from memory) and the CTA then streams the update over the chunk's rows; the
+// gradient arrays are not written.
+// The plain instance's stand-in for FusedAdam: the same members, one model, never read.
+struct NoAdam {
+    FusedAdamModel m[1];
+    float b1, b2, eps, ibc1, ibc2;
+    const int *step_dev;
+};
+template <bool ADAM>
+using AdamArg = typename std::conditional<ADAM, FusedAdam, NoAdam>::type;
+
+template <bool ADAM>
 __global__ void __launch_bounds__(kBwdThreads, 3)
-k_gauss_bwd(Ctx c, int max_k) {
+k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
     extern __shared__ float smem[];
     float *s_dG = smem;                                   // [16][14][32]
     float *s_psi = s_dG + kFG2 * kNch * kBwdChunk;        // [16][max_k]
     float *s_dgc = s_psi + kFG2 * max_k;                  // [k][A][32]: the chunk's blendshapes
+    __shared__ __align__(16) float s_g0[ADAM ? kNch * kBwdChunk : 1];  // ADAM: the G0 gradients
     __shared__ long long s_rec[kFG2];
     __shared__ int s_wh[kFG2][2];
     __shared__ const float *s_verts[kFG2];
@@ -324,6 +342,12 @@ k_gauss_bwd(Ctx c, int max_k) {
     const bool valid = i < m.n;      // real Gaussian
     const bool in_pad = i < m.n_pad; // row slot (padding slots receive zeros)
     const int K = m.k, A = m.A;
+    float ibc1 = 0.f, ibc2 = 0.f;
+    if (ADAM) {
+        ibc1 = fa.step_dev ? adam_ibc(fa.step_dev, fa.b1) : fa.ibc1;
+        ibc2 = fa.step_dev ? adam_ibc(fa.step_dev, fa.b2) : fa.ibc2;
+    }
+    const FusedAdamModel &am = fa.m[ADAM ? blockIdx.y : 0];
     {  // the chunk's blendshape rows travel to shared memory while the chain rule runs
         const int per_row = min(kBwdChunk, m.n_pad - i0) >> 2;  // n_pad, i0 multiples of 4
         for (int e = threadIdx.x; e < K * A * per_row; e += kBwdThreads) {
@@ -404,12 +428,16 @@ k_gauss_bwd(Ctx c, int max_k) {
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
         // dG0[ch][i] = sum_b dG_b[ch][i]
-        if (m.gg0 && in_pad) {
+        if ((ADAM ? am.p0 != nullptr : m.gg0 != nullptr) && in_pad) {
             for (int ch = warp; ch < kNch; ch += kWarps) {
                 float a = 0.f;
                 for (int fl = 0; fl < ng; ++fl) a += s_dG[(fl * kNch + ch) * kBwdChunk + lane];
-                float *o = m.gg0 + (size_t)ch * m.n_pad + i;
-                *o = (g0 == 0 ? 0.f : *o) + a;
+                const size_t o = (size_t)ch * m.n_pad + i;
+                if (ADAM) {  // parked for the update below, exactly as the separate update reads it
+                    s_g0[ch * kBwdChunk + lane] = 0.f + a;
+                } else {
+                    m.gg0[o] = (g0 == 0 ? 0.f : m.gg0[o]) + a;
+                }
             }
         }
         // ddG[k][a][i] = sum_b psi_b[k] dG_b[ch_a][i];  dpsi_b[k] partial = sum_a,i dG_k[a][i] dG_b[ch_a][i]
@@ -439,7 +467,11 @@ k_gauss_bwd(Ctx c, int max_k) {
                     s0[fl] = fmaf(dg0, d, s0[fl]);
                     s1[fl] = fmaf(dg1, d, s1[fl]);
                 }
-                if (m.gdg && in_pad) {
+                if (ADAM) {
+                    // this lane was the staged value's only reader: the slot now parks the gradient
+                    s_dgc[(kk * A + a) * kBwdChunk + lane] = 0.f + acc0;
+                    if (two) s_dgc[((kk + 1) * A + a) * kBwdChunk + lane] = 0.f + acc1;
+                } else if (m.gdg && in_pad) {
                     float *o = m.gdg + off0;
                     *o = (g0 == 0 ? 0.f : *o) + acc0;
                     if (two) {
@@ -460,6 +492,49 @@ k_gauss_bwd(Ctx c, int max_k) {
             }
         }
         __syncthreads();
+    }
+    if (ADAM) {
+        // the update, streamed over the chunk's rows (G0 rows, then blendshape rows) by the whole
+        // CTA, float4 by float4, with the loads of several float4s in flight per thread
+        const int cols4 = min(kBwdChunk, m.n_pad - i0) >> 2;
+        const int rows0 = am.p0 ? kNch : 0, rowsd = am.pd ? K * A : 0;
+        const int total = (rows0 + rowsd) * cols4;
+        constexpr int kU = 4;
+        for (int e0 = threadIdx.x; e0 < total; e0 += kU * kBwdThreads) {
+            float4 pp[kU], mm[kU], vv[kU];
+            int rows[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {  // every load first
+                const int e = e0 + u * kBwdThreads;
+                rows[u] = e < total ? e / cols4 : -1;
+                if (rows[u] >= 0) {
+                    const int row = rows[u], c4 = e - row * cols4;
+                    const bool base = row < rows0;
+                    const size_t off = (size_t)(base ? row : row - rows0) * m.n_pad + i0 + 4 * c4;
+                    pp[u] = *reinterpret_cast<const float4 *>((base ? am.p0 : am.pd) + off);
+                    mm[u] = *reinterpret_cast<const float4 *>((base ? am.m0 : am.md) + off);
+                    vv[u] = *reinterpret_cast<const float4 *>((base ? am.v0 : am.vd) + off);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                if (rows[u] < 0) continue;
+                const int e = e0 + u * kBwdThreads, row = rows[u], c4 = e - row * cols4;
+                const bool base = row < rows0;
+                const int rr = base ? row : row - rows0;
+                const size_t off = (size_t)rr * m.n_pad + i0 + 4 * c4;
+                const float4 g = *reinterpret_cast<const float4 *>((base ? s_g0 : s_dgc) + rr * kBwdChunk + 4 * c4);
+                const float lr = base ? am.lr0[rr] : am.lrd[rr % A];
+                float p4[4] = {pp[u].x, pp[u].y, pp[u].z, pp[u].w}, m4[4] = {mm[u].x, mm[u].y, mm[u].z, mm[u].w},
+                      v4[4] = {vv[u].x, vv[u].y, vv[u].z, vv[u].w};
+                const float g4[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) adam_update(p4[q], g4[q], m4[q], v4[q], lr, fa.b1, fa.b2, fa.eps, ibc1, ibc2);
+                *reinterpret_cast<float4 *>((base ? am.p0 : am.pd) + off) = make_float4(p4[0], p4[1], p4[2], p4[3]);
+                *reinterpret_cast<float4 *>((base ? am.m0 : am.md) + off) = make_float4(m4[0], m4[1], m4[2], m4[3]);
+                *reinterpret_cast<float4 *>((base ? am.v0 : am.vd) + off) = make_float4(v4[0], v4[1], v4[2], v4[3]);
+            }
+        }
     }
 }
 
@@ -495,8 +570,10 @@ __global__ void __launch_bounds__(kDpsiThreads) k_dpsi_reduce(Ctx c) {
 
 }  // namespace
 
-cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_k, int max_ka, cudaStream_t s) {
-    if (c.M == 0 || max_chunks == 0) return cudaSuccess;
+namespace {
+template <bool ADAM>
+cudaError_t gauss_bwd_inst(const Ctx &c, int max_chunks, int max_k, int max_ka, const AdamArg<ADAM> &fa,
+                           cudaStream_t s) {
     auto bytes = [](int k, int ka) { return (kFG2 * kNch * kBwdChunk + kFG2 * k + ka * kBwdChunk) * (int)sizeof(float); };
     // set once, at the largest size any batch can ask for, so no attribute call happens while
     // a stream is being captured
@@ -505,13 +582,22 @@ cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_k, int max_ka
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (attr_device != dev) {
-        e = cudaFuncSetAttribute(k_gauss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_gauss_bwd<ADAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  bytes(RGBA_MAX_K, RGBA_MAX_K * 13));
         if (e != cudaSuccess) return e;
         attr_device = dev;
     }
     dim3 g2(max_chunks, c.M);
-    return launch_pdl(k_gauss_bwd, g2, dim3(kBwdThreads), (size_t)bytes(max_k, max_ka), s, c, max_k);
+    return launch_pdl(k_gauss_bwd<ADAM>, g2, dim3(kBwdThreads), (size_t)bytes(max_k, max_ka), s, c, max_k, fa);
+}
+}  // namespace
+
+cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_k, int max_ka, const FusedAdam *fa,
+                             cudaStream_t s) {
+    if (c.M == 0 || max_chunks == 0) return cudaSuccess;
+    if (fa) return gauss_bwd_inst<true>(c, max_chunks, max_k, max_ka, *fa, s);
+    const NoAdam none{};
+    return gauss_bwd_inst<false>(c, max_chunks, max_k, max_ka, none, s);
 }
 
 cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s) {

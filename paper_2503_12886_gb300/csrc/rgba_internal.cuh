@@ -175,10 +175,51 @@ cudaError_t launch_color_finish(const Ctx &c, int max_n, float delta, const uint
                                 int n_models, cudaStream_t s);
 cudaError_t launch_render_bwd(const Ctx &c, int grid, int smem_batch, const float *dl_dimg,
                               const float *T_final, const int *n_contrib, cudaStream_t s);
-// max_ka: the largest k * A over the models (rows of blendshapes a chunk stages).
-cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_k, int max_ka, cudaStream_t s);
+// One Adam update (Kingma & Ba, ICLR 2015) of parameter p with gradient g:
+//   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,  p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
+// with ibc = 1 / (1 - b^t). The separate and the fused update both call this, so they agree
+// bit for bit.
+__device__ __forceinline__ void adam_update(float &p, float g, float &m, float &v, float lr, float b1, float b2,
+                                            float eps, float ibc1, float ibc2) {
+    m = fmaf(b1, m, (1.f - b1) * g);
+    v = fmaf(b2, v, (1.f - b2) * g * g);
+    p -= lr * (m * ibc1) / (sqrtf(v * ibc2) + eps);
+}
+
+// 1 / (1 - b^t) for t = *step_dev + 1 (completed steps + 1, read on the device so that graph
+// replays advance it): 1 - b^t = -expm1(t log1p(b - 1)), no cancellation when b^t is close to 1
+// (1 - b is exact in binary32 for b in [0.5, 1]).
+__device__ __forceinline__ float adam_ibc(const int *step_dev, float b) {
+    const float t = (float)(*step_dev + 1);
+    return -1.0f / expm1f(t * log1pf(-(1.0f - b)));
+}
+
+// The Adam update fused into the projection/blend backward (rgba_step_adam_async): per model
+// the parameters, moments and learning rates (NULL parameters: not updated).
+constexpr int kFusedAdamModels = 16;
+struct FusedAdamModel {
+    float *p0, *m0, *v0;  // [14][n_pad]
+    float *pd, *md, *vd;  // [k][A][n_pad]
+    float lr0[kNch];
+    float lrd[kNch];      // per blended slot a (first A used)
+};
+struct FusedAdam {
+    FusedAdamModel m[kFusedAdamModels];
+    float b1, b2, eps, ibc1, ibc2;  // ibc from the host when step_dev is NULL
+    const int *step_dev;
+};
+// Fills fa for the batch's models; false when the update cannot be fused (too many models).
+bool make_fused_adam(const ModelInfo *models, int n_models, const rgba_adam_cfg &cfg, const rgba_adam_state *st,
+                     int step, const int *step_dev, FusedAdam &fa);
+
+// max_ka: the largest k * A over the models (rows of blendshapes a chunk stages). fa (may be
+// NULL): apply Adam to G0 and the blendshapes where their gradients are reduced, instead of
+// writing the gradients (every model must be rendered by 1..16 frames).
+cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_k, int max_ka, const FusedAdam *fa,
+                             cudaStream_t s);
 cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s);
 cudaError_t launch_adam(const ModelInfo *models, int n_models, const rgba_adam_cfg &cfg,
                         const rgba_adam_state *st, int step, int *step_dev, int sms, cudaStream_t s);
+cudaError_t launch_step_advance(int *step_dev, cudaStream_t s);
 
 }  // namespace rgba

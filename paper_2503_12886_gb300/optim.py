@@ -45,3 +45,16 @@ class Adam:
         """One update from the gradients the last backward wrote (device-side step count)."""
         api.rgba_adam(self.ctx, self.db.struct(), self.cfg, self.states, 0,
                       self.step_dev.data_ptr(), stream if stream is not None else stream_ptr())
+
+    def train_step(self, ws: torch.Tensor, target: torch.Tensor, loss_kind: int = api.RGBA_LOSS_L1,
+                   img: torch.Tensor | None = None, stream: int | None = None,
+                   db: DeviceBatch | None = None):
+        """A whole training step with this update fused into the backward
+        (rgba_step_adam_async): no host synchronisation; the loss and pair count are in the
+        workspace counters. db: another batch over the same models (other frames, weights,
+        cameras), else the optimizer's own."""
+        b = (db or self.db).struct()
+        api.rgba_step_adam_async(self.ctx, b, ws.data_ptr(), ws.numel(), target.data_ptr(),
+                                 loss_kind, img.data_ptr() if img is not None else None, self.cfg,
+                                 self.states, 0, self.step_dev.data_ptr(),
+                                 stream if stream is not None else stream_ptr())
