@@ -255,6 +255,34 @@ int rgba_step_adam_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size
                          const float *target, int loss_kind, float *img, const rgba_adam_cfg *cfg,
                          const rgba_adam_state *states, int step, int32_t *step_dev, void *stream);
 
+/* A training step captured once as a CUDA graph and replayed with one host synchronisation per
+ * step (Sec. 3.2: one synchronisation per batch). rgba_step_capture runs the step once eagerly
+ * on `stream` (a non-default stream; no update applied), then captures rgba_step_async, the
+ * Adam update when cfg is non-NULL (rgba_adam with states and the device step counter
+ * step_dev, both required then) and the read of the counters. The graph keeps every pointer:
+ * batch arrays, workspace, target, img, moments and step_dev must stay valid and in place
+ * while it is used; their contents may change between replays (new weights, cameras, targets).
+ * Stage profiling must be off. rgba_step_replay launches it on the capture stream, waits and
+ * fills out like rgba_step; RGBA_ERR_CAPACITY (out->pairs_needed set) means the workspace is
+ * too small for this step: grow it and capture again. rgba_graph_destroy frees the graph. */
+typedef struct rgba_graph *rgba_graph_t;
+int rgba_step_capture(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
+                      const float *target, int loss_kind, float *img, const rgba_adam_cfg *cfg,
+                      const rgba_adam_state *states, int32_t *step_dev, void *stream,
+                      rgba_graph_t *out);
+int rgba_step_replay(rgba_graph_t graph, rgba_step_out *out);
+void rgba_graph_destroy(rgba_graph_t graph);
+
+/* The (frame, tile) lists of the last binning on this workspace (rgba_bin_sort, rgba_step or a
+ * forward), for tests and debugging; synchronous. *n_pairs (host) receives the pair count.
+ * tile_start (device uint32[T + 1], or NULL): list starts, T = total tiles of the batch, frame
+ * after frame, tiles row-major. sorted (device uint32[sorted_cap], or NULL): every list's
+ * Gaussian indices in (depth bits, index) order. RGBA_ERR_CAPACITY if that binning overflowed,
+ * RGBA_ERR_INVALID_ARG if sorted_cap is below the pair count. */
+int rgba_debug_keys(rgba_ctx_t ctx, const rgba_batch *batch, const void *ws, size_t ws_bytes,
+                    uint32_t *tile_start, uint32_t *sorted, size_t sorted_cap, int64_t *n_pairs,
+                    void *stream);
+
 /* Per-stage device timing with CUDA events on the call's stream (off by default). Stages, in
  * launch order: 0 table upload, 1 preprocess (fused blend + projection), 2 tile-count scan,
  * 3 pair scatter, 4 per-tile depth sort, 5 compositing forward (+ fused loss), 6 compositing

@@ -26,7 +26,8 @@ EXPORTS = ("rgba_last_error", "rgba_create", "rgba_destroy", "rgba_workspace_siz
            "rgba_workspace_layout", "rgba_blend", "rgba_preprocess", "rgba_bin_sort",
            "rgba_render_fwd", "rgba_render_bwd", "rgba_step", "rgba_step_async",
            "rgba_profile_enable", "rgba_profile_read", "rgba_render_fwd_noalloc", "rgba_adam",
-           "rgba_step_adam_async", "rgba_color_init")
+           "rgba_step_adam_async", "rgba_step_capture", "rgba_step_replay", "rgba_graph_destroy",
+           "rgba_debug_keys", "rgba_color_init")
 RGBA_N_STAGES = 9
 STAGES = ("upload", "preprocess", "scan", "scatter", "sort", "render_fwd", "render_bwd",
           "gauss_bwd", "dpsi_reduce")
@@ -119,6 +120,15 @@ def lib() -> C.CDLL:
             L.rgba_step_adam_async.argtypes = [P, Bp, P, sz, P, i32, P, C.POINTER(RgbaAdamCfg),
                                                C.POINTER(RgbaAdamState), i32, P, P]
             L.rgba_step_adam_async.restype = i32
+            L.rgba_step_capture.argtypes = [P, Bp, P, sz, P, i32, P, C.POINTER(RgbaAdamCfg),
+                                            C.POINTER(RgbaAdamState), P, P, C.POINTER(P)]
+            L.rgba_step_capture.restype = i32
+            L.rgba_step_replay.argtypes = [P, C.POINTER(RgbaStepOut)]
+            L.rgba_step_replay.restype = i32
+            L.rgba_graph_destroy.argtypes = [P]
+            L.rgba_graph_destroy.restype = None
+            L.rgba_debug_keys.argtypes = [P, Bp, P, sz, P, P, sz, C.POINTER(i64), P]
+            L.rgba_debug_keys.restype = i32
             L.rgba_render_fwd_noalloc.argtypes = [P, Bp, P, P, P, C.POINTER(RgbaStepOut), P]
             L.rgba_color_init.argtypes = [P, Bp, P, sz, P, C.c_float, C.POINTER(P),
                                           C.POINTER(RgbaStepOut), P]
@@ -243,6 +253,40 @@ def rgba_step_adam_async(ctx, batch, ws, ws_bytes, target, loss_kind, img, cfg: 
     """rgba_step_async + rgba_adam with the update fused into the backward (see rgba.h)."""
     return check(lib().rgba_step_adam_async(ctx, C.byref(batch), ws, ws_bytes, target, loss_kind, img,
                                             C.byref(cfg), states, step, step_dev, stream))
+
+
+def rgba_step_capture(ctx, batch, ws, ws_bytes, target, loss_kind, img, cfg, states, step_dev,
+                      stream):
+    """Captures a training step (and the Adam update when cfg is not None) as a CUDA graph;
+    returns the graph handle. See rgba.h."""
+    g = C.c_void_p()
+    check(lib().rgba_step_capture(ctx, C.byref(batch), ws, ws_bytes, target, loss_kind, img,
+                                  C.byref(cfg) if cfg is not None else None, states, step_dev,
+                                  stream, C.byref(g)))
+    return g
+
+
+def rgba_step_replay(graph) -> tuple[int, RgbaStepOut]:
+    """One replay and its host synchronisation: (status, out); RGBA_ERR_CAPACITY is returned,
+    not raised."""
+    out = RgbaStepOut()
+    rc = lib().rgba_step_replay(graph, C.byref(out))
+    if rc not in (RGBA_OK, RGBA_ERR_CAPACITY):
+        check(rc)
+    return rc, out
+
+
+def rgba_graph_destroy(graph) -> None:
+    lib().rgba_graph_destroy(graph)
+
+
+def rgba_debug_keys(ctx, batch, ws, ws_bytes, tile_start, sorted_, sorted_cap, stream) -> int:
+    """Copies the last binning's tile starts and sorted lists (device pointers, or None);
+    returns the pair count."""
+    n = C.c_int64()
+    check(lib().rgba_debug_keys(ctx, C.byref(batch), ws, ws_bytes, tile_start, sorted_, sorted_cap,
+                                C.byref(n), stream))
+    return int(n.value)
 
 
 def rgba_adam(ctx, batch, cfg: RgbaAdamCfg, states, step: int, step_dev, stream) -> int:

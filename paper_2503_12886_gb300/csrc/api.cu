@@ -700,6 +700,117 @@ int rgba_step(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes
     return read_out(ctx, batch, ws, ws_bytes, out, stream);
 }
 
+int rgba_step_capture(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *target,
+                      int loss_kind, float *img, const rgba_adam_cfg *cfg, const rgba_adam_state *states,
+                      int32_t *step_dev, void *stream, rgba_graph_t *out) {
+    if (!out) return fail(RGBA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctx) return fail(RGBA_ERR_INVALID_ARG, "ctx is NULL");
+    if (ctx->prof) return fail(RGBA_ERR_INVALID_ARG, "stage profiling is on: it cannot be captured");
+    if (cfg && (!states || !step_dev))
+        return fail(RGBA_ERR_INVALID_ARG, "a captured Adam update needs states and the device step counter");
+    if (!stream) return fail(RGBA_ERR_INVALID_ARG, "capture needs a non-default stream");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // one eager step first: validates the arguments and sets every kernel attribute outside
+    // the capture (the update is not applied)
+    int rc = rgba_step_async(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream);
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    Plan p;
+    make_plan(batch, p);
+    rgba_graph *g = new rgba_graph();
+    g->ctx = ctx;
+    g->stream = s;
+    g->ws = static_cast<unsigned char *>(ws);
+    g->ws_bytes = ws_bytes;
+    g->counters_off = p.L.counters;
+    g->cap = cap_for_bytes(p.L, ws_bytes);
+    if ((e = cudaMallocHost(reinterpret_cast<void **>(&g->host), sizeof(rgba_counters))) != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "cudaMallocHost");
+    }
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        cudaFreeHost(g->host);
+        delete g;
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    rc = rgba_step_async(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream);
+    if (!rc && cfg) rc = rgba_adam(ctx, batch, cfg, states, 0, step_dev, stream);
+    if (!rc && (e = cudaMemcpyAsync(g->host, g->ws + g->counters_off, sizeof(rgba_counters), cudaMemcpyDeviceToHost,
+                                    s)) != cudaSuccess)
+        rc = cuda_fail(e, "read counters");
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(s, &graph);
+    if (!rc && e_end != cudaSuccess) rc = cuda_fail(e_end, "cudaStreamEndCapture");
+    if (!rc && (e = cudaGraphInstantiate(&g->exec, graph, 0)) != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate");
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        cudaFreeHost(g->host);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return RGBA_OK;
+}
+
+int rgba_step_replay(rgba_graph_t g, rgba_step_out *out) {
+    if (!g || !out) return fail(RGBA_ERR_INVALID_ARG, "graph/out is NULL");
+    memset(out, 0, sizeof(*out));
+    cudaError_t e = cudaSetDevice(g->ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if ((e = cudaGraphLaunch(g->exec, g->stream)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    const rgba_counters &h = *g->host;
+    out->loss = h.loss;
+    out->pairs = h.pairs;
+    out->pair_capacity = g->cap;
+    out->overflow = h.overflow;
+    out->device_error = h.device_error;
+    if (h.overflow) {
+        out->pairs_needed = h.pairs;
+        return fail(RGBA_ERR_CAPACITY, "pair buffer too small: need " + std::to_string(h.pairs) + " pairs");
+    }
+    if (h.device_error & 2u) return fail(RGBA_ERR_INVALID_ARG, "tangent-space binding index out of range");
+    return RGBA_OK;
+}
+
+void rgba_graph_destroy(rgba_graph_t g) {
+    if (!g) return;
+    cudaSetDevice(g->ctx->device);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->host) cudaFreeHost(g->host);
+    delete g;
+}
+
+int rgba_debug_keys(rgba_ctx_t ctx, const rgba_batch *batch, const void *ws, size_t ws_bytes, uint32_t *tile_start,
+                    uint32_t *sorted, size_t sorted_cap, int64_t *n_pairs, void *stream) {
+    if (!n_pairs) return fail(RGBA_ERR_INVALID_ARG, "n_pairs is NULL");
+    Call k;
+    int rc = prologue(ctx, batch, const_cast<void *>(ws), ws_bytes, stream, k);
+    if (rc) return rc;
+    const Layout &L = k.p.L;
+    rgba_counters h;
+    cudaError_t e = cudaMemcpyAsync(&h, k.ws + L.counters, sizeof(h), cudaMemcpyDeviceToHost, k.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(k.s);
+    if (e != cudaSuccess) return cuda_fail(e, "read counters");
+    *n_pairs = h.pairs;
+    if (h.overflow) return fail(RGBA_ERR_CAPACITY, "the last binning overflowed: its lists are incomplete");
+    if (tile_start &&
+        (e = cudaMemcpyAsync(tile_start, k.ws + L.tile_start, 4 * (size_t)(L.T + 1), cudaMemcpyDeviceToDevice, k.s)) !=
+            cudaSuccess)
+        return cuda_fail(e, "copy tile starts");
+    if (sorted) {
+        if (sorted_cap < (size_t)h.pairs) return fail(RGBA_ERR_INVALID_ARG, "sorted_cap is smaller than the pair count");
+        if (h.pairs &&
+            (e = cudaMemcpyAsync(sorted, k.ws + L.sorted, 4 * (size_t)h.pairs, cudaMemcpyDeviceToDevice, k.s)) != cudaSuccess)
+            return cuda_fail(e, "copy sorted lists");
+    }
+    if ((e = cudaStreamSynchronize(k.s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return RGBA_OK;
+}
+
 int rgba_color_init(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *target,
                     float delta, uint8_t *const *done, rgba_step_out *out, void *stream) {
     if (!out) return fail(RGBA_ERR_INVALID_ARG, "out is NULL");

@@ -16,6 +16,18 @@ struct rgba_ctx {
     int launches;
 };
 
+// A captured training step (rgba_step_capture): the instantiated graph, the stream it replays
+// on, and its own pinned landing spot for the counters.
+struct rgba_graph {
+    rgba_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0, counters_off = 0;
+    long long cap = 0;
+    rgba_counters *host = nullptr;
+};
+
 namespace rgba {
 
 constexpr int kNch = 14;

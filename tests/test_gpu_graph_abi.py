@@ -1,0 +1,110 @@
+"""The C ABI's captured training step (rgba_step_capture / rgba_step_replay) and its debug getter
+for the binned lists (rgba_debug_keys).
+
+Bars: a replayed step (with the captured Adam update) follows the eager rgba_step + rgba_adam
+sequence: losses to 1e-5 relative, parameters after three steps to 1e-5 absolute (the
+compositing backward's atomics sum in another order in the two runs); a graph whose workspace
+is too small returns RGBA_ERR_CAPACITY with the pair count it needs; the debug getter returns
+exactly the tile starts and sorted lists of the oracle's binning (bit-exact)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2503_12886_gb300 import api, synth
+from paper_2503_12886_gb300.optim import Adam
+from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer, stream_ptr
+
+from gpu_helpers import frame_tile_bases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def renderer():
+    import __graft_entry__
+    __graft_entry__.build()
+    r = Renderer(0)
+    yield r
+    r.close()
+
+
+def small_batch():
+    models = [synth.make_model(120, 4000, 6), synth.make_model(121, 3000, 4, mask=synth.MASK_PAPER)]
+    fr = [synth.Frame(0, 96, 80), synth.Frame(1, 80, 96), synth.Frame(0, 64, 64)]
+    return synth.make_batch(models, fr, seed=120, jitter_deg=15, random_bg=True)
+
+
+def test_replayed_step_follows_eager_steps(renderer):
+    batch = small_batch()
+    targets = synth.make_targets(batch, 6)
+    dbA, dbB = DeviceBatch(batch, "cuda:0"), DeviceBatch(batch, "cuda:0")
+    optA, optB = Adam(renderer, dbA), Adam(renderer, dbB)
+    tgA, tgB = dbA.pack_images(targets), dbB.pack_images(targets)
+    bB = dbB.struct()
+    ws = torch.empty(api.rgba_workspace_size(bB, 8 * dbB.total_rec + 4096), dtype=torch.uint8, device="cuda:0")
+    img = torch.empty(3 * dbB.total_pix, device="cuda:0")
+    s = torch.cuda.Stream()
+    g0_init = [m.g0.clone() for m in dbB.models]
+    g = api.rgba_step_capture(renderer.ctx, bB, ws.data_ptr(), ws.numel(), tgB.data_ptr(), api.RGBA_LOSS_L1,
+                              img.data_ptr(), optB.cfg, optB.states, optB.step_dev.data_ptr(), s.cuda_stream)
+    try:
+        for _ in range(3):
+            outA = renderer.step(dbA, tgA, api.RGBA_LOSS_L1)
+            optA.step()
+            rc, outB = api.rgba_step_replay(g)
+            assert rc == api.RGBA_OK and outB.overflow == 0
+            assert abs(outA.loss - outB.loss) <= 1e-5 * abs(outA.loss)
+            assert outA.pairs == outB.pairs
+    finally:
+        api.rgba_graph_destroy(g)
+    torch.cuda.synchronize()
+    assert int(optB.step_dev.item()) == 3
+    for mA, mB, init in zip(dbA.models, dbB.models, g0_init):
+        torch.testing.assert_close(mB.g0, mA.g0, rtol=0, atol=1e-5)
+        torch.testing.assert_close(mB.dg, mA.dg, rtol=0, atol=1e-5)
+        assert not torch.equal(mB.g0, init)  # the captured update ran
+
+
+def test_replay_reports_capacity(renderer):
+    batch = small_batch()
+    db = DeviceBatch(batch, "cuda:0")
+    tg = db.pack_images(synth.make_targets(batch, 7))
+    b = db.struct()
+    ws = torch.empty(api.rgba_workspace_size(b, 1000), dtype=torch.uint8, device="cuda:0")
+    s = torch.cuda.Stream()
+    g = api.rgba_step_capture(renderer.ctx, b, ws.data_ptr(), ws.numel(), tg.data_ptr(), api.RGBA_LOSS_L2,
+                              None, None, None, None, s.cuda_stream)
+    try:
+        rc, out = api.rgba_step_replay(g)
+    finally:
+        api.rgba_graph_destroy(g)
+    assert rc == api.RGBA_ERR_CAPACITY
+    assert out.overflow == 1 and out.pairs_needed > out.pair_capacity >= 1000
+
+
+def test_debug_keys_equal_oracle_lists(renderer):
+    batch = small_batch()
+    db = DeviceBatch(batch, "cuda:0", grads=False)
+    renderer.forward(db)
+    ws = renderer.ws
+    lay = renderer.layout(db)
+    T = lay.tiles_total
+    ts = torch.empty(T + 1, dtype=torch.int32, device="cuda:0")
+    n = api.rgba_debug_keys(renderer.ctx, db.struct(), ws.data_ptr(), ws.numel(), ts.data_ptr(), None, 0,
+                            stream_ptr())
+    srt = torch.empty(max(1, n), dtype=torch.int32, device="cuda:0")
+    assert api.rgba_debug_keys(renderer.ctx, db.struct(), ws.data_ptr(), ws.numel(), None, srt.data_ptr(), n,
+                               stream_ptr()) == n
+    with pytest.raises(api.RgbaError):
+        api.rgba_debug_keys(renderer.ctx, db.struct(), ws.data_ptr(), ws.numel(), None, srt.data_ptr(), n - 1,
+                            stream_ptr())
+    ts, srt = ts.cpu().numpy().astype(np.int64), srt.cpu().numpy().astype(np.int64)
+    assert ts[-1] == n
+    ores = oracle.forward(batch, splat="spec")
+    bases = frame_tile_bases(batch)
+    for b, (fr, o) in enumerate(zip(batch.frames, ores)):
+        nt = len(o.tile_start) - 1
+        t = ts[bases[b]: bases[b] + nt + 1]
+        np.testing.assert_array_equal(t - t[0], o.tile_start.astype(np.int64))
+        np.testing.assert_array_equal(srt[t[0]: t[-1]], o.lst.astype(np.int64))
