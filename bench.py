@@ -710,11 +710,13 @@ def run_online(local_rank, seconds=10.0, fps=25.0, batch=16):
     """Online reconstruction (Sec. 3.3, Alg. 2): frames of a 25 FPS stream (renders of the
     reference avatar at new weights, poses and backgrounds, arriving in real time) enter the
     local/global pools; every training step (graph-replayed, Adam) takes a batch of 16 with
-    eta = 0.7 from the pools. The stream starts with 16 frames already received."""
+    eta = 0.7 from the pools. The stream starts with 16 frames already received. Two input
+    buffers alternate: while step i trains, the host samples step i + 1's frames and a copy
+    stream gathers them, so the GPU does not wait for the host between steps; the loss and pair
+    count of each step are read (one host synchronisation) while the next one runs."""
     import numpy as np
     import torch
-    from paper_2503_12886_gb300 import synth
-    from paper_2503_12886_gb300.batching import GraphStep
+    from paper_2503_12886_gb300 import api, synth
     from paper_2503_12886_gb300.online import LocalGlobalSampler
     from paper_2503_12886_gb300.optim import Adam
     from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
@@ -724,6 +726,9 @@ def run_online(local_rank, seconds=10.0, fps=25.0, batch=16):
     model = stream.models[0]
     ref = synth.reference_avatar(model, 7001)
     r = Renderer(local_rank)
+    rs = torch.cuda.Stream(device=dev)  # arriving frames are rendered here
+    cs = torch.cuda.Stream(device=dev)  # batch gathers
+    s = torch.cuda.Stream(device=dev)   # training steps
     # the store: every frame's target (rendered when it arrives), weights and camera
     px = 3 * RES * RES
     store_tg = torch.empty(n_frames, px, device=dev)
@@ -732,13 +737,18 @@ def run_online(local_rank, seconds=10.0, fps=25.0, batch=16):
     one = [synth.Batch([ref], [stream.frames[f]], stream.psi[f:f + 1], stream.fparams[f:f + 1],
                        stream.k_stride) for f in range(n_frames)]
     ref_dm = None
+    received_ev = [None]
 
     def receive(f):
         nonlocal ref_dm
-        d = DeviceBatch(one[f], dev, grads=False, models=ref_dm)
-        ref_dm = d.models
-        img, _, _ = r.forward(d)
-        store_tg[f].copy_(img)
+        with torch.cuda.stream(rs):
+            d = DeviceBatch(one[f], dev, grads=False, models=ref_dm)
+            ref_dm = d.models
+            img, _, _ = r.forward(d)
+            store_tg[f].copy_(img)
+            ev = torch.cuda.Event()
+            ev.record(rs)
+        received_ev[0] = ev
         sampler.push(f)
 
     sampler = LocalGlobalSampler(150, 1000, 0.7, seed=7002)
@@ -746,18 +756,57 @@ def run_online(local_rank, seconds=10.0, fps=25.0, batch=16):
         receive(f)
     step_batch = synth.Batch([model], stream.frames[:batch], stream.psi[:batch], stream.fparams[:batch],
                              stream.k_stride)
-    db = DeviceBatch(step_batch, dev)
-    tg = torch.empty(batch * px, device=dev)
+    dbs = [DeviceBatch(step_batch, dev)]
+    dbs.append(DeviceBatch(step_batch, dev, models=dbs[0].models))
+    tgs = [torch.empty(batch * px, device=dev) for _ in dbs]
+    idx_h = [torch.zeros(batch, dtype=torch.int64).pin_memory() for _ in dbs]
+    idx_d = [torch.zeros(batch, dtype=torch.int64, device=dev) for _ in dbs]
+    host_cnt = [torch.zeros(24, dtype=torch.uint8).pin_memory() for _ in dbs]
+    done_ev = [torch.cuda.Event() for _ in dbs]
+    opt = Adam(r, dbs[0])  # both buffers train the same model
+    structs = [d.struct() for d in dbs]
+    img = torch.empty(batch * px, device=dev)
 
-    def load(idx):
-        it = torch.as_tensor(idx, device=dev)
-        tg.view(batch, px).copy_(store_tg.index_select(0, it))
-        db.psi.copy_(store_psi.index_select(0, it))
-        db.fparams.copy_(store_fp.index_select(0, it))
+    def load(j, idx):
+        idx_h[j].numpy()[:] = idx
+        with torch.cuda.stream(cs):
+            if received_ev[0] is not None:
+                cs.wait_event(received_ev[0])
+            idx_d[j].copy_(idx_h[j], non_blocking=True)
+            tgs[j].view(batch, px).copy_(store_tg.index_select(0, idx_d[j]))
+            dbs[j].psi.copy_(store_psi.index_select(0, idx_d[j]))
+            dbs[j].fparams.copy_(store_fp.index_select(0, idx_d[j]))
+            ev = torch.cuda.Event()
+            ev.record(cs)
+        return ev
 
-    load(sampler.sample(batch))
-    gs = GraphStep(r, db, tg, optimizer=Adam(r, db), headroom=1.6)
-    received, steps, ages = batch, 0, []
+    cap = {"graphs": [], "ws": None}
+
+    def capture(n_pairs):
+        torch.cuda.synchronize()
+        ws = torch.empty(api.rgba_workspace_size(structs[0], n_pairs), dtype=torch.uint8, device=dev)
+        lay = api.rgba_workspace_layout(structs[0], ws.numel())
+        cap["ws"], cap["graphs"] = ws, []
+        with torch.cuda.stream(s):
+            api.rgba_step_async(r.ctx, structs[0], ws.data_ptr(), ws.numel(), tgs[0].data_ptr(),
+                                api.RGBA_LOSS_L1, img.data_ptr(), s.cuda_stream)
+            s.synchronize()
+            for j in range(len(dbs)):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s):
+                    api.rgba_step_async(r.ctx, structs[j], ws.data_ptr(), ws.numel(), tgs[j].data_ptr(),
+                                        api.RGBA_LOSS_L1, img.data_ptr(), s.cuda_stream)
+                    opt.step(s.cuda_stream)
+                    host_cnt[j].copy_(ws[lay.counters: lay.counters + 24], non_blocking=True)
+                cap["graphs"].append(g)
+        torch.cuda.synchronize()
+
+    load(0, sampler.sample(batch)).synchronize()
+    pairs = r.step(dbs[0], tgs[0], api.RGBA_LOSS_L1, img).pairs
+    capture(int(pairs * 1.6) + 4096)
+    received, steps, ages, regrow = batch, 0, [], 0
+    loss = float("nan")
+    pending = None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     while True:
@@ -767,11 +816,26 @@ def run_online(local_rank, seconds=10.0, fps=25.0, batch=16):
         while received < n_frames and received - batch < now * fps:
             receive(received)
             received += 1
+        j = steps % len(dbs)
         idx = sampler.sample(batch)
         ages.extend(received - 1 - np.asarray(idx))
-        load(idx)
-        loss, pairs = gs.replay()
+        # buffer j was last read by step i - 2, which finished before step i - 1 was waited for
+        s.wait_event(load(j, idx))
+        with torch.cuda.stream(s):
+            cap["graphs"][j].replay()
+            done_ev[j].record(s)
+        if pending is not None:  # the previous step's one host synchronisation
+            done_ev[pending].synchronize()
+            u = host_cnt[pending][:8].numpy().view(np.uint32)
+            loss = float(host_cnt[pending][16:24].numpy().view(np.float64)[0])
+            if u[1]:  # overflow: grow the workspace and capture again
+                regrow += 1
+                capture(int(u[0] * 1.3) + 4096)
+        pending = j
         steps += 1
+    if pending is not None:
+        done_ev[pending].synchronize()
+        loss = float(host_cnt[pending][16:24].numpy().view(np.float64)[0])
     t = time.perf_counter() - t0
     r.close()
     ages = np.asarray(ages)
@@ -781,7 +845,7 @@ def run_online(local_rank, seconds=10.0, fps=25.0, batch=16):
             "seconds": t, "frames_received": received, "steps": steps, "steps_per_s": steps / t,
             "img_per_s": steps * batch / t, "steps_per_frame": steps / max(1, received - batch),
             "sample_age_frames": {"median": float(np.median(ages)), "p90": float(np.percentile(ages, 90))},
-            "last_loss": loss}
+            "workspace_regrowths": regrow, "last_loss": loss}
 
 
 def run_serve(local_rank, seconds):
