@@ -59,7 +59,7 @@ class GraphStep:
             with torch.cuda.graph(self.graph, stream=self.stream):
                 if self.fused:
                     self.opt.train_step(self.ws, self.target, self.loss_kind, self.img,
-                                        self.stream.cuda_stream)
+                                        self.stream.cuda_stream, db=self.db)
                 else:
                     api.rgba_step_async(r.ctx, b, self.ws.data_ptr(), self.ws.numel(),
                                         self.target.data_ptr(), self.loss_kind, self.img.data_ptr(),

@@ -115,3 +115,20 @@ def test_fused_step_needs_no_gradient_arrays(renderer):
     with pytest.raises(api.RgbaError) as e:
         opt17.train_step(_workspace(db17), db17.pack_images(synth.make_targets(b17, 5)))
     assert e.value.code == api.RGBA_ERR_INVALID_ARG
+
+
+def test_graph_step_with_fused_update_trains(renderer):
+    """GraphStep(fused=True) captures rgba_step_adam_async: replays advance the step count and
+    fit the targets (images of a reference avatar)."""
+    from paper_2503_12886_gb300.batching import GraphStep
+    batch = two_models()
+    refs = [synth.reference_avatar(m, 130 + j) for j, m in enumerate(batch.models)]
+    rb = synth.Batch(refs, batch.frames, batch.psi, batch.fparams, batch.k_stride)
+    tg, _, _ = renderer.forward(DeviceBatch(rb, "cuda:0", grads=False))
+    tg = tg.clone()
+    db = DeviceBatch(batch, "cuda:0", grads=False)
+    opt = Adam(renderer, db)
+    gs = GraphStep(renderer, db, tg, optimizer=opt, headroom=1.6, fused=True)
+    losses = [gs.replay()[0] for _ in range(30)]
+    assert int(opt.step_dev.item()) == 30
+    assert losses[-1] < 0.7 * losses[0], losses
