@@ -444,7 +444,8 @@ def run_ours(args, rank, world, local_rank):
                         "path": "captured step graphs (rgba_step_async + rgba_adam through the C "
                                 "ABI, one per input variant), every step's inputs copied from "
                                 "pinned host on a copy stream while the previous step computes, "
-                                "counters read back, one sync per step"},
+                                "each step's counters read back (one sync per step) while the "
+                                "next step runs"},
                 "per_frame": per_frame,
                 "speedup_vs_per_frame": (value / per_frame["value"]) if per_frame else None,
                 "gpu_launches": launches_per_step * args.steps,
@@ -461,12 +462,14 @@ def e2e_run(dbs, tgs, host_in, s, cs, steps, cap, host_cnt, capture):
     """`steps` training steps end to end through the captured step graphs (rgba_step_async +
     rgba_adam + the counter read, one graph per input variant): every step's inputs (targets,
     weights, cameras) are copied from pinned host memory on the copy stream cs while the
-    previous step computes on s (the variants rotate, so a variant's buffers are refilled only
-    after the step that read them has been synchronised); each step waits for its copies,
-    replays its graph and synchronises once to read its loss and pair count."""
+    previous step computes on s; each step waits for its copies and replays its graph, and the
+    host reads step i's loss and pair count (its one host synchronisation) while step i + 1
+    runs. A variant's buffers are refilled only after the step that last read them is known to
+    be complete. A step that overflowed the pair buffer is replayed after the workspace grows."""
     import numpy as np
     import torch
     nv = len(dbs)
+    done = [torch.cuda.Event() for _ in range(nv)]
 
     def issue(i):
         j = i % nv
@@ -479,20 +482,38 @@ def e2e_run(dbs, tgs, host_in, s, cs, steps, cap, host_cnt, capture):
             ev.record(cs)
         return ev
 
+    def overflowed(j):
+        return bool(host_cnt[j][:8].numpy().view(np.uint32)[1])
+
+    def redo(j):  # grow, capture again, replay variant j's step until it fits
+        while overflowed(j):
+            cap["regrow"] += 1
+            capture(int(host_cnt[j][:8].numpy().view(np.uint32)[0] * 1.3) + 4096)
+            cap["graphs"][j].replay()
+            s.synchronize()
+
     ready = issue(0)
+    pending = None
     for i in range(steps):
-        nxt = issue(i + 1) if i + 1 < steps else None
         j = i % nv
         s.wait_event(ready)
-        while True:
-            cap["graphs"][j].replay()
-            s.synchronize()  # the step's one host synchronisation: its loss and pair count
-            u = host_cnt[j][:8].numpy().view(np.uint32)
-            if not u[1]:
-                break
-            cap["regrow"] += 1
-            capture(int(u[0] * 1.3) + 4096)
-        ready = nxt
+        cap["graphs"][j].replay()
+        done[j].record(s)
+        if pending is not None:  # the previous step's one host synchronisation
+            done[pending].synchronize()
+            if overflowed(pending):
+                s.synchronize()
+                redo(pending)
+                redo(j)  # ran with the old workspace: check it too
+        if i + 1 < steps:
+            if nv < 2:  # step i + 1 - nv is step i itself, still running
+                s.synchronize()
+            ready = issue(i + 1)
+        pending = j
+    if pending is not None:
+        done[pending].synchronize()
+        if overflowed(pending):
+            redo(pending)
 
 
 def per_frame_path(api, work0, dev, r):
