@@ -1,7 +1,6 @@
 """Edge cases of the CUDA path through the C ABI: empty batches, empty models, everything
 culled, tiny and ragged images, the largest frame and K, pair-buffer overflow with retry, and
 tangent-space bindings with degenerate triangles or out-of-range indices."""
-import ctypes as C
 import math
 
 import numpy as np

@@ -1,6 +1,5 @@
 """The three forms built on the per-frame path: differentiation (autograd.Function), batching
 (uneven batches, CUDA-graph replay, autotuner) and serving (continuous batching)."""
-import math
 
 import numpy as np
 import pytest
@@ -11,7 +10,7 @@ from paper_2503_12886_gb300 import api, synth
 from paper_2503_12886_gb300.autograd import rasterize
 from paper_2503_12886_gb300.batching import GraphStep, autotune
 from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
-from paper_2503_12886_gb300.serving import Request, Server, requests_from_trace
+from paper_2503_12886_gb300.serving import Server, requests_from_trace
 
 from gpu_helpers import grad_error
 

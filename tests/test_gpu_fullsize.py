@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2503_12886_gb300 import api, synth
+from paper_2503_12886_gb300 import synth
 from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
 
 from gpu_helpers import (GRAD_FLOOR, GRAD_RTOL, compare_decisions, compare_images,

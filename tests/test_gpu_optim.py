@@ -4,9 +4,9 @@ import pytest
 import torch
 
 import oracle
-from paper_2503_12886_gb300 import api, synth
+from paper_2503_12886_gb300 import synth
 from paper_2503_12886_gb300.batching import GraphStep
-from paper_2503_12886_gb300.optim import PAPER_DELTA_SCALE, PAPER_LR, Adam, paper_cfg
+from paper_2503_12886_gb300.optim import PAPER_DELTA_SCALE, PAPER_LR, Adam
 from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
 
 pytestmark = pytest.mark.gpu

@@ -8,7 +8,6 @@ is the identity, invariance of the projected splats under a rigid motion of the 
 with the opposite motion of the camera, and central finite differences through the transform.
 """
 import dataclasses
-import math
 
 import numpy as np
 import pytest

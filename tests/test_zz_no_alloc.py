@@ -4,7 +4,6 @@ Callers that cannot use cudaMalloc (inside another framework's memory pool, plug
 forbids device allocation) get the forward render with the library's fixed 64 MiB scratch
 block. This file runs last so that a run stopping at the first failure has run everything else.
 """
-import numpy as np
 import pytest
 import torch
 
