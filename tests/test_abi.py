@@ -106,3 +106,33 @@ def test_null_arguments(api):
 def test_empty_batch_is_a_noop_size(api):
     b, _, _ = _batch(api, n_frames=0)
     assert api.rgba_workspace_size(b, 0) > 0
+
+
+def test_null_arguments_of_the_step_variants(api):
+    """The fused step, the captured step and the debug getter reject missing arguments on the
+    host, before touching a device (no GPU is needed to run this)."""
+    L = api.lib()
+    b, _, _ = _batch(api)
+    cfg = api.RgbaAdamCfg()
+    cfg.beta1, cfg.beta2, cfg.eps = 0.9, 0.999, 1e-8
+    st = (api.RgbaAdamState * 1)()
+    E = api.RGBA_ERR_INVALID_ARG
+    # no context / no configuration / no states
+    assert L.rgba_step_adam_async(None, C.byref(b), None, 0, None, 1, None, C.byref(cfg), st, 1, None, None) == E
+    assert L.rgba_step_adam_async(C.c_void_p(1), C.byref(b), None, 0, None, 1, None, None, st, 1, None, None) == E
+    # step count must start at 1 without a device counter; betas in [0, 1), eps > 0
+    assert L.rgba_step_adam_async(C.c_void_p(1), C.byref(b), None, 0, None, 1, None, C.byref(cfg), st, 0,
+                                  None, None) == E
+    bad = api.RgbaAdamCfg()
+    bad.beta1, bad.beta2, bad.eps = 1.0, 0.999, 1e-8
+    assert L.rgba_step_adam_async(C.c_void_p(1), C.byref(b), None, 0, None, 1, None, C.byref(bad), st, 1,
+                                  None, None) == E
+    # capture: no output slot / no context
+    assert L.rgba_step_capture(None, C.byref(b), None, 0, None, 1, None, None, None, None, None, None) == E
+    g = C.c_void_p(123)
+    assert L.rgba_step_capture(None, C.byref(b), None, 0, None, 1, None, None, None, None, None, C.byref(g)) == E
+    assert g.value is None  # cleared on failure
+    assert L.rgba_step_replay(None, C.byref(api.RgbaStepOut())) == E
+    L.rgba_graph_destroy(None)  # a no-op
+    # debug getter: no pair-count slot
+    assert L.rgba_debug_keys(None, C.byref(b), None, 0, None, None, 0, None, None) == E
