@@ -70,6 +70,18 @@ def dense_batch():
     return synth.make_batch([m], [synth.Frame(0, 64, 64)], seed=93)
 
 
+def cluster_batch():
+    """A tight cluster of 300 Gaussians at nearly one depth (steps of about two ulps) among 1,700
+    spread ones: the cluster's tile lists put ~150 distinct keys into each of one or two of the
+    sort's 4096 depth buckets, more than its rank placement takes, so those segments take the
+    full-key fallback; buckets of a few keys take the rank placement."""
+    m = synth.make_model(95, 2000, 4, sd_dmean=0.0, log_scale_mu=math.log(5e-3))
+    g0 = m.g0.copy()
+    g0[0:2, :300] = 0.0
+    g0[2, :300] = 0.05 + 2.4e-7 * np.arange(300)
+    return synth.make_batch([dataclasses.replace(m, g0=g0)], [synth.Frame(0, 96, 96)], seed=95)
+
+
 def tangent_batch(mask=synth.MASK_MEAN_SCALE_COLOR, seed=81):
     """Gaussians bound to a head mesh (tangent space, Supp. "Gaussian Transformation"), three
     frames with different mesh expressions, jittered cameras, random background."""
@@ -87,6 +99,7 @@ CASES = {
     "ragged_8x32": (ragged_batch, (8, 32), 64),
     "uneven": (uneven_batch, (16, 16), 128),
     "depth_ties": (ties_batch, (16, 16), 128),
+    "depth_cluster": (cluster_batch, (16, 16), 64),
     "dense_lists": (dense_batch, (16, 16), 64),
     "tangent": (tangent_batch, (16, 16), 64),
     "tangent_paper_mask": (lambda: tangent_batch(synth.MASK_PAPER, 82), (8, 32), 128),
