@@ -82,6 +82,26 @@ def cluster_batch():
     return synth.make_batch([dataclasses.replace(m, g0=g0)], [synth.Frame(0, 96, 96)], seed=95)
 
 
+MASK_ALL = sum(1 << c for c in range(14) if c != 10)   # every channel but opacity
+MASK_MEAN_COLOR = 0x7 | (0x7 << 11)
+
+
+def all_channels_batch():
+    """The largest blend: K = 64 blendshapes on all 13 blendable channels (a mask without a
+    compiled instance: the preprocess reads it at run time), 14 + 832 staged rows per chunk."""
+    m = synth.make_model(97, 1500, 64, mask=MASK_ALL)
+    return synth.make_batch([m], [synth.Frame(0, 96, 96), synth.Frame(0, 80, 112)], seed=97,
+                            jitter_deg=10, random_bg=True)
+
+
+def mixed_masks_batch():
+    """Two avatars with different channel masks in one batch (mean + colour, and the paper's):
+    no common mask, so the preprocess takes its run-time-mask instance."""
+    ms = [synth.make_model(98, 3000, 12, mask=MASK_MEAN_COLOR), synth.make_model(99, 2500, 8, mask=synth.MASK_PAPER)]
+    fr = [synth.Frame(0, 96, 80), synth.Frame(1, 80, 96), synth.Frame(1, 64, 64)]
+    return synth.make_batch(ms, fr, seed=98, jitter_deg=15, random_bg=True)
+
+
 def tangent_batch(mask=synth.MASK_MEAN_SCALE_COLOR, seed=81):
     """Gaussians bound to a head mesh (tangent space, Supp. "Gaussian Transformation"), three
     frames with different mesh expressions, jittered cameras, random background."""
@@ -100,6 +120,8 @@ CASES = {
     "uneven": (uneven_batch, (16, 16), 128),
     "depth_ties": (ties_batch, (16, 16), 128),
     "depth_cluster": (cluster_batch, (16, 16), 64),
+    "all_channels_k64": (all_channels_batch, (16, 16), 64),
+    "mixed_masks": (mixed_masks_batch, (8, 32), 128),
     "dense_lists": (dense_batch, (16, 16), 64),
     "tangent": (tangent_batch, (16, 16), 64),
     "tangent_paper_mask": (lambda: tangent_batch(synth.MASK_PAPER, 82), (8, 32), 128),
