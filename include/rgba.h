@@ -13,10 +13,12 @@
  * Conventions shared by every entry point
  *  - Memory: every array argument is caller-owned DEVICE memory unless marked "host". The
  *    library allocates nothing on the device; scratch lives in a caller-allocated workspace
- *    sized by rgba_workspace_size. No pointer is retained after a call returns.
+ *    sized by rgba_workspace_size. No pointer is retained after a call returns, except by a
+ *    captured step (rgba_step_capture), whose graph keeps them until rgba_graph_destroy.
  *  - Streams: every call is asynchronous on the given stream (0 = legacy default stream) and
  *    enqueues kernels and memsets only, so it can be captured in a CUDA graph, except
- *    rgba_step, which ends with one device-to-host read and a stream synchronisation.
+ *    rgba_step, rgba_color_init, rgba_step_replay and rgba_debug_keys, which end with one
+ *    device-to-host read and a stream synchronisation, and rgba_step_capture, which captures.
  *  - Errors: every call returns an rgba_status. Host-side validation failures return before
  *    anything is enqueued. rgba_last_error() gives a thread-local message for the last failure.
  *    No call aborts or exits the process.
