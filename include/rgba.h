@@ -17,8 +17,9 @@
  *    captured step (rgba_step_capture), whose graph keeps them until rgba_graph_destroy.
  *  - Streams: every call is asynchronous on the given stream (0 = legacy default stream) and
  *    enqueues kernels and memsets only, so it can be captured in a CUDA graph, except
- *    rgba_step, rgba_color_init, rgba_step_replay and rgba_debug_keys, which end with one
- *    device-to-host read and a stream synchronisation, and rgba_step_capture, which captures.
+ *    rgba_step, rgba_color_init, rgba_render_fwd_noalloc, rgba_step_replay and rgba_debug_keys,
+ *    which end with one device-to-host read and a stream synchronisation, and
+ *    rgba_step_capture, which captures.
  *  - Errors: every call returns an rgba_status. Host-side validation failures return before
  *    anything is enqueued. rgba_last_error() gives a thread-local message for the last failure.
  *    No call aborts or exits the process.
