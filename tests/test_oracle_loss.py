@@ -2,9 +2,10 @@
 workload) and of its normalisation (a mean over each frame's 3 H W values, then a mean over the
 frames of the batch).
 
-What pins it: with the near plane beyond the avatar every Gaussian is culled, so each frame's image is its background, so
-against a constant target the loss has a closed form per frame, and frames of different sizes
-weigh the same; dL/dimg is sign(d) / (3 H W B) for L1 and d / (3 H W B) for L2."""
+What pins it: with the near plane beyond the avatar every Gaussian is culled and each frame's
+image is its background, so against a constant target the loss has a closed form per frame,
+and frames of different sizes weigh the same; dL/dimg is sign(d) / (3 H W B) for L1 and
+d / (3 H W B) for L2."""
 import numpy as np
 import pytest
 
