@@ -63,6 +63,30 @@ def test_autograd_matches_oracle_gradient(renderer, mask):
     assert max(errs.values()) <= 1.0, errs
 
 
+def test_autograd_tangent_space_matches_oracle_gradient(renderer):
+    """The autograd path with a tangent-space binding and a deformed mesh per frame: the
+    oracle's dL/dimg (zero at the pixels it flags as ambiguous) back through rasterize() gives
+    the oracle's gradients of G0, the blendshapes and the weights."""
+    from gpu_helpers import oracle_fwd_bwd
+    from paper_2503_12886_gb300.rasterizer import DeviceBinding
+    from test_gpu_parity import tangent_batch
+    batch = tangent_batch()
+    targets = synth.make_targets(batch, 41)
+    ores, L, dls, per_model, dpsi, _ = oracle_fwd_bwd(batch, targets, "l1", drop_flagged=True)
+    frames, psi, fp, models = _autograd_inputs(batch)
+    bindings = [DeviceBinding.of(m.binding, "cuda:0") for m in batch.models]
+    verts = [torch.from_numpy(f.verts).cuda() for f in batch.frames]
+    imgs = rasterize(renderer, frames, psi, fp, models, bindings=bindings, verts=verts)
+    torch.autograd.backward(imgs, [torch.from_numpy(d.astype(np.float32)).cuda() for d in dls])
+    m = batch.models[0]
+    g0, dg = models[0][3].grad, models[0][4].grad
+    errs = {"g0": grad_error(g0.cpu().numpy()[:, :m.n], per_model[0][0][:, :m.n]),
+            "dg": grad_error(dg.cpu().numpy()[..., :m.n].reshape(-1, m.n),
+                             per_model[0][1][..., :m.n].reshape(-1, m.n)),
+            "psi": grad_error(psi.grad.cpu().numpy(), dpsi, axis_rows=False)}
+    assert max(errs.values()) <= 1.0, errs
+
+
 def test_autograd_central_differences(renderer):
     """dL/dtheta from the backward against central differences of the fp32 forward itself,
     for a weighted sum of pixels (steps sized for fp32, Gaussians with large gradients)."""
