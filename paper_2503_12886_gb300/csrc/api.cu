@@ -665,8 +665,11 @@ int rgba_step_adam_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size
     return do_render_bwd(ctx, k, dl, T, n, true, &fa);
 }
 
+}  // extern "C"
+
 // The one host synchronisation of a synchronous entry point: reads the counters into out.
-int read_out(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, rgba_step_out *out, void *stream) {
+int rgba::read_out(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, rgba_step_out *out,
+                   void *stream) {
     Plan p;
     make_plan(batch, p);
     const long long cap = cap_for_bytes(p.L, ws_bytes);
@@ -689,6 +692,8 @@ int read_out(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
     if (h.device_error & 2u) return fail(RGBA_ERR_INVALID_ARG, "tangent-space binding index out of range");
     return RGBA_OK;
 }
+
+extern "C" {
 
 int rgba_step(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *target,
               int loss_kind, float *img, rgba_step_out *out, void *stream) {

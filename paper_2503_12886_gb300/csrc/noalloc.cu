@@ -6,6 +6,7 @@
 // (preprocess, bin/sort, compositing) with all scratch taken from one fixed block of device
 // memory that is part of this library's image: every GPU that loads the library holds the
 // block until the process exits, and no call allocates or frees device memory.
+#include <cstring>
 #include <mutex>
 
 #include "rgba_internal.cuh"
@@ -42,11 +43,11 @@ extern "C" int rgba_render_fwd_noalloc(rgba_ctx_t ctx, const rgba_batch *batch, 
                                        void *stream) {
     if (!ctx || !batch || !out) return rgba::set_error(RGBA_ERR_INVALID_ARG, "ctx/batch/out is NULL");
     memset(out, 0, sizeof(*out));
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return rgba::set_error(RGBA_ERR_CUDA, "cudaSetDevice failed");
-    // the batch must leave room in the block for at least one pair per Gaussian record
+    // every host-side check comes before the first enqueue
     size_t fixed = 0;
     int rc = rgba_workspace_size(batch, 0, &fixed);
     if (rc) return rc;
+    // the batch must leave room in the block for at least one pair per Gaussian record
     rgba_ws_layout lay;
     if (fixed > kScratchBytes || (rc = rgba_workspace_layout(batch, kScratchBytes, &lay)) != RGBA_OK ||
         lay.pair_capacity < lay.records_total)
@@ -55,6 +56,9 @@ extern "C" int rgba_render_fwd_noalloc(rgba_ctx_t ctx, const rgba_batch *batch, 
                                "with one pair per Gaussian record must fit); use rgba_render_fwd "
                                "with a caller-allocated workspace");
     if (batch->n_frames == 0) return RGBA_OK;
+    if (!img || !T_final || !n_contrib)
+        return rgba::set_error(RGBA_ERR_INVALID_ARG, "img/T_final/n_contrib is NULL");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return rgba::set_error(RGBA_ERR_CUDA, "cudaSetDevice failed");
     void *ws = nullptr;
     if ((rc = scratch_address(ctx->device, &ws)) != RGBA_OK)
         return rgba::set_error(rc, "could not resolve the scratch block's device address");
@@ -64,19 +68,8 @@ extern "C" int rgba_render_fwd_noalloc(rgba_ctx_t ctx, const rgba_batch *batch, 
     if ((rc = rgba_bin_sort(ctx, batch, ws, kScratchBytes, stream)) != RGBA_OK) return rc;
     if ((rc = rgba_render_fwd(ctx, batch, ws, kScratchBytes, img, T_final, n_contrib, stream)) != RGBA_OK)
         return rc;
-    rgba_counters h;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(&h, static_cast<unsigned char *>(ws) + lay.counters, sizeof(h),
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return rgba::set_error(RGBA_ERR_CUDA, "reading the no-alloc counters failed");
-    out->pairs = h.pairs;
-    out->pair_capacity = lay.pair_capacity;
-    out->overflow = h.overflow;
-    out->device_error = h.device_error;
-    if (h.overflow) {
-        out->pairs_needed = h.pairs;
-        return rgba::set_error(RGBA_ERR_CAPACITY, "pairs exceed the no-alloc scratch block");
-    }
-    return RGBA_OK;
+    // the same counter read as the other synchronous entry points: a pair overflow gives
+    // RGBA_ERR_CAPACITY (out->pairs_needed set), an out-of-range tangent-space binding index
+    // RGBA_ERR_INVALID_ARG
+    return rgba::read_out(ctx, batch, ws, kScratchBytes, out, stream);
 }

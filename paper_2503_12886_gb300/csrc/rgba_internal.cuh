@@ -154,6 +154,12 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 // Records msg as the calling thread's rgba_last_error() text and returns code.
 int set_error(int code, const char *msg);
 
+// The one host synchronisation of a synchronous entry point: reads the workspace counters on
+// `stream`, waits, fills out (pair capacity from ws_bytes) and maps the overflow flag and the
+// device error bits to RGBA_ERR_CAPACITY, RGBA_ERR_TIMEOUT and RGBA_ERR_INVALID_ARG.
+int read_out(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, rgba_step_out *out,
+             void *stream);
+
 // Launch wrappers (each returns the cudaError_t of its launch).
 cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t s);
 // One launch for the start of a step: n16[t] 16-byte units of table t from host src[t] to dst[t]

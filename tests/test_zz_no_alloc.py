@@ -58,3 +58,54 @@ def test_noalloc_rejects_batches_beyond_its_block(renderer):
                                     torch.cuda.current_stream().cuda_stream)
     assert e.value.code == api.RGBA_ERR_INVALID_ARG
     assert "no-alloc scratch block" in str(e.value)
+
+
+def test_noalloc_reports_a_pair_overflow_then_recovers(renderer):
+    """A batch whose records and pixels fit the block but whose (Gaussian, tile) pairs do not:
+    large splats over a 1024x1024 frame. The call returns RGBA_ERR_CAPACITY with the pair count
+    it needed; the next call with a batch that fits still matches the workspace path."""
+    import math
+    m = synth.make_model(11, 8000, 4, radii=(0.3, 0.3, 0.2), log_scale_mu=math.log(0.05))
+    big = synth.make_batch([m], [synth.Frame(0, 1024, 1024)], seed=11)
+    db = DeviceBatch(big, "cuda:0", grads=False)
+    img = torch.empty(3 * db.total_pix, device="cuda:0")
+    T = torch.empty(db.total_pix, device="cuda:0")
+    n = torch.empty(db.total_pix, dtype=torch.int32, device="cuda:0")
+    s = torch.cuda.current_stream().cuda_stream
+    rc, out = api.rgba_render_fwd_noalloc(renderer.ctx, db.struct(), img.data_ptr(), T.data_ptr(),
+                                          n.data_ptr(), s)
+    assert rc == api.RGBA_ERR_CAPACITY, api.last_error()
+    assert out.overflow == 1 and out.pair_capacity > 0
+    assert out.pairs_needed > out.pair_capacity and out.pairs_needed == out.pairs
+    test_noalloc_matches_workspace_path_twice(renderer)
+
+
+def test_noalloc_reports_a_binding_index_out_of_range(renderer):
+    """A tangent-space binding whose face index is past the mesh: the Gaussian is culled and
+    the call returns RGBA_ERR_INVALID_ARG after its synchronisation, like rgba_step."""
+    import dataclasses
+    mesh = synth.make_head_mesh(303, 12, 24)
+    m = synth.make_bound_model(303, 2000, 4, mesh)
+    face_of = m.binding.face_of.copy()
+    face_of[5] = m.binding.faces.shape[0] + 7
+    m = dataclasses.replace(m, binding=dataclasses.replace(m.binding, face_of=face_of))
+    fr = [synth.Frame(0, 96, 80, synth.frame_verts(mesh, 303, f)) for f in range(2)]
+    batch = synth.make_batch([m], fr, 303, jitter_deg=10, random_bg=True)
+    db = DeviceBatch(batch, "cuda:0", grads=False)
+    img = torch.empty(3 * db.total_pix, device="cuda:0")
+    T = torch.empty(db.total_pix, device="cuda:0")
+    n = torch.empty(db.total_pix, dtype=torch.int32, device="cuda:0")
+    with pytest.raises(api.RgbaError) as e:
+        api.rgba_render_fwd_noalloc(renderer.ctx, db.struct(), img.data_ptr(), T.data_ptr(),
+                                    n.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == api.RGBA_ERR_INVALID_ARG and "binding index" in str(e.value)
+
+
+def test_noalloc_rejects_null_outputs_before_enqueueing(renderer):
+    db = DeviceBatch(small_batch(), "cuda:0", grads=False)
+    T = torch.empty(db.total_pix, device="cuda:0")
+    n = torch.empty(db.total_pix, dtype=torch.int32, device="cuda:0")
+    with pytest.raises(api.RgbaError) as e:
+        api.rgba_render_fwd_noalloc(renderer.ctx, db.struct(), None, T.data_ptr(), n.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == api.RGBA_ERR_INVALID_ARG and "NULL" in str(e.value)
