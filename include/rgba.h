@@ -201,10 +201,14 @@ int rgba_render_fwd(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
 /* Back-propagation of dL/dimg (same layout as img) through compositing, projection,
  * activations and the blend. Uses only T_final and n_contrib from the forward (recomputes the
  * compositing in reverse). Writes models[m].grad_g0 / grad_dg and batch->grad_psi (those that
- * are non-NULL); the per-(frame, Gaussian) 2-D gradients stay in the workspace (grad2d). */
+ * are non-NULL); the per-(frame, Gaussian) 2-D gradients stay in the workspace (grad2d).
+ * grad_blended (device, 16-byte aligned, or NULL): also the gradient with respect to each
+ * frame's blended Gaussians G^psi_b of Eq. 1, before the blend's adjoint reduces it over the
+ * frames: frame b's [14][n_pad] block at float offset 14 * (sum of n_pad over frames before b),
+ * the layout of rgba_blend's out; zero for culled Gaussians and padding columns. */
 int rgba_render_bwd(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes,
                     const float *dL_dimg, const float *T_final, const int32_t *n_contrib,
-                    void *stream);
+                    float *grad_blended, void *stream);
 
 /* One training step: preprocess, bin/sort, render with the fused loss against `target`
  * (layout of img), backward, then ONE device-to-host read of the counters and a stream

@@ -112,7 +112,7 @@ def lib() -> C.CDLL:
             L.rgba_preprocess.argtypes = [P, Bp, P, sz, P]
             L.rgba_bin_sort.argtypes = [P, Bp, P, sz, P]
             L.rgba_render_fwd.argtypes = [P, Bp, P, sz, P, P, P, P]
-            L.rgba_render_bwd.argtypes = [P, Bp, P, sz, P, P, P, P]
+            L.rgba_render_bwd.argtypes = [P, Bp, P, sz, P, P, P, P, P]
             L.rgba_step.argtypes = [P, Bp, P, sz, P, i32, P, C.POINTER(RgbaStepOut), P]
             L.rgba_step_async.argtypes = [P, Bp, P, sz, P, i32, P, P]
             L.rgba_adam.argtypes = [P, Bp, C.POINTER(RgbaAdamCfg), C.POINTER(RgbaAdamState), i32, P, P]
@@ -192,9 +192,12 @@ def rgba_render_fwd(ctx, batch, ws, ws_bytes, img, T_final, n_contrib, stream) -
                                        n_contrib, stream))
 
 
-def rgba_render_bwd(ctx, batch, ws, ws_bytes, dL_dimg, T_final, n_contrib, stream) -> int:
+def rgba_render_bwd(ctx, batch, ws, ws_bytes, dL_dimg, T_final, n_contrib, grad_blended,
+                    stream) -> int:
+    """grad_blended: device pointer for the per-frame dL/dG^psi_b (layout of rgba_blend's
+    out), or None."""
     return check(lib().rgba_render_bwd(ctx, C.byref(batch), ws, ws_bytes, dL_dimg, T_final,
-                                       n_contrib, stream))
+                                       n_contrib, grad_blended, stream))
 
 
 def rgba_step(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream) -> tuple[int, RgbaStepOut]:

@@ -574,11 +574,13 @@ int rgba_render_fwd(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
 }
 
 int rgba_render_bwd(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *dL_dimg,
-                    const float *T_final, const int32_t *n_contrib, void *stream) {
+                    const float *T_final, const int32_t *n_contrib, float *grad_blended, void *stream) {
     Call k;
     int rc = prologue(ctx, batch, ws, ws_bytes, stream, k);
     if (rc || k.p.L.B == 0) return rc;
     if (!dL_dimg || !T_final || !n_contrib) return fail(RGBA_ERR_INVALID_ARG, "dL_dimg/T_final/n_contrib is NULL");
+    if (reinterpret_cast<uintptr_t>(grad_blended) & 15) return fail(RGBA_ERR_INVALID_ARG, "grad_blended must be 16-byte aligned");
+    k.c.grad_blended = grad_blended;
     return do_render_bwd(ctx, k, dL_dimg, T_final, n_contrib);
 }
 

@@ -413,6 +413,11 @@ k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
                 }
 #pragma unroll
                 for (int q = 0; q < kNch; ++q) s_dG[(fl * kNch + q) * kBwdChunk + li] = dG[q];
+                if (c.grad_blended && fl < ng && i0 + li < m.n_pad) {  // rgba_render_bwd's optional output
+                    float *o = c.grad_blended + s_rec[fl] * kNch + i0 + li;
+#pragma unroll
+                    for (int q = 0; q < kNch; ++q) o[(size_t)q * m.n_pad] = dG[q];
+                }
 #pragma unroll
                 for (int w = 0; w + 1 < kItems; ++w) {
                     c0[w] = c0[w + 1];

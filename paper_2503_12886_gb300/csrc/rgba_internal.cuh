@@ -104,6 +104,7 @@ struct Ctx {
     const float *psi;
     const float *fparams;
     float *grad_psi;
+    float *grad_blended;   // [sum over frames of 14 n_pad] or nullptr: dL/dG^psi_b per frame
     Counters *cnt;
     unsigned *tile_count;  // [T] ranked (<= kRankSlots tiles), then [T][kSubCounters] the others
     unsigned *tile_start;

@@ -220,10 +220,15 @@ class Renderer:
             self.ensure_workspace(db, int(out.pairs_needed * 1.25) + 4096)
         raise api.RgbaError(api.RGBA_ERR_CAPACITY, "workspace growth did not converge")
 
-    def backward(self, db: DeviceBatch, dl_dimg: torch.Tensor, T: torch.Tensor, n: torch.Tensor):
+    def backward(self, db: DeviceBatch, dl_dimg: torch.Tensor, T: torch.Tensor, n: torch.Tensor,
+                 grad_blended: torch.Tensor | None = None):
+        """grad_blended (optional, float32 [total_rec * 14] on the device): receives the
+        per-frame gradient with respect to the blended Gaussians (layout of blend())."""
         b = db.struct()
         api.rgba_render_bwd(self.ctx, b, self.ws.data_ptr(), self.ws.numel(),
-                            dl_dimg.data_ptr(), T.data_ptr(), n.data_ptr(), stream_ptr())
+                            dl_dimg.data_ptr(), T.data_ptr(), n.data_ptr(),
+                            grad_blended.data_ptr() if grad_blended is not None else None,
+                            stream_ptr())
 
     def blend(self, db: DeviceBatch) -> torch.Tensor:
         out = torch.zeros(db.total_rec * 14, dtype=torch.float32, device=f"cuda:{self.device}")

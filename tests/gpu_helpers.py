@@ -130,17 +130,45 @@ def grad_error(g: np.ndarray, ref: np.ndarray, axis_rows=True):
     return float((np.abs(gr - rows) / tol).max())
 
 
-def oracle_fwd_bwd(batch, targets, kind, tile=(16, 16), drop_flagged=False):
+def oracle_fwd_bwd(batch, targets, kind, tile=(16, 16), drop_flagged=False, with_blended=False):
     """Oracle forward, loss and backward. With drop_flagged, dL/dimg is zeroed at the pixels
     the oracle flags as ambiguous (a compositing cutoff within AMBIG_EPS / AMBIG_EPS_T): there
     the fp32 path may legitimately take the other decision, and the gradient of that pixel is
-    discontinuous, so both backward passes then see the same, decision-stable dL/dimg."""
+    discontinuous, so both backward passes then see the same, decision-stable dL/dimg.
+    with_blended: also return the per-frame gradients with respect to the blended Gaussians
+    ([14][n_pad] per frame)."""
     ores = oracle.forward(batch, tile=tile, eps=AMBIG_EPS, splat="spec", eps_t=AMBIG_EPS_T)
     L, dls = oracle.loss(batch, ores, targets, kind)
     if drop_flagged:
         dls = [np.where(r.flags[None] != 0, 0.0, d) for r, d in zip(ores, dls)]
     per_model, dpsi, g2s, dgbs = oracle.backward(batch, ores, dls, tile=tile)
+    if with_blended:
+        return ores, L, dls, per_model, dpsi, g2s, dgbs
     return ores, L, dls, per_model, dpsi, g2s
+
+
+def backward_errors(batch, db, per_model, dpsi, dgbs=None, grad_blended=None):
+    """grad_error of every model's dG0 and ddG, of dpsi and (when both are given) of each
+    frame's gradient with respect to its blended Gaussians (one row per channel). Also checks
+    that padding columns of dG0 stay zero."""
+    errs = {}
+    for mi, m in enumerate(db.models):
+        g0_ref, dg_ref = per_model[mi]
+        errs[f"g0[{mi}]"] = grad_error(m.grad_g0.cpu().numpy()[:, :m.n], g0_ref[:, :m.n])
+        errs[f"dg[{mi}]"] = grad_error(m.grad_dg.cpu().numpy()[..., :m.n].reshape(-1, m.n),
+                                       dg_ref[..., :m.n].reshape(-1, m.n))
+        assert np.all(m.grad_g0.cpu().numpy()[:, m.n:] == 0)
+    errs["psi"] = grad_error(db.grad_psi.cpu().numpy(), dpsi, axis_rows=False)
+    if dgbs is not None and grad_blended is not None:
+        gb = grad_blended.cpu().numpy()
+        worst = 0.0
+        for b, (mi, _, _) in enumerate(db.frames):
+            m = db.models[mi]
+            got = gb[db.rec_offsets[b] * 14: (db.rec_offsets[b] + m.n_pad) * 14].reshape(14, m.n_pad)
+            worst = max(worst, grad_error(got[:, :m.n], dgbs[b][:, :m.n]))
+            assert np.all(got[:, m.n:] == 0)
+        errs["blended"] = worst
+    return errs
 
 
 def gpu_step(batch, targets, kind, tile=(16, 16), smem_batch=64, renderer=None):

@@ -9,8 +9,8 @@ import oracle
 from paper_2503_12886_gb300 import synth
 from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
 
-from gpu_helpers import (GRAD_FLOOR, GRAD_RTOL, compare_decisions, compare_images,
-                         read_intermediates)
+from gpu_helpers import (GRAD_FLOOR, GRAD_RTOL, PIX_ATOL, backward_errors, compare_decisions,
+                         compare_images, oracle_fwd_bwd, read_intermediates)
 
 pytestmark = pytest.mark.gpu
 
@@ -80,6 +80,29 @@ def test_batched_workload_full_size(renderer):
         assert err.max() <= 1.0, (b, err.max())
         checked += len(idx)
     assert checked > 300
+
+
+def test_batched_workload_gradients_full_size(renderer):
+    """The batched training workload at its full size (N=60,000, K=32, B=16 at 512x512, the
+    bench's 16x16 tiles and 64-entry staging): every pixel of every frame, then dG0, ddG, dpsi
+    and each frame's gradient with respect to its blended Gaussians against the oracle, from
+    the same L1 dL/dimg (zero at the pixels the oracle flags as ambiguous)."""
+    batch = synth.workload_batched()
+    targets = synth.make_targets(batch, 99)
+    ores, L, dls, per_model, dpsi, g2s, dgbs = oracle_fwd_bwd(batch, targets, "l1",
+                                                               drop_flagged=True, with_blended=True)
+    db = DeviceBatch(batch, "cuda:0", tile=(16, 16), smem_batch=64)
+    img, T, n = renderer.forward(db)
+    torch.cuda.synchronize()
+    st = compare_images(batch, ores, db, img, T, n)
+    assert st["max_err"] <= PIX_ATOL and st["n_mismatch"] == 0, st
+    assert st["flagged"] <= 0.001 * st["pixels"], st
+    dl = db.pack_images([d.astype(np.float32) for d in dls])
+    gb = torch.full((db.total_rec * 14,), float("nan"), device="cuda:0")
+    renderer.backward(db, dl, T, n, grad_blended=gb)
+    torch.cuda.synchronize()
+    errs = backward_errors(batch, db, per_model, dpsi, dgbs, gb)
+    assert max(errs.values()) <= 1.0, errs
 
 
 class _view_batch:

@@ -15,8 +15,8 @@ import oracle
 from paper_2503_12886_gb300 import api, synth
 from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
 
-from gpu_helpers import (PIX_ATOL, compare_decisions, compare_images, grad_error,
-                         oracle_fwd_bwd, read_intermediates, run_gpu_forward)
+from gpu_helpers import (PIX_ATOL, backward_errors, compare_decisions, compare_images,
+                         grad_error, oracle_fwd_bwd, read_intermediates, run_gpu_forward)
 
 pytestmark = pytest.mark.gpu
 
@@ -244,3 +244,46 @@ def test_identity_frames_match_the_unbound_path_bit_for_bit(renderer):
             assert torch.equal(a, c)
         else:
             np.testing.assert_array_equal(a, c)
+
+
+def many_frames_batch(nframes, seed):
+    """One avatar rendered by more frames than the kernels take in one group (16): ragged
+    sizes, jittered cameras, random backgrounds."""
+    m = synth.make_model(seed, 3000, 8, log_scale_mu=math.log(5e-3))
+    sizes = [(64, 64), (96, 80), (80, 96)]
+    fr = [synth.Frame(0, *sizes[f % 3]) for f in range(nframes)]
+    return synth.make_batch([m], fr, seed=seed, jitter_deg=20, random_bg=True)
+
+
+def two_avatars_many_frames():
+    """50 frames interleaved over two avatars (33 and 17 frames): both past one frame group."""
+    ms = [synth.make_model(611, 3000, 8, log_scale_mu=math.log(5e-3)),
+          synth.make_model(612, 2500, 12, log_scale_mu=math.log(5e-3))]
+    fr = [synth.Frame(1 if f % 3 == 2 else 0, 64 + 16 * (f % 2), 80) for f in range(50)]
+    return synth.make_batch(ms, fr, seed=613, jitter_deg=20, random_bg=True)
+
+
+MANY = {"17": lambda: many_frames_batch(17, 601), "33": lambda: many_frames_batch(33, 602),
+        "40": lambda: many_frames_batch(40, 603), "33+17": two_avatars_many_frames}
+
+
+@pytest.mark.parametrize("case", list(MANY))
+def test_more_than_sixteen_frames_per_avatar(renderer, case):
+    """The preprocess runs a model's frames in rounds of 16 and the projection/blend backward
+    reduces them in groups of 16: decisions, pixels, dG0, ddG, dpsi and each frame's gradient
+    with respect to its blended Gaussians against the oracle when a model has 17 to 40."""
+    batch = MANY[case]()
+    targets = synth.make_targets(batch, 97)
+    ores, L, dls, per_model, dpsi, g2s, dgbs = oracle_fwd_bwd(batch, targets, "l1",
+                                                               drop_flagged=True, with_blended=True)
+    r, db, img, T, n = run_gpu_forward(batch, (16, 16), 64, renderer)
+    compare_decisions(batch, oracle.forward(batch, do_render=False), read_intermediates(r, db), db)
+    st = compare_images(batch, ores, db, img, T, n)
+    assert st["max_err"] <= PIX_ATOL and st["n_mismatch"] == 0, st
+    assert st["flagged"] <= 0.001 * st["pixels"], st
+    dl = db.pack_images([d.astype(np.float32) for d in dls])
+    gb = torch.full((db.total_rec * 14,), float("nan"), device="cuda:0")
+    r.backward(db, dl, T, n, grad_blended=gb)
+    torch.cuda.synchronize()
+    errs = backward_errors(batch, db, per_model, dpsi, dgbs, gb)
+    assert max(errs.values()) <= 1.0, errs
