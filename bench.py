@@ -238,12 +238,12 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     torch.cuda.set_device(local_rank)
-    from paper_2503_12886_gb300 import api, synth
+    from paper_2503_12886_gb300 import api, sharding, synth
     from paper_2503_12886_gb300.optim import Adam
     from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
 
     dev = f"cuda:{local_rank}"
-    work = make_workload(variants=args.variants)
+    work = make_workload(variants=args.variants, rank=rank)
     r = Renderer(local_rank)
     ref = synth.reference_avatar(work[0][0].models[0], 3999)
     dbs, tgs = [], []
@@ -254,6 +254,13 @@ def run_ours(args, rank, world, local_rank):
         rb = synth.Batch([ref], b.frames, b.psi, b.fparams, b.k_stride)
         timg, _, _ = r.forward(DeviceBatch(rb, dev, grads=False))
         tgs.append(timg.clone())
+    flat = None
+    if world > 1:
+        # frame-sharded data parallelism: this rank's 16 frames are its share of a global batch
+        # of 16 x world, and dG0 / ddG live in one flat buffer that the step all-reduces
+        for db in dbs:
+            db.loss_frames = FRAMES * world
+        flat = sharding.attach_flat_grads(dbs[0].models)
     img = torch.empty(3 * dbs[0].total_pix, dtype=torch.float32, device=dev)
     # size the workspace from eager steps: training moves the splats (on these targets the pair
     # count settles about 40 % above its start), so 1.6x headroom, and a replay that still
@@ -281,34 +288,63 @@ def run_ours(args, rank, world, local_rank):
                     api.rgba_step_async(r.ctx, structs[j], ws.data_ptr(), ws.numel(),
                                         tgs[j].data_ptr(), api.RGBA_LOSS_L1, img.data_ptr(),
                                         s.cuda_stream)
-                    opt.step(s.cuda_stream)
-                    host_cnt[j].copy_(ws[lay.counters: lay.counters + 24], non_blocking=True)
-                cap["graphs"].append(g)
+                    if world == 1:
+                        opt.step(s.cuda_stream)
+                        host_cnt[j].copy_(ws[lay.counters: lay.counters + 24], non_blocking=True)
+                tail = None
+                if world > 1:  # the update after the all-reduce, in a second graph
+                    tail = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(tail, stream=s):
+                        opt.step(s.cuda_stream)
+                        host_cnt[j].copy_(ws[lay.counters: lay.counters + 24], non_blocking=True)
+                cap["graphs"].append((g, tail))
         torch.cuda.synchronize()
 
     capture(int(pairs * 1.6) + 4096)
 
+    def replay(j):
+        """Step j's graph; with several ranks, then the step's one all-reduce of dG0 / ddG
+        (NCCL, on its own stream ordered after s) and the update's graph."""
+        g, tail = cap["graphs"][j]
+        g.replay()
+        if tail is not None:
+            sharding.all_reduce_grads(flat)
+            tail.replay()
+
+    def overflowed(j):
+        return bool(host_cnt[j][:8].numpy().view(np.uint32)[1])
+
+    def regrow(j):
+        cap["regrow"] += 1
+        capture(int(host_cnt[j][:8].numpy().view(np.uint32)[0] * 1.3) + 4096)
+
     def step(i):
         j = i % len(cap["graphs"])
         while True:
-            cap["graphs"][j].replay()
+            replay(j)
             s.synchronize()  # the one host synchronisation of the step
-            u = host_cnt[j][:8].numpy().view(np.uint32)
-            if not u[1]:
+            if not overflowed(j):
                 return
-            cap["regrow"] += 1
-            capture(int(u[0] * 1.3) + 4096)
+            regrow(j)
+            if world > 1:
+                # an overflowed rank contributed zero gradients to this step's all-reduce; it
+                # regrows for the next step instead of repeating this one, so that every rank
+                # runs the same collectives
+                return
 
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     with torch.cuda.stream(s):
+        t_w = time.perf_counter()
         for i in range(args.warmup):
             step(i)
-        t_end = time.perf_counter() + 1.0  # keep the GPU busy while the sampler starts
-        i = 0
-        while time.perf_counter() < t_end:
+        # keep the GPU busy for about a second while the sampler starts; every rank runs the
+        # same number of steps (each step has a collective), from the slowest rank's pace
+        per_step = (time.perf_counter() - t_w) / max(1, args.warmup)
+        if world > 1:
+            per_step = max_over_ranks(per_step, dev)
+        for i in range(int(1.0 / max(per_step, 1e-4)) + 1):
             step(i)
-            i += 1
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -394,25 +430,33 @@ def run_ours(args, rank, world, local_rank):
     cs = torch.cuda.Stream(device=dev)  # copy stream: step i + 1's inputs travel during step i
     n_e2e = max(10, min(args.steps, 100))
     with torch.cuda.stream(s):
-        e2e_run(dbs, tgs, host_in, s, cs, 3, cap, host_cnt, capture)
+        e2e_run(dbs, tgs, host_in, s, cs, 3, replay, overflowed, regrow, world == 1)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
-        e2e_run(dbs, tgs, host_in, s, cs, n_e2e, cap, host_cnt, capture)
+        e2e_run(dbs, tgs, host_in, s, cs, n_e2e, replay, overflowed, regrow, world == 1)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t_e2e = max_over_ranks(t_e2e, dev)
     e2e_value = world * FRAMES * n_e2e / t_e2e
 
     # the plain per-frame path (Fig. 4a): every frame its own step with its own host sync
+    # (the single-GPU comparison paths and the other workloads run at N = 1 only)
+    solo = world == 1
     per_frame = None
-    if not args.no_per_frame:
+    if solo and not args.no_per_frame:
         per_frame = per_frame_path(api, work[0], dev, r)
+    if world > 1:
+        last_loss = sharding.all_reduce_loss(last_loss, dev)
 
     r.close()
-    uneven = None if args.no_uneven else run_uneven(local_rank)
-    tangent = None if args.no_tangent else run_tangent(local_rank)
-    color_init = None if args.no_tangent else run_color_init(local_rank)
-    online = None if args.no_online else run_online(local_rank)
-    serve = None if args.no_serve else run_serve(local_rank, args.serve_seconds)
+    uneven = None if args.no_uneven or not solo else run_uneven(local_rank)
+    tangent = None if args.no_tangent or not solo else run_tangent(local_rank)
+    color_init = None if args.no_tangent or not solo else run_color_init(local_rank)
+    online = None if args.no_online or not solo else run_online(local_rank)
+    serve = None if args.no_serve or not solo else run_serve(local_rank, args.serve_seconds)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -428,7 +472,10 @@ def run_ours(args, rank, world, local_rank):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic (seeded generator, random-init avatar)",
                 "config": {"workload": WORKLOAD, "global_batch": FRAMES * world, "seq_len": None,
-                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "parallelism": (f"frame-sharded data parallel x{world}: {FRAMES} "
+                                           f"frames per GPU, one NCCL all-reduce (sum) of dG0 + "
+                                           f"ddG ({4 * flat.numel()} bytes) per step, identical "
+                                           f"Adam on every rank") if world > 1 else "single GPU",
                            "n_gaussians": N_GAUSS, "k": K_BASES, "resolution": RES,
                            "input_variants": len(dbs),
                            "l2": "inputs larger than L2 (bases 69 MB + targets 50 MB + "
@@ -458,15 +505,17 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def e2e_run(dbs, tgs, host_in, s, cs, steps, cap, host_cnt, capture):
+def e2e_run(dbs, tgs, host_in, s, cs, steps, replay, overflowed, regrow, redo):
     """`steps` training steps end to end through the captured step graphs (rgba_step_async +
-    rgba_adam + the counter read, one graph per input variant): every step's inputs (targets,
+    rgba_adam + the counter read, one graph per input variant; with several ranks the step's
+    all-reduce between the step's graph and the update's): every step's inputs (targets,
     weights, cameras) are copied from pinned host memory on the copy stream cs while the
     previous step computes on s; each step waits for its copies and replays its graph, and the
     host reads step i's loss and pair count (its one host synchronisation) while step i + 1
     runs. A variant's buffers are refilled only after the step that last read them is known to
-    be complete. A step that overflowed the pair buffer is replayed after the workspace grows."""
-    import numpy as np
+    be complete. A step that overflowed the pair buffer grows the workspace and, with `redo`
+    (one rank), is replayed; with several ranks it is not repeated, so that every rank runs the
+    same collectives."""
     import torch
     nv = len(dbs)
     done = [torch.cuda.Event() for _ in range(nv)]
@@ -482,14 +531,12 @@ def e2e_run(dbs, tgs, host_in, s, cs, steps, cap, host_cnt, capture):
             ev.record(cs)
         return ev
 
-    def overflowed(j):
-        return bool(host_cnt[j][:8].numpy().view(np.uint32)[1])
-
-    def redo(j):  # grow, capture again, replay variant j's step until it fits
+    def fix(j):  # grow and capture again; with redo, replay variant j's step until it fits
         while overflowed(j):
-            cap["regrow"] += 1
-            capture(int(host_cnt[j][:8].numpy().view(np.uint32)[0] * 1.3) + 4096)
-            cap["graphs"][j].replay()
+            regrow(j)
+            if not redo:
+                return
+            replay(j)
             s.synchronize()
 
     ready = issue(0)
@@ -497,14 +544,15 @@ def e2e_run(dbs, tgs, host_in, s, cs, steps, cap, host_cnt, capture):
     for i in range(steps):
         j = i % nv
         s.wait_event(ready)
-        cap["graphs"][j].replay()
+        replay(j)
         done[j].record(s)
         if pending is not None:  # the previous step's one host synchronisation
             done[pending].synchronize()
             if overflowed(pending):
                 s.synchronize()
-                redo(pending)
-                redo(j)  # ran with the old workspace: check it too
+                fix(pending)
+                if redo:
+                    fix(j)  # ran with the old workspace: check it too
         if i + 1 < steps:
             if nv < 2:  # step i + 1 - nv is step i itself, still running
                 s.synchronize()
@@ -513,7 +561,7 @@ def e2e_run(dbs, tgs, host_in, s, cs, steps, cap, host_cnt, capture):
     if pending is not None:
         done[pending].synchronize()
         if overflowed(pending):
-            redo(pending)
+            fix(pending)
 
 
 def per_frame_path(api, work0, dev, r):

@@ -72,7 +72,8 @@ typedef enum {
 #define RGBA_MAX_DIM 4096
 
 /* Loss kinds for rgba_step (Sec. 3.2 "Loss Function" uses L1). Each frame's loss is the mean
- * over its 3*H*W values; the batch loss is the mean over frames. */
+ * over its 3*H*W values; the batch loss is their sum over the batch's frames divided by
+ * rgba_batch.loss_frames (the mean over frames when that is 0). */
 #define RGBA_LOSS_L1 1
 #define RGBA_LOSS_L2 2 /* 1/2 (I - target)^2 */
 
@@ -121,6 +122,10 @@ typedef struct {
     float *grad_psi;            /* device [n_frames][k_stride] or NULL, overwritten */
     int32_t tile_w, tile_h;     /* screen tile shape: 16x16 or 8x32 (tile_w * tile_h == 256) */
     int32_t smem_batch;         /* list entries a compositing warp stages per step: 64, 128 or 256 (0: 64) */
+    int32_t loss_frames;        /* frames the batch loss is averaged over: 0 = n_frames; a rank of
+                                   a frame-sharded data-parallel step passes the global batch size
+                                   (>= n_frames), so that its loss and gradients are its share of
+                                   the global batch's and a sum over ranks gives the batch's */
 } rgba_batch;
 
 typedef struct {

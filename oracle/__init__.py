@@ -264,9 +264,12 @@ def forward(batch, tile=(16, 16), render_frames=None, tile_masks=None, eps=1e-5,
     return out
 
 
-def loss(batch, res, targets, kind="l1"):
-    """Mean per frame, averaged over frames; returns (L, [dL/dimg per frame])."""
-    B = len(batch.frames)
+def loss(batch, res, targets, kind="l1", n_total=None):
+    """Mean per frame, averaged over frames; returns (L, [dL/dimg per frame]). n_total: the
+    frame count of the whole batch when `batch` holds only some of its frames (one rank's share
+    of a frame-sharded batch): L and its gradients are then this share's part of the whole
+    batch's mean, and the sum over the shares is the whole batch's."""
+    B = len(batch.frames) if n_total is None else n_total
     total = 0.0
     grads = []
     for b, fr in enumerate(batch.frames):

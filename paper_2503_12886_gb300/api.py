@@ -51,7 +51,7 @@ class RgbaBatch(C.Structure):
                 ("n_frames", C.c_int32), ("frames", C.POINTER(RgbaFrame)),
                 ("k_stride", C.c_int32), ("psi", C.c_void_p), ("fparams", C.c_void_p),
                 ("grad_psi", C.c_void_p), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
-                ("smem_batch", C.c_int32)]
+                ("smem_batch", C.c_int32), ("loss_frames", C.c_int32)]
 
 
 class RgbaStepOut(C.Structure):

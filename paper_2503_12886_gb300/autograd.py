@@ -37,6 +37,7 @@ def _device_batch(spec: _Frames, psi, fparams, models, grads: bool) -> DeviceBat
     db.grad_psi = torch.zeros_like(psi) if grads else None
     db.tile = spec.tile
     db.smem_batch = spec.smem_batch
+    db.loss_frames = 0
     offs, tot = [], 0
     for _, w, h in db.frames:
         offs.append(tot)

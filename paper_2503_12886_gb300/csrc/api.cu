@@ -130,6 +130,8 @@ int make_plan(const rgba_batch *b, Plan &p) {
         p.max_k = std::max(p.max_k, mi.k);
     }
     if (B > 0 && (!b->psi || !b->fparams)) return fail(RGBA_ERR_INVALID_ARG, "psi/fparams is NULL");
+    if (b->loss_frames != 0 && b->loss_frames < B)
+        return fail(RGBA_ERR_INVALID_ARG, "loss_frames must be 0 or at least n_frames");
     long long dpsi = 0;
     for (int m = 0; m < M; ++m) {
         ModelInfo &mi = p.models[m];
@@ -150,6 +152,7 @@ int make_plan(const rgba_batch *b, Plan &p) {
     L.tw = tw;
     L.th = th;
     L.smem_batch = sb;
+    L.loss_frames = b->loss_frames ? b->loss_frames : B;
     L.dpsi_floats = dpsi;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -237,6 +240,7 @@ Ctx make_ctx(const Layout &L, unsigned char *ws, const rgba_batch *b) {
     c.k_stride = L.k_stride;
     c.tw = L.tw;
     c.th = L.th;
+    c.loss_frames = L.loss_frames;
     return c;
 }
 

@@ -200,7 +200,7 @@ __device__ __forceinline__ void finish_pixel(const Ctx &c, const FrameInfo &f, i
     n_contrib[f.pix_base + pix] = p.last;
     if (target) {
         const float *tg = target + f.pix_base * 3 + pix;
-        const float scale = 1.0f / (3.0f * (float)hw * (float)c.B);
+        const float scale = 1.0f / (3.0f * (float)hw * (float)c.loss_frames);
         const float d0 = o0 - tg[0], d1 = o1 - tg[hw], d2 = o2 - tg[2 * hw];
         float *dl = dl_dimg + f.pix_base * 3 + pix;
         if (loss_kind == RGBA_LOSS_L1) {

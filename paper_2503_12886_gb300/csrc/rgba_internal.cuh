@@ -93,6 +93,7 @@ struct Layout {
     long long dpsi_floats;
     long long cap;
     int B, M, k_stride, tw, th, smem_batch;
+    int loss_frames;       // the loss's frame count (rgba_batch.loss_frames, or B)
     int max_n_pad;
 };
 
@@ -123,6 +124,7 @@ struct Ctx {
     float *depth;      // [R]: view-space depth of each kept record (the scatter's sort key)
     long long R, T, cap;
     int B, M, k_stride, tw, th;
+    int loss_frames;       // the loss is averaged over this many frames (>= B)
 };
 
 // Programmatic dependent launch (Hopper/Blackwell): a kernel launched with launch_pdl may be

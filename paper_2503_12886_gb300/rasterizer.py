@@ -96,6 +96,9 @@ class DeviceBatch:
             rt += self.models[mi].n_pad
         self.rec_offsets = rec
         self.total_rec = rt
+        # frames the loss is averaged over (0: this batch's own); a rank of a frame-sharded
+        # data-parallel step sets the global batch size (sharding.py)
+        self.loss_frames = 0
         self._struct = None
 
     @property
@@ -122,6 +125,7 @@ class DeviceBatch:
         b.grad_psi = self.grad_psi.data_ptr() if self.grad_psi is not None else None
         b.tile_w, b.tile_h = self.tile
         b.smem_batch = self.smem_batch
+        b.loss_frames = self.loss_frames
         self._keep = (ms, fs)
         self._struct = b
         return b
