@@ -930,13 +930,28 @@ def run_serve(local_rank, seconds):
     srv.run(warm, realtime=True)
     st = srv.run(requests_from_trace(trace, avatars), realtime=True)
     pf = srv.run_per_frame(requests_from_trace(trace, avatars), realtime=True)
+    # capacity: the first n_sat requests of the same trace all waiting at once (a closed loop
+    # that never lets either path idle), frames/s until the last one completes
+    n_sat = min(len(trace), 4000)
+    cap_cb = srv.run(requests_from_trace(trace[:n_sat], avatars), realtime=False)
+    cap_pf = srv.run_per_frame(requests_from_trace(trace[:n_sat], avatars), realtime=False)
     srv.close()
     return {"workload": "32 avatars N U[30k,100k] K=32; Poisson 2000 req/s for "
                         f"{seconds:g} s; 80 % 512x512 / 20 % 1024x1024; 40 GB budget",
             "frames_per_s": st["frames_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-            "requests": st["requests"], "batches": st["batches"],
+            "max_ms": st["max_ms"], "requests": st["requests"], "batches": st["batches"],
+            "regrowths": st["regrowths"],
+            "slots": {"count": len(srv.slots), "max_frames": srv.max_frames,
+                      "pairs_per_gaussian": srv.ppg, "pair_capacity": srv.pair_capacity,
+                      "fixed_bytes": srv.fixed_bytes},
             "per_frame": {"frames_per_s": pf["frames_per_s"], "p50_ms": pf["p50_ms"],
-                          "p99_ms": pf["p99_ms"]}}
+                          "p99_ms": pf["p99_ms"], "max_ms": pf["max_ms"]},
+            "capacity": {"requests": n_sat,
+                         "continuous_batching_frames_per_s": cap_cb["frames_per_s"],
+                         "batches": cap_cb["batches"], "regrowths": cap_cb["regrowths"],
+                         "per_frame_frames_per_s": cap_pf["frames_per_s"],
+                         "how": "all requests waiting at t = 0 (closed loop), frames/s until "
+                                "the last completes"}}
 
 
 def main():

@@ -15,7 +15,9 @@ The per-frame path (one request per launch, a host sync per request) is the comp
 from __future__ import annotations
 
 import collections
+import contextlib
 import ctypes as C
+import gc
 import time
 from dataclasses import dataclass, field
 
@@ -41,6 +43,24 @@ class Request:
     image: np.ndarray | None = None
 
 
+@contextlib.contextmanager
+def _no_gc_pauses():
+    """The request loops run with Python's cyclic garbage collector off (one collection and a
+    freeze of what exists before the loop): a full collection stops the host thread, and with it
+    every queued request, for tens of milliseconds (measured: single 31-36 ms stalls of both
+    loops at 2,000 requests/s). Reference counting still frees the loop's own objects."""
+    was = gc.isenabled()
+    gc.collect()
+    gc.freeze()
+    gc.disable()
+    try:
+        yield
+    finally:
+        gc.unfreeze()
+        if was:
+            gc.enable()
+
+
 @dataclass
 class _Slot:
     stream: torch.cuda.Stream
@@ -62,7 +82,8 @@ class _Slot:
 class Server:
     def __init__(self, avatars: list[synth.Model], device: int = 0, hbm_budget: float = 40e9,
                  max_frames: int = 32, slots: int = 2, max_res: int = 1024, tile=(16, 16),
-                 smem_batch: int = 64, pairs_per_gaussian: float = 4.0):
+                 smem_batch: int = 64, pairs_per_gaussian: float | None = None,
+                 headroom: float = 1.3):
         if any(m.binding is not None for m in avatars):
             raise ValueError("the server renders world-space avatars; a tangent-space avatar "
                              "needs a deformed mesh per request")
@@ -76,16 +97,30 @@ class Server:
         self.used = 0.0
         self.max_frames = max_frames
         self.tile, self.smem_batch = tile, smem_batch
-        self.ppg = pairs_per_gaussian
         max_n = max(m.n_pad for m in self.models)
         max_pix = max_frames * max_res * max_res
         self.max_res = max_res
-        # workspace sized for the largest possible batch
+        self.regrowths = 0
+        # (Gaussian, tile) pairs per Gaussian at the largest resolution, measured once at start-up
+        # (every avatar from the corners of the request camera range), times the headroom: the
+        # slot workspaces then hold a batch of max_frames such frames of the largest avatar, so
+        # that no batch overflows and nothing is allocated inside the request loop
+        self.ppg = (pairs_per_gaussian if pairs_per_gaussian is not None
+                    else headroom * self._measure_pairs_per_gaussian(max_res))
         frames = [(0, max_res, max_res)] * max_frames
         probe = self._struct([0] * 0, frames, None, None, models=[self.models[int(np.argmax(
             [m.n_pad for m in self.models]))]])
-        pairs = int(max_frames * max_n * self.ppg)
+        pairs = int(max_frames * max_n * self.ppg) + 4096
         ws_bytes = api.rgba_workspace_size(probe, pairs)
+        self.pair_capacity = pairs
+        # the slots' device memory (workspaces, outputs, weights and cameras) is held for the
+        # server's life and counts against the HBM budget; requests are admitted in what is left
+        self.fixed_bytes = float(slots * (ws_bytes + 4 * (5 * max_pix + max_frames * (self.k_stride
+                                                                                     + api.RGBA_FP_STRIDE))))
+        if self.fixed_bytes >= self.budget:
+            self.r.close()
+            raise ValueError(f"the slots alone need {self.fixed_bytes / 1e9:.2f} GB, more than the "
+                             f"{self.budget / 1e9:.2f} GB budget")
         self.slots = []
         for _ in range(slots):
             self.slots.append(_Slot(
@@ -102,6 +137,25 @@ class Server:
                 event=torch.cuda.Event()))
         self.lat: list[float] = []
         self.frames_done = 0
+
+    def _measure_pairs_per_gaussian(self, res: int) -> float:
+        """The largest (Gaussian, tile) pair count per Gaussian over every avatar rendered at
+        res x res from five cameras (straight on and the four corners of the +-20 deg yaw /
+        pitch range), zero weights."""
+        from .rasterizer import DeviceBatch
+        worst = 0.0
+        for a, m in enumerate(self.models):
+            cams = [(0.0, 0.0)] + [(sy * np.radians(20.0), sp * np.radians(20.0))
+                                   for sy in (-1, 1) for sp in (-1, 1)]
+            fp = np.stack([synth.camera_params(res, res, y, p) for y, p in cams]).astype(np.float32)
+            b = synth.Batch([], [synth.Frame(0, res, res)] * len(cams),
+                            np.zeros((len(cams), self.k_stride), np.float32), fp, self.k_stride)
+            db = DeviceBatch(b, self.models[0].g0.device, tile=self.tile,
+                             smem_batch=self.smem_batch, grads=False, models=[m])
+            self.r.forward(db)
+            worst = max(worst, self.r.counters(db)["pairs"] / (len(cams) * m.n))
+        self.r.ws = None  # the probe's workspace goes back to the caching allocator
+        return worst
 
     # -- helpers ---------------------------------------------------------------------------
     def _struct(self, order, frames, psi_ptr, fp_ptr, models=None):
@@ -156,10 +210,12 @@ class Server:
 
     def _finish(self, slot: _Slot, now: float, keep_images: bool):
         u = slot.cnt_h.numpy()[:16].view(np.uint32)
-        if u[1]:  # overflow: grow this slot's workspace and render the batch again
+        if u[1]:  # overflow (not expected: the capacity is sized at start-up): grow, render again
             b, _ = slot.keep
             need = api.rgba_workspace_size(b, int(u[0] * 1.25) + 4096)
+            self.fixed_bytes += need - slot.ws.numel()
             slot.ws = torch.empty(need, dtype=torch.uint8, device=slot.ws.device)
+            self.regrowths += 1
             self._launch(slot, slot.reqs)
             return
         off = 0
@@ -180,11 +236,16 @@ class Server:
             timeout_s: float = 600.0) -> dict:
         """Serves the requests (sorted by t_arrival). With realtime, request i becomes visible
         at t0 + t_arrival; otherwise all are visible at once. Returns throughput and latency."""
+        with _no_gc_pauses():
+            return self._run(requests, realtime, keep_images, timeout_s)
+
+    def _run(self, requests, realtime, keep_images, timeout_s) -> dict:
         reqs = sorted(requests, key=lambda q: q.t_arrival)
         arrivals = collections.deque(reqs)
         waiting: collections.deque = collections.deque()  # arrived, waiting for budget
         admitted: collections.deque = collections.deque()
         self.lat, self.frames_done = [], 0
+        regrow0 = self.regrowths
         t0 = time.perf_counter()
         n_total = len(reqs)
         finished = 0
@@ -201,7 +262,7 @@ class Server:
                     q.status, q.error = "rejected", "unknown avatar"
                     finished += 1
                     continue
-                if self.request_bytes(q) > self.budget:
+                if self.request_bytes(q) > self.budget - self.fixed_bytes:
                     q.status, q.error = "rejected", "request larger than the HBM budget"
                     finished += 1
                     continue
@@ -210,7 +271,7 @@ class Server:
                     finished += 1
                     continue
                 waiting.append(q)
-            while waiting and self.used + self.request_bytes(waiting[0]) <= self.budget:
+            while waiting and self.used + self.request_bytes(waiting[0]) <= self.budget - self.fixed_bytes:
                 q = waiting.popleft()
                 self.used += self.request_bytes(q)
                 q.status = "admitted"
@@ -235,11 +296,15 @@ class Server:
                 "wall_s": wall, "frames_per_s": self.frames_done / wall,
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                "max_ms": 1e3 * float(lat.max())}
+                "max_ms": 1e3 * float(lat.max()), "regrowths": self.regrowths - regrow0}
 
     def run_per_frame(self, requests: list[Request], realtime: bool = True) -> dict:
         """The per-frame path: each request rendered alone as soon as the previous one finished,
         with a host synchronisation per request."""
+        with _no_gc_pauses():
+            return self._run_per_frame(requests, realtime)
+
+    def _run_per_frame(self, requests, realtime) -> dict:
         reqs = sorted(requests, key=lambda q: q.t_arrival)
         slot = self.slots[0]
         lat = []
@@ -260,7 +325,8 @@ class Server:
         lat = np.sort(np.array(lat))
         return {"requests": len(reqs), "wall_s": wall, "frames_per_s": len(reqs) / wall,
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "max_ms": 1e3 * float(lat.max())}
 
     def close(self):
         self.r.close()

@@ -226,13 +226,30 @@ def test_serving_realtime_overlap_and_latency():
 
 
 def test_serving_admission_budget_and_rejections():
-    avatars, srv = _small_server(budget=30e6, slots=2)
+    avatars, srv = _small_server(slots=2)
+    srv.budget = srv.fixed_bytes + 30e6       # 30 MB for requests beside the slots' memory
     reqs = _requests(avatars, 10)
     reqs[3].avatar = 99                         # injected host-side failure: unknown avatar
     reqs[5].width = reqs[5].height = 4096       # larger than the whole budget
     st = srv.run(reqs, realtime=False)
     assert reqs[3].status == "rejected" and reqs[5].status == "rejected"
     done = [q for q in reqs if q.status == "done"]
-    assert len(done) == 8 and st["served"] == 8
+    assert len(done) == 8 and st["served"] == 8 and st["regrowths"] == 0
     assert srv.used == pytest.approx(0.0, abs=1.0)
+    srv.close()
+
+
+def test_serving_slots_sized_from_measured_pairs():
+    """The slot workspaces hold a full batch of the largest avatar at the largest resolution
+    (pairs per Gaussian measured at start-up): a batch of max_frames such requests renders
+    without a regrowth, and a budget smaller than the slots' own memory is refused."""
+    avatars, srv = _small_server()
+    assert srv.ppg > 1.0 and srv.pair_capacity >= srv.max_frames * max(m.n for m in avatars)
+    big = int(np.argmax([m.n for m in avatars]))
+    trace = [(0.0, big, 512, (0.3 * np.random.default_rng(i).standard_normal(8)).astype(np.float32))
+             for i in range(srv.max_frames)]
+    st = srv.run(requests_from_trace(trace, avatars, 7), realtime=False)
+    assert st["served"] == srv.max_frames and st["regrowths"] == 0
+    with pytest.raises(ValueError):
+        Server(avatars, 0, hbm_budget=srv.fixed_bytes / 2, max_frames=8, slots=2, max_res=512)
     srv.close()
