@@ -39,6 +39,9 @@ N_GAUSS, K_BASES, FRAMES, RES = 60_000, 32, 16, 512
 # conic/mean/opacity terms 19 (counted from the kernel's arithmetic; a fused multiply-add is 2).
 BWD_FLOPS_PER_UNIT = 59
 FWD_FLOPS_PER_UNIT = 20
+# FP32 FLOPs of an entry that does not blend at a pixel: the offset from the splat's mean and
+# the power of the conic (2 subtractions, 2 multiply-adds, 3 multiplies) before the cutoff test
+REJECT_FLOPS = 9
 SMS, FP32_LANES = 152, 128
 
 
@@ -126,9 +129,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(kernel: str, src_file: str):
-    """DRAM bytes per launch from the committed ncu summary, only while the kernel source is
-    unchanged since the capture."""
+def traffic_for(kernel: str, src_file: str, key: str = "dram_bytes_per_launch"):
+    """A per-launch ncu figure (DRAM bytes by default) from the committed summary, only while
+    the kernel source is unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -138,19 +141,21 @@ def traffic_for(kernel: str, src_file: str):
         return None
     with open(os.path.join(ROOT, "paper_2503_12886_gb300", "csrc", src_file), "rb") as f:
         sha = hashlib.sha1(f.read()).hexdigest()
-    return d.get("dram_bytes_per_launch") if d.get("src_sha1") == sha else None
+    return d.get(key) if d.get("src_sha1") == sha else None
 
 
 # ---------------------------------------------------------------------------------------------
-def make_workload(seed_base=3000, variants=4):
+def make_workload(seed_base=3000, variants=4, rank=0):
+    """`variants` batches of FRAMES frames of one avatar. Every rank of a data-parallel run has
+    the same avatar (the replicas start equal) and its own frames (weights, cameras, targets)."""
     from paper_2503_12886_gb300 import synth
     model = synth.make_model(seed_base, N_GAUSS, K_BASES)
     frames = [synth.Frame(0, RES, RES) for _ in range(FRAMES)]
     out = []
     for j in range(variants):
-        b = synth.make_batch([model], frames, seed_base + 101 * (j + 1), jitter_deg=20.0,
-                             random_bg=True)
-        out.append((b, synth.make_targets(b, seed_base + 7 * (j + 1))))
+        b = synth.make_batch([model], frames, seed_base + 101 * (j + 1) + 7919 * rank,
+                             jitter_deg=20.0, random_bg=True)
+        out.append((b, synth.make_targets(b, seed_base + 7 * (j + 1) + 7919 * rank)))
     return out
 
 
@@ -366,11 +371,16 @@ def run_ours(args, rank, world, local_rank):
 
     # per-stage device time (CUDA events on the launching stream), eager steps
     api.rgba_profile_enable(r.ctx, True)
-    prof, adam_ms = [], []
+    prof, adam_ms, ar_ms = [], [], []
     with torch.cuda.stream(s):
         for j in range(len(dbs)):
             api.rgba_step_async(r.ctx, structs[j], ws.data_ptr(), ws.numel(), tgs[j].data_ptr(),
                                 api.RGBA_LOSS_L1, img.data_ptr(), s.cuda_stream)
+            if world > 1:  # the step's all-reduce, timed on the stream that orders it
+                x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                x0.record(s)
+                sharding.all_reduce_grads(flat)
+                x1.record(s)
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(s)
             opt.step(s.cuda_stream)
@@ -378,9 +388,23 @@ def run_ours(args, rank, world, local_rank):
             prof.append(api.rgba_profile_read(r.ctx))
             torch.cuda.synchronize()
             adam_ms.append(a0.elapsed_time(a1))
+            if world > 1:
+                ar_ms.append(x0.elapsed_time(x1))
+    # one more eager step with the compositing statistics counted (counting instances of the
+    # two compositing kernels; not timed): how many (pixel, entry) pairs blend, how many
+    # (entry, pixel block) visits the kernels evaluate
+    api.rgba_profile_enable(r.ctx, 2)
+    with torch.cuda.stream(s):
+        api.rgba_step_async(r.ctx, structs[-1], ws.data_ptr(), ws.numel(), tgs[-1].data_ptr(),
+                            api.RGBA_LOSS_L1, img.data_ptr(), s.cuda_stream)
+        rstats = api.rgba_debug_render_stats(r.ctx, structs[-1], ws.data_ptr(), ws.numel(),
+                                             s.cuda_stream)
+        api.rgba_profile_read(r.ctx)
     api.rgba_profile_enable(r.ctx, False)
     stage_ms = {k: float(np.mean([p[k] for p in prof])) for k in api.STAGES}
     stage_ms["adam"] = float(np.mean(adam_ms))
+    if world > 1:
+        stage_ms["all_reduce"] = float(np.mean(ar_ms))
     launches_per_step = prof[-1]["launches"]
     # units of the compositing backward of the last profiled step: sum over pixels of
     # n_contrib, which rgba_step keeps in the workspace
@@ -392,30 +416,54 @@ def run_ours(args, rank, world, local_rank):
     fp32_peak_tflops = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
     roof = None
     if dominant == "render_bwd":
-        ach = units_bwd * BWD_FLOPS_PER_UNIT / (stage_ms["render_bwd"] / 1e3) / 1e12
+        sec = stage_ms["render_bwd"] / 1e3
+        ach = units_bwd * BWD_FLOPS_PER_UNIT / sec / 1e12
+        blends = rstats["bwd_pairs"]
+        # the same kernel against the work a per-pixel backward cannot avoid: every entry up to
+        # the pixel's last contributor evaluated (REJECT_FLOPS), the blended ones differentiated
+        useful = (units_bwd * REJECT_FLOPS + blends * (BWD_FLOPS_PER_UNIT - REJECT_FLOPS)) / sec / 1e12
+        # from the committed ncu capture: its warp instructions over the visits the counting
+        # instance found in the same (seeded) profiled step
+        ipv = traffic_for("render_bwd", "render.cu", "warp_instructions_per_visit")
         roof = {"bound": "alu", "kernel": "k_render_bwd", "achieved": ach,
                 "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops,
                 "traffic": traffic_for("render_bwd", "render.cu"),
                 "peak_source": f"FP32 lanes x 2 x {clock_mhz:.0f} MHz (recipe unit counts)",
-                "units": units_bwd, "flops_per_unit": BWD_FLOPS_PER_UNIT}
+                "units": units_bwd, "flops_per_unit": BWD_FLOPS_PER_UNIT,
+                "accounting": "units = (pixel, list entry up to the pixel's last contributor), "
+                              f"{BWD_FLOPS_PER_UNIT} FLOP each (the hot-path table's per-unit "
+                              "figure)",
+                "blend_pairs": blends, "blend_fraction_of_units": blends / max(1, units_bwd),
+                "visits": rstats["bwd_visits"],
+                "lanes_blending_per_visit": blends / max(1, rstats["bwd_visits"]),
+                "useful_achieved": useful, "useful_frac": useful / fp32_peak_tflops,
+                "useful_accounting": f"units x {REJECT_FLOPS} FLOP (evaluate and cut) + blend "
+                                     f"pairs x {BWD_FLOPS_PER_UNIT - REJECT_FLOPS} FLOP (the "
+                                     "gradient of a blending entry)",
+                "warp_instructions_per_visit": ipv}
     else:
         ach_ms = stage_ms[dominant]
         roof = {"bound": "alu", "kernel": dominant, "achieved": None, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": None, "traffic": None, "note": f"{ach_ms:.3f} ms"}
-    # HBM-bound stages, algorithmic bytes
+    # HBM-bound stages against their ALGORITHMIC bytes (the hot-path table's per-stage minimum,
+    # per (frame, Gaussian) of the batch): the preprocess reads the bases once and writes one
+    # 48-byte splat record per (frame, Gaussian); the projection/blend backward reads the 36-byte
+    # 2-D gradient of every (frame, Gaussian), reads the bases again (for dpsi) and writes dG0
+    # and ddG. What the kernels move beyond that (rectangles, tile slots, depth keys, the
+    # backward cache, zeroed gradient slots) is implementation traffic, reported beside it.
     R = dbs[0].total_rec
+    BN = FRAMES * N_GAUSS
     A, K = 9, K_BASES
-    # preprocess: bases once; per record the render record, rectangle, backward cache, zeroed
-    # 2-D gradient slots, tile slots and depth key
-    pre_bytes = 4 * N_GAUSS * (14 + K * A) + R * (48 + 8 + 48 + 48 + 32 + 4)
-    # Gaussian backward: bases for the weight gradients and both gradient arrays; per record the
-    # cache and the 2-D gradients; the weight partials
-    gbwd_bytes = 4 * N_GAUSS * (14 + 2 * K * A) + R * (48 + 48) + FRAMES * K * 4
+    pre_bytes = 4 * N_GAUSS * (14 + K * A) + 48 * BN
+    pre_impl = 4 * N_GAUSS * (14 + K * A) + R * (48 + 8 + 48 + 48 + 32 + 4)
+    gbwd_bytes = 4 * N_GAUSS * (14 + 2 * K * A) + 36 * BN
+    gbwd_impl = 4 * N_GAUSS * (14 + 2 * K * A) + R * (48 + 48) + FRAMES * K * 4
     stages = {k: {"ms": v} for k, v in stage_ms.items()}
-    stages["preprocess"]["GB/s"] = pre_bytes / (stage_ms["preprocess"] / 1e3) / 1e9
-    stages["preprocess"]["frac_hbm"] = stages["preprocess"]["GB/s"] / peaks["hbm_gbs"]
-    stages["gauss_bwd"]["GB/s"] = gbwd_bytes / (stage_ms["gauss_bwd"] / 1e3) / 1e9
-    stages["gauss_bwd"]["frac_hbm"] = stages["gauss_bwd"]["GB/s"] / peaks["hbm_gbs"]
+    for name, alg, impl in (("preprocess", pre_bytes, pre_impl), ("gauss_bwd", gbwd_bytes, gbwd_impl)):
+        sec = stage_ms[name] / 1e3
+        stages[name].update({"algorithmic_bytes": alg, "GB/s": alg / sec / 1e9,
+                             "frac_hbm": alg / sec / 1e9 / peaks["hbm_gbs"],
+                             "implementation_bytes": impl, "impl_GB/s": impl / sec / 1e9})
     adam_bytes = 7 * 4 * N_GAUSS * (14 + K * A)  # param, grad, m, v read; param, m, v written
     stages["adam"]["GB/s"] = adam_bytes / (stage_ms["adam"] / 1e3) / 1e9
     stages["adam"]["frac_hbm"] = stages["adam"]["GB/s"] / peaks["hbm_gbs"]

@@ -308,9 +308,27 @@ typedef struct {
     int32_t pad_;
 } rgba_profile;
 
+/* on: 0 off, 1 stage timing, 2 stage timing and compositing statistics (rgba_debug_render_stats;
+ * the two compositing kernels then run counting instances, built for 16x16 tiles with 64-entry
+ * staging only: other shapes count nothing). */
 int rgba_profile_enable(rgba_ctx_t ctx, int on);
 /* Waits for the recorded events, fills `out` (host) and resets the launch count. */
 int rgba_profile_read(rgba_ctx_t ctx, rgba_profile *out);
+
+/* Compositing statistics of the forward and backward that ran on this workspace since its last
+ * preprocess, counted while rgba_profile_enable(ctx, 2) was on (zero otherwise), for roofline
+ * accounting: how many list entries the kernels evaluated and how many of those blend.
+ * Synchronous; out: host. */
+typedef struct {
+    int64_t fwd_visits;  /* (list entry, 8x4 pixel block) visits at which the forward evaluated the
+                            entry (its box meets the block and some pixel passes the cutoffs) */
+    int64_t fwd_blends;  /* (pixel, entry) pairs the forward blended */
+    int64_t bwd_visits;  /* the same visits of the backward's reverse walk */
+    int64_t bwd_pairs;   /* (pixel, entry) pairs the backward took a gradient of (those that
+                            blended: equal to fwd_blends after one forward and one backward) */
+} rgba_render_stats;
+int rgba_debug_render_stats(rgba_ctx_t ctx, const rgba_batch *batch, const void *ws, size_t ws_bytes,
+                            rgba_render_stats *out, void *stream);
 
 /* Colour initialisation (Sec. 3.2 "Initialization", Eq. 3), synchronous. Renders the batch
  * (preprocess, bin/sort, front-to-back compositing) and, for every Gaussian, sums over all

@@ -27,7 +27,7 @@ EXPORTS = ("rgba_last_error", "rgba_create", "rgba_destroy", "rgba_workspace_siz
            "rgba_render_fwd", "rgba_render_bwd", "rgba_step", "rgba_step_async",
            "rgba_profile_enable", "rgba_profile_read", "rgba_render_fwd_noalloc", "rgba_adam",
            "rgba_step_adam_async", "rgba_step_capture", "rgba_step_replay", "rgba_graph_destroy",
-           "rgba_debug_keys", "rgba_color_init")
+           "rgba_debug_keys", "rgba_color_init", "rgba_debug_render_stats")
 RGBA_N_STAGES = 9
 STAGES = ("upload", "preprocess", "scan", "scatter", "sort", "render_fwd", "render_bwd",
           "gauss_bwd", "dpsi_reduce")
@@ -76,6 +76,11 @@ class RgbaAdamCfg(C.Structure):
 class RgbaAdamState(C.Structure):
     _fields_ = [("m_g0", C.c_void_p), ("v_g0", C.c_void_p), ("m_dg", C.c_void_p),
                 ("v_dg", C.c_void_p)]
+
+
+class RgbaRenderStats(C.Structure):
+    _fields_ = [("fwd_visits", C.c_int64), ("fwd_blends", C.c_int64), ("bwd_visits", C.c_int64),
+                ("bwd_pairs", C.c_int64)]
 
 
 class RgbaProfile(C.Structure):
@@ -129,6 +134,8 @@ def lib() -> C.CDLL:
             L.rgba_graph_destroy.restype = None
             L.rgba_debug_keys.argtypes = [P, Bp, P, sz, P, P, sz, C.POINTER(i64), P]
             L.rgba_debug_keys.restype = i32
+            L.rgba_debug_render_stats.argtypes = [P, Bp, P, sz, C.POINTER(RgbaRenderStats), P]
+            L.rgba_debug_render_stats.restype = i32
             L.rgba_render_fwd_noalloc.argtypes = [P, Bp, P, P, P, C.POINTER(RgbaStepOut), P]
             L.rgba_color_init.argtypes = [P, Bp, P, sz, P, C.c_float, C.POINTER(P),
                                           C.POINTER(RgbaStepOut), P]
@@ -228,8 +235,16 @@ def rgba_step_async(ctx, batch, ws, ws_bytes, target, loss_kind, img, stream) ->
                                        img, stream))
 
 
-def rgba_profile_enable(ctx, on: bool) -> int:
-    return check(lib().rgba_profile_enable(ctx, 1 if on else 0))
+def rgba_profile_enable(ctx, on) -> int:
+    """on: False / 0 off, True / 1 stage timing, 2 stage timing and compositing statistics."""
+    return check(lib().rgba_profile_enable(ctx, int(on)))
+
+
+def rgba_debug_render_stats(ctx, batch, ws, ws_bytes, stream) -> dict:
+    """The compositing statistics counted on this workspace (profiling mode 2)."""
+    out = RgbaRenderStats()
+    check(lib().rgba_debug_render_stats(ctx, C.byref(batch), ws, ws_bytes, C.byref(out), stream))
+    return {name: int(getattr(out, name)) for name, _ in RgbaRenderStats._fields_}
 
 
 def rgba_profile_read(ctx) -> dict:

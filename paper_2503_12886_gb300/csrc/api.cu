@@ -379,7 +379,8 @@ int do_bin_sort(rgba_ctx_t ctx, Call &k) {
 int do_render_fwd(rgba_ctx_t ctx, Call &k, float *img, float *T, int *n, const float *target, int loss_kind, float *dl,
                   const float *acc_target = nullptr) {
     StageScope sc(ctx, ST_FWD, k.s, 1);
-    cudaError_t e = launch_render_fwd(k.c, ctx->sms, k.p.L.smem_batch, img, T, n, target, loss_kind, dl, acc_target, k.s);
+    cudaError_t e = launch_render_fwd(k.c, ctx->sms, k.p.L.smem_batch, img, T, n, target, loss_kind, dl, acc_target,
+                                      ctx->stats, k.s);
     return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "render fwd");
 }
 
@@ -395,7 +396,7 @@ int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, cons
     cudaError_t e;
     {
         StageScope sc(ctx, ST_BWD, k.s, 1);
-        e = launch_render_bwd(k.c, ctx->sms, L.smem_batch, dl, T, n, k.s);
+        e = launch_render_bwd(k.c, ctx->sms, L.smem_batch, dl, T, n, ctx->stats, k.s);
         if (e != cudaSuccess) return cuda_fail(e, "render bwd");
     }
     for (const ModelInfo &m : k.p.models) {
@@ -476,6 +477,7 @@ int rgba_profile_enable(rgba_ctx_t ctx, int on) {
         }
     }
     ctx->prof = on != 0;
+    ctx->stats = on == 2;
     for (int i = 0; i < RGBA_N_STAGES; ++i) ctx->recorded[i] = false;
     return RGBA_OK;
 }
@@ -819,6 +821,24 @@ int rgba_debug_keys(rgba_ctx_t ctx, const rgba_batch *batch, const void *ws, siz
             return cuda_fail(e, "copy sorted lists");
     }
     if ((e = cudaStreamSynchronize(k.s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return RGBA_OK;
+}
+
+int rgba_debug_render_stats(rgba_ctx_t ctx, const rgba_batch *batch, const void *ws, size_t ws_bytes,
+                            rgba_render_stats *out, void *stream) {
+    if (!out) return fail(RGBA_ERR_INVALID_ARG, "out is NULL");
+    memset(out, 0, sizeof(*out));
+    Call k;
+    int rc = prologue(ctx, batch, const_cast<void *>(ws), ws_bytes, stream, k);
+    if (rc) return rc;
+    Counters h;
+    cudaError_t e = cudaMemcpyAsync(&h, k.ws + k.p.L.counters, sizeof(h), cudaMemcpyDeviceToHost, k.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(k.s);
+    if (e != cudaSuccess) return cuda_fail(e, "read counters");
+    out->fwd_visits = (int64_t)h.st_fwd_visits;
+    out->fwd_blends = (int64_t)h.st_fwd_blends;
+    out->bwd_visits = (int64_t)h.st_bwd_visits;
+    out->bwd_pairs = (int64_t)h.st_bwd_pairs;
     return RGBA_OK;
 }
 

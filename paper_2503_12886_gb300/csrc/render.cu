@@ -222,7 +222,9 @@ __device__ __forceinline__ void finish_pixel(const Ctx &c, const FrameInfo &f, i
 // ACC (colour initialisation, Eq. 3): every blended entry also adds its splatting weight w and
 // w times the pixel's colour in acc_target to the record's first four 2-D gradient slots
 // (one warp reduction and four atomics per entry and pixel block).
-template <int TW, int BATCH, bool ACC>
+// STATS (the counting instance): also count the visits that evaluate an entry and the
+// (pixel, entry) pairs that blend, into the compositing statistics of the counters.
+template <int TW, int BATCH, bool ACC, bool STATS = false>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *__restrict__ n_contrib,
              const float *__restrict__ target, int loss_kind, float *__restrict__ dl_dimg,
@@ -242,6 +244,8 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
     const unsigned n_work = c.cnt->n_work, n_blocks = n_work * NB;
     const unsigned n_items = n_blocks + ((unsigned)c.T - n_work);
     float loss_acc = 0.0f;
+    unsigned long long st_visits = 0;  // STATS: warp-uniform
+    unsigned st_blends = 0;            // STATS: this lane's
     while (true) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(&c.cnt->next_fwd, 1u);
@@ -313,6 +317,10 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
                     const bool live = !p.done && !skip(power, Q.y);
                     if (!__any_sync(0xffffffffu, live)) continue;  // the colour is not even read
                     const float w = composite(p, live, power, wc[j], pos0 + j);
+                    if (STATS) {
+                        ++st_visits;
+                        st_blends += w > 0.0f ? 1u : 0u;
+                    }
                     if (ACC && __any_sync(0xffffffffu, w > 0.0f)) {
                         const float v[4] = {w, w * I0, w * I1, w * I2};
                         const float mine = warp_reduce4(v, lane);
@@ -323,6 +331,13 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
         }
         if (p.inside)
             finish_pixel(c, f, b, px, py, p, img, T_final, n_contrib, target, loss_kind, dl_dimg, loss_acc);
+    }
+    if (STATS) {
+        for (int o = 16; o > 0; o >>= 1) st_blends += __shfl_xor_sync(0xffffffffu, st_blends, o);
+        if (lane == 0) {
+            atomicAdd(&c.cnt->st_fwd_visits, st_visits);
+            atomicAdd(&c.cnt->st_fwd_blends, (unsigned long long)st_blends);
+        }
     }
     // the last warp out puts the work counter back to zero for the next launch
     if (lane == 0 && atomicAdd(&c.cnt->done_fwd, 1u) == gridDim.x * kWarpsPerCta - 1) {
@@ -417,7 +432,9 @@ __device__ __forceinline__ void warp_reduce9(const float v[9], int lane, float &
     v8 = x;
 }
 
-template <int TW, int BATCH>
+// STATS (the counting instance): also count the visits that evaluate an entry and the
+// (pixel, entry) pairs that take a gradient, into the compositing statistics of the counters.
+template <int TW, int BATCH, bool STATS = false>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__ T_final,
              const int *__restrict__ n_contrib) {
@@ -433,6 +450,8 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
     float2 *wq = s_q[wid];
     unsigned *widx = s_idx[wid];
     const unsigned n_items = c.cnt->n_work * NB;
+    unsigned long long st_visits = 0;  // STATS: warp-uniform
+    unsigned st_pairs = 0;             // STATS: this lane's
     while (true) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(&c.cnt->next_bwd, 1u);
@@ -498,6 +517,10 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
                     const float power = power_of(dx, dy, A, Q);
                     const bool live = pos <= p.last && !skip(power, Q.y);
                     if (!__any_sync(0xffffffffu, live)) continue;  // the colour is not even read
+                    if (STATS) {
+                        ++st_visits;
+                        st_pairs += live ? 1u : 0u;
+                    }
                     float v[9];
                     accumulate(p, live, dx, dy, power, A, Q, wc[j], v);
                     float mine, v8;
@@ -507,6 +530,13 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
                     if (lane == 0) atomicAdd(dst + 8, v8);
                 }
             }
+        }
+    }
+    if (STATS) {
+        for (int o = 16; o > 0; o >>= 1) st_pairs += __shfl_xor_sync(0xffffffffu, st_pairs, o);
+        if (lane == 0) {
+            atomicAdd(&c.cnt->st_bwd_visits, st_visits);
+            atomicAdd(&c.cnt->st_bwd_pairs, (unsigned long long)st_pairs);
         }
     }
     // the last warp out puts the work counter back to zero for the next launch
@@ -532,18 +562,20 @@ int persistent_grid(K kernel, int sms_hint, int threads, int &cached) {
     return cached;
 }
 
-template <int TW, int BATCH, bool ACC>
+template <int TW, int BATCH, bool ACC, bool STATS = false>
 cudaError_t fwd_inst(const Ctx &c, int grid, float *img, float *T, int *n, const float *tg, int lk,
                      float *dl, const float *acc_tg, cudaStream_t s) {
     static int cached = 0;
-    const int g = persistent_grid(k_render_fwd<TW, BATCH, ACC>, grid, 32 * kWarpsPerCta, cached);
-    return launch_pdl(k_render_fwd<TW, BATCH, ACC>, dim3(g), dim3(32 * kWarpsPerCta), 0, s, c, img, T, n, tg, lk, dl,
-                      acc_tg);
+    const int g = persistent_grid(k_render_fwd<TW, BATCH, ACC, STATS>, grid, 32 * kWarpsPerCta, cached);
+    return launch_pdl(k_render_fwd<TW, BATCH, ACC, STATS>, dim3(g), dim3(32 * kWarpsPerCta), 0, s, c, img, T, n,
+                      tg, lk, dl, acc_tg);
 }
 
 template <bool ACC>
 cudaError_t fwd_dispatch(const Ctx &c, int grid, int sb, float *img, float *T, int *n, const float *tg,
-                         int lk, float *dl, const float *acc_tg, cudaStream_t s) {
+                         int lk, float *dl, const float *acc_tg, bool stats, cudaStream_t s) {
+    if (!ACC && stats && c.tw == 16 && sb == 64)
+        return fwd_inst<16, 64, false, true>(c, grid, img, T, n, tg, lk, dl, acc_tg, s);
     if (c.tw == 16) {
         if (sb == 64) return fwd_inst<16, 64, ACC>(c, grid, img, T, n, tg, lk, dl, acc_tg, s);
         if (sb == 128) return fwd_inst<16, 128, ACC>(c, grid, img, T, n, tg, lk, dl, acc_tg, s);
@@ -554,28 +586,29 @@ cudaError_t fwd_dispatch(const Ctx &c, int grid, int sb, float *img, float *T, i
     return fwd_inst<8, 256, ACC>(c, grid, img, T, n, tg, lk, dl, acc_tg, s);
 }
 
-template <int TW, int BATCH>
+template <int TW, int BATCH, bool STATS = false>
 cudaError_t bwd_inst(const Ctx &c, int grid, const float *dl, const float *T, const int *n,
                      cudaStream_t s) {
     static int cached = 0;
-    const int g = persistent_grid(k_render_bwd<TW, BATCH>, grid, 32 * kWarpsPerCta, cached);
-    return launch_pdl(k_render_bwd<TW, BATCH>, dim3(g), dim3(32 * kWarpsPerCta), 0, s, c, dl, T, n);
+    const int g = persistent_grid(k_render_bwd<TW, BATCH, STATS>, grid, 32 * kWarpsPerCta, cached);
+    return launch_pdl(k_render_bwd<TW, BATCH, STATS>, dim3(g), dim3(32 * kWarpsPerCta), 0, s, c, dl, T, n);
 }
 
 }  // namespace
 
 cudaError_t launch_render_fwd(const Ctx &c, int grid, int smem_batch, float *img, float *T_final,
                               int *n_contrib, const float *target, int loss_kind,
-                              float *dl_dimg, const float *acc_target, cudaStream_t s) {
+                              float *dl_dimg, const float *acc_target, bool stats, cudaStream_t s) {
     if (acc_target)
         return fwd_dispatch<true>(c, grid, smem_batch, img, T_final, n_contrib, target, loss_kind, dl_dimg,
-                                  acc_target, s);
+                                  acc_target, false, s);
     return fwd_dispatch<false>(c, grid, smem_batch, img, T_final, n_contrib, target, loss_kind, dl_dimg,
-                               nullptr, s);
+                               nullptr, stats, s);
 }
 
 cudaError_t launch_render_bwd(const Ctx &c, int grid, int smem_batch, const float *dl_dimg,
-                              const float *T_final, const int *n_contrib, cudaStream_t s) {
+                              const float *T_final, const int *n_contrib, bool stats, cudaStream_t s) {
+    if (stats && c.tw == 16 && smem_batch == 64) return bwd_inst<16, 64, true>(c, grid, dl_dimg, T_final, n_contrib, s);
     if (c.tw == 16) {
         if (smem_batch == 64) return bwd_inst<16, 64>(c, grid, dl_dimg, T_final, n_contrib, s);
         if (smem_batch == 128) return bwd_inst<16, 128>(c, grid, dl_dimg, T_final, n_contrib, s);

@@ -11,6 +11,7 @@ struct rgba_ctx {
     int sms;
     rgba_counters *pinned;  // host-pinned landing spot of rgba_step's single read
     bool prof;
+    bool stats;             // compositing kernels run their counting instances
     bool recorded[RGBA_N_STAGES];
     cudaEvent_t ev0[RGBA_N_STAGES], ev1[RGBA_N_STAGES];
     int launches;
@@ -81,7 +82,12 @@ struct Counters {
     unsigned done_sort;   // CTAs / warps of each persistent kernel that ran out of work: the
     unsigned done_fwd;    // last one to leave puts its kernel's counters back to zero, so
     unsigned done_bwd;    // every launch starts from zero without a memset
-    unsigned pad_[6];
+    // compositing statistics, counted only by the counting instances of the compositing kernels
+    // (rgba_profile_enable(ctx, 2)); zeroed with the rest at the start of every preprocess
+    unsigned long long st_fwd_visits;  // (entry, pixel block) visits the forward evaluated
+    unsigned long long st_fwd_blends;  // (pixel, entry) pairs the forward blended
+    unsigned long long st_bwd_visits;  // (entry, pixel block) visits the backward evaluated
+    unsigned long long st_bwd_pairs;   // (pixel, entry) pairs the backward took a gradient of
 };
 static_assert(sizeof(Counters) <= 256, "counters fit in one 256-byte block");
 
@@ -189,13 +195,15 @@ cudaError_t launch_scan(const Ctx &c, cudaStream_t s);
 size_t scan_aux_bytes(long long T);
 cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s);
 cudaError_t launch_tile_sort(const Ctx &c, int sms, cudaStream_t s);
+// stats: run the counting instance (16 x 16 tiles, 64-entry staging only), which adds the
+// compositing statistics of Counters
 cudaError_t launch_render_fwd(const Ctx &c, int grid, int smem_batch, float *img, float *T_final,
                               int *n_contrib, const float *target, int loss_kind,
-                              float *dl_dimg, const float *acc_target, cudaStream_t s);
+                              float *dl_dimg, const float *acc_target, bool stats, cudaStream_t s);
 cudaError_t launch_color_finish(const Ctx &c, int max_n, float delta, const uint8_t *const *done_host,
                                 int n_models, cudaStream_t s);
 cudaError_t launch_render_bwd(const Ctx &c, int grid, int smem_batch, const float *dl_dimg,
-                              const float *T_final, const int *n_contrib, cudaStream_t s);
+                              const float *T_final, const int *n_contrib, bool stats, cudaStream_t s);
 // One Adam update (Kingma & Ba, ICLR 2015) of parameter p with gradient g:
 //   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,  p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
 // with ibc = 1 / (1 - b^t). The separate and the fused update both call this, so they agree

@@ -46,6 +46,9 @@ def main():
     p.add_argument("--smem-batch", type=int, default=64)
     p.add_argument("--train", type=int, default=0)
     p.add_argument("--adam", default="none", choices=("none", "separate", "fused"))
+    p.add_argument("--stats", action="store_true",
+                   help="after the profiled steps, one more step with the compositing statistics "
+                        "counted (profiling mode 2), printed with the stage times")
     a = p.parse_args()
     tw, th = (int(x) for x in a.tile.split("x"))
     batch = make(a.workload)
@@ -88,9 +91,17 @@ def main():
     prof = api.rgba_profile_read(r.ctx)
     if adam_ms is not None:
         prof["adam"] = adam_ms
+    stats = None
+    if a.stats:  # the same step state as the last profiled step (no update in between)
+        api.rgba_profile_enable(r.ctx, 2)
+        r.step(db, tg, api.RGBA_LOSS_L1, img)
+        stats = api.rgba_debug_render_stats(r.ctx, db.struct(), ws.data_ptr(), ws.numel(),
+                                            torch.cuda.current_stream().cuda_stream)
+        api.rgba_profile_enable(r.ctx, 0)
     r.close()
     print(json.dumps({"workload": a.workload, "frames": db.n_frames, "pairs": out.pairs,
-                      "loss": out.loss, "step_ms": [1e3 * w for w in wall], "stages_ms": prof}))
+                      "loss": out.loss, "step_ms": [1e3 * w for w in wall], "stages_ms": prof,
+                      "render_stats": stats}))
 
 
 if __name__ == "__main__":

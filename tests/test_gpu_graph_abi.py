@@ -108,3 +108,39 @@ def test_debug_keys_equal_oracle_lists(renderer):
         t = ts[bases[b]: bases[b] + nt + 1]
         np.testing.assert_array_equal(t - t[0], o.tile_start.astype(np.int64))
         np.testing.assert_array_equal(srt[t[0]: t[-1]], o.lst.astype(np.int64))
+
+
+def test_render_stats_count_blends_without_changing_results(renderer):
+    """Profiling mode 2 runs counting instances of the two compositing kernels: their images
+    equal the plain kernels' bit for bit and their loss and gradients up to the order of the
+    atomic sums (same arithmetic, only counters added), the backward takes a gradient of exactly the (pixel, entry) pairs the forward
+    blended, and that count lies between the pixels with a contributor and the sum of the
+    contributor counts (the entries scanned up to each pixel's last blend)."""
+    batch = synth.workload_batched(n=20_000, k=16, frames=3, res=256)
+    db = DeviceBatch(batch, "cuda:0")
+    tg = db.pack_images(synth.make_targets(batch, 12))
+    ws = renderer.ensure_workspace(db)
+    lay = renderer.layout(db)
+    s = stream_ptr()
+    outs = []
+    for mode in (0, 2):
+        api.rgba_profile_enable(renderer.ctx, mode)
+        img = torch.empty(3 * db.total_pix, device="cuda:0")
+        rc, out = api.rgba_step(renderer.ctx, db.struct(), ws.data_ptr(), ws.numel(), tg.data_ptr(),
+                                api.RGBA_LOSS_L1, img.data_ptr(), s)
+        assert rc == api.RGBA_OK
+        st = api.rgba_debug_render_stats(renderer.ctx, db.struct(), ws.data_ptr(), ws.numel(), s)
+        n = ws[lay.pix_n: lay.pix_n + 4 * db.total_pix].view(torch.int32).clone()
+        outs.append((img, out.loss, db.models[0].grad_g0.clone(), db.models[0].grad_dg.clone(),
+                     db.grad_psi.clone(), n, st))
+    api.rgba_profile_enable(renderer.ctx, 0)
+    (i0, l0, g0, d0, p0, n0, s0), (i2, l2, g2, d2, p2, n2, s2) = outs
+    assert s0 == {"fwd_visits": 0, "fwd_blends": 0, "bwd_visits": 0, "bwd_pairs": 0}
+    assert torch.equal(i0, i2) and torch.equal(n0, n2)
+    assert abs(l0 - l2) <= 1e-6 * l0  # fp32 per-CTA loss partials are added by atomics, in any order
+    # the compositing backward's atomics may sum in another order: equal up to that
+    for a, b in ((g0, g2), (d0, d2), (p0, p2)):
+        assert float((a - b).abs().max()) <= 1e-5 * float(a.abs().max())
+    assert s2["fwd_blends"] == s2["bwd_pairs"] > 0
+    assert s2["fwd_visits"] > 0 and s2["bwd_visits"] > 0
+    assert int((n2 > 0).sum()) <= s2["fwd_blends"] <= int(n2.to(torch.int64).sum())
