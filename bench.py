@@ -412,34 +412,42 @@ def run_ours(args, rank, world, local_rank):
     units_bwd = int(ws[lay.pix_n: lay.pix_n + 4 * P].view(torch.int32).sum(dtype=torch.int64))
     peaks, peak_kind = load_peaks()
     dominant = max(stage_ms, key=lambda k: stage_ms[k])
+    stage_ms = {k: v for k, v in stage_ms.items() if v >= 0}  # stages this step did not run
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak_tflops = SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
     roof = None
-    if dominant == "render_bwd":
-        sec = stage_ms["render_bwd"] / 1e3
-        ach = units_bwd * BWD_FLOPS_PER_UNIT / sec / 1e12
+    # the compositing kernel of the step: the one-kernel forward + loss + backward (stage
+    # render_step), or the separate backward when the step ran the two kernels
+    comp = "render_step" if stage_ms.get("render_step", -1.0) > 0 else "render_bwd"
+    if dominant in ("render_step", "render_bwd"):
+        sec = stage_ms[comp] / 1e3
+        per_unit = BWD_FLOPS_PER_UNIT + (FWD_FLOPS_PER_UNIT if comp == "render_step" else 0)
+        ach = units_bwd * per_unit / sec / 1e12
         blends = rstats["bwd_pairs"]
-        # the same kernel against the work a per-pixel backward cannot avoid: every entry up to
-        # the pixel's last contributor evaluated (REJECT_FLOPS), the blended ones differentiated
-        useful = (units_bwd * REJECT_FLOPS + blends * (BWD_FLOPS_PER_UNIT - REJECT_FLOPS)) / sec / 1e12
+        # the same kernel against the work a per-pixel compositing cannot avoid: every entry up
+        # to the pixel's last contributor evaluated (REJECT_FLOPS, in each direction), the
+        # blended ones composited and differentiated
+        rej = REJECT_FLOPS * (2 if comp == "render_step" else 1)
+        useful = (units_bwd * rej + blends * (per_unit - rej)) / sec / 1e12
+        kname = "k_render_step" if comp == "render_step" else "k_render_bwd"
         # from the committed ncu capture: its warp instructions over the visits the counting
-        # instance found in the same (seeded) profiled step
-        ipv = traffic_for("render_bwd", "render.cu", "warp_instructions_per_visit")
-        roof = {"bound": "alu", "kernel": "k_render_bwd", "achieved": ach,
+        # instances found in the same (seeded) profiled step
+        ipv = traffic_for(comp, "render.cu", "warp_instructions_per_visit")
+        roof = {"bound": "alu", "kernel": kname, "achieved": ach,
                 "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops,
-                "traffic": traffic_for("render_bwd", "render.cu"),
+                "traffic": traffic_for(comp, "render.cu"),
                 "peak_source": f"FP32 lanes x 2 x {clock_mhz:.0f} MHz (recipe unit counts)",
-                "units": units_bwd, "flops_per_unit": BWD_FLOPS_PER_UNIT,
+                "units": units_bwd, "flops_per_unit": per_unit,
                 "accounting": "units = (pixel, list entry up to the pixel's last contributor), "
-                              f"{BWD_FLOPS_PER_UNIT} FLOP each (the hot-path table's per-unit "
-                              "figure)",
+                              f"{per_unit} FLOP each (the hot-path table's per-unit figures: "
+                              f"{FWD_FLOPS_PER_UNIT} forward, {BWD_FLOPS_PER_UNIT} backward)",
                 "blend_pairs": blends, "blend_fraction_of_units": blends / max(1, units_bwd),
-                "visits": rstats["bwd_visits"],
+                "visits_fwd": rstats["fwd_visits"], "visits_bwd": rstats["bwd_visits"],
                 "lanes_blending_per_visit": blends / max(1, rstats["bwd_visits"]),
                 "useful_achieved": useful, "useful_frac": useful / fp32_peak_tflops,
-                "useful_accounting": f"units x {REJECT_FLOPS} FLOP (evaluate and cut) + blend "
-                                     f"pairs x {BWD_FLOPS_PER_UNIT - REJECT_FLOPS} FLOP (the "
-                                     "gradient of a blending entry)",
+                "useful_accounting": f"units x {rej} FLOP (evaluate and cut) + blend pairs x "
+                                     f"{per_unit - rej} FLOP (composite and differentiate a "
+                                     "blending entry)",
                 "warp_instructions_per_visit": ipv}
     else:
         ach_ms = stage_ms[dominant]

@@ -146,7 +146,12 @@ typedef struct {
     size_t rects;        /* uint16[R][4]: tile rectangle x0, y0, x1, y1 (half-open) */
     size_t tile_start;   /* uint32[T + 1]: start of each (frame, tile) list */
     size_t sorted;       /* uint32[capacity]: Gaussian index per list entry */
-    size_t grad2d;       /* float[R][12]: dL/d(u, v, conic a, b, c, opacity, r, g, b) */
+    size_t grad2d;       /* float[R][12]: per (frame, Gaussian), the compositing backward's sums
+                            over the pixels that blend it: S1..S5, S0 of g (dx, dy, dx^2, dx dy,
+                            dy^2, 1), g = dL/dpower at the pixel, (dx, dy) = pixel centre - mean,
+                            then dL/d(r, g, b). The 2-D gradients follow with the record's conic
+                            (a, b, c) and opacity o: dL/du = a S1 + b S2, dL/dv = b S1 + c S2,
+                            dL/d(a, b, c) = (-S3/2, -S4, -S5/2), dL/do = S0 / o */
     size_t pix_T;        /* float[P]: T_final of rgba_step (P = total pixels of the batch) */
     size_t pix_n;        /* int32[P]: n_contrib of rgba_step */
     size_t pix_dl;       /* float[3P]: dL/dimg of rgba_step's fused loss */
@@ -206,7 +211,8 @@ int rgba_render_fwd(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
 /* Back-propagation of dL/dimg (same layout as img) through compositing, projection,
  * activations and the blend. Uses only T_final and n_contrib from the forward (recomputes the
  * compositing in reverse). Writes models[m].grad_g0 / grad_dg and batch->grad_psi (those that
- * are non-NULL); the per-(frame, Gaussian) 2-D gradients stay in the workspace (grad2d).
+ * are non-NULL); the per-(frame, Gaussian) sums the 2-D gradients follow from stay in the
+ * workspace (grad2d, see rgba_ws_layout).
  * grad_blended (device, 16-byte aligned, or NULL): also the gradient with respect to each
  * frame's blended Gaussians G^psi_b of Eq. 1, before the blend's adjoint reduces it over the
  * frames: frame b's [14][n_pad] block at float offset 14 * (sum of n_pad over frames before b),

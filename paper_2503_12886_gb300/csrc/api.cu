@@ -384,21 +384,12 @@ int do_render_fwd(rgba_ctx_t ctx, Call &k, float *img, float *T, int *n, const f
     return e == cudaSuccess ? RGBA_OK : cuda_fail(e, "render fwd");
 }
 
-// g2_zeroed: the preprocess of the same call zeroed the 2-D gradients (the fused step); a
-// standalone backward clears them itself.
-int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, const int *n, bool g2_zeroed = false,
-                  const FusedAdam *fa = nullptr) {
+// The projection and blend backward after the compositing backward: zeroes the gradients of
+// models no frame renders, then the Gaussian backward (optionally with the fused Adam update)
+// and the weight-gradient reduction.
+int do_gauss_bwd(rgba_ctx_t ctx, Call &k, const FusedAdam *fa) {
     int rc;
-    const Layout &L = k.p.L;
-    if (!g2_zeroed &&
-        (rc = memset_async(k.ws + L.grad2d, sizeof(float) * kG2Floats * (size_t)L.R, k.s, "memset grad2d")))
-        return rc;
     cudaError_t e;
-    {
-        StageScope sc(ctx, ST_BWD, k.s, 1);
-        e = launch_render_bwd(k.c, ctx->sms, L.smem_batch, dl, T, n, ctx->stats, k.s);
-        if (e != cudaSuccess) return cuda_fail(e, "render bwd");
-    }
     for (const ModelInfo &m : k.p.models) {
         if (m.nb) continue;  // no frame renders it: zero gradient
         if (m.gg0 && (rc = memset_async(m.gg0, sizeof(float) * kNch * (size_t)m.n_pad, k.s, "memset grad_g0"))) return rc;
@@ -407,8 +398,12 @@ int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, cons
     {
         StageScope sc(ctx, ST_GBWD, k.s, 1);
         int max_ka = 0;
-        for (const ModelInfo &m : k.p.models) max_ka = std::max(max_ka, m.k * m.A);
-        if ((e = launch_gauss_bwd(k.c, k.p.max_chunks, k.p.max_k, max_ka, fa, k.s)) != cudaSuccess)
+        bool any_bound = false;
+        for (const ModelInfo &m : k.p.models) {
+            max_ka = std::max(max_ka, m.k * m.A);
+            any_bound = any_bound || m.n_faces > 0;
+        }
+        if ((e = launch_gauss_bwd(k.c, k.p.max_chunks, k.p.max_k, max_ka, fa, any_bound, k.s)) != cudaSuccess)
             return cuda_fail(e, "gauss bwd");
     }
     if (k.c.grad_psi) {
@@ -421,6 +416,33 @@ int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, cons
             return cuda_fail(e, "step advance");
     }
     return RGBA_OK;
+}
+
+// g2_zeroed: the preprocess of the same call zeroed the 2-D gradients (the fused step); a
+// standalone backward clears them itself.
+int do_render_bwd(rgba_ctx_t ctx, Call &k, const float *dl, const float *T, const int *n, bool g2_zeroed = false,
+                  const FusedAdam *fa = nullptr) {
+    int rc;
+    const Layout &L = k.p.L;
+    if (!g2_zeroed &&
+        (rc = memset_async(k.ws + L.grad2d, sizeof(float) * kG2Floats * (size_t)L.R, k.s, "memset grad2d")))
+        return rc;
+    {
+        StageScope sc(ctx, ST_BWD, k.s, 1);
+        cudaError_t e = launch_render_bwd(k.c, ctx->sms, L.smem_batch, dl, T, n, ctx->stats, k.s);
+        if (e != cudaSuccess) return cuda_fail(e, "render bwd");
+    }
+    return do_gauss_bwd(ctx, k, fa);
+}
+
+// The training step's compositing and backward: the forward with the fused loss (dL/dimg into
+// the workspace), the compositing backward, then the projection and blend backward.
+int do_render_step(rgba_ctx_t ctx, Call &k, float *img, float *T, int *n, const float *target, int loss_kind,
+                   const FusedAdam *fa = nullptr) {
+    float *dl = reinterpret_cast<float *>(k.ws + k.p.L.pix_dl);
+    int rc = do_render_fwd(ctx, k, img, T, n, target, loss_kind, dl);
+    if (rc) return rc;
+    return do_render_bwd(ctx, k, dl, T, n, true, fa);
 }
 
 }  // namespace
@@ -624,11 +646,9 @@ int rgba_step_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
     float *im = img ? img : reinterpret_cast<float *>(k.ws + L.pix_img);
     float *T = reinterpret_cast<float *>(k.ws + L.pix_T);
     int *n = reinterpret_cast<int *>(k.ws + L.pix_n);
-    float *dl = reinterpret_cast<float *>(k.ws + L.pix_dl);
     if ((rc = do_preprocess(ctx, k))) return rc;
     if ((rc = do_bin_sort(ctx, k))) return rc;
-    if ((rc = do_render_fwd(ctx, k, im, T, n, target, loss_kind, dl))) return rc;
-    return do_render_bwd(ctx, k, dl, T, n, true);
+    return do_render_step(ctx, k, im, T, n, target, loss_kind);
 }
 
 int rgba_step_adam_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws_bytes, const float *target,
@@ -666,11 +686,9 @@ int rgba_step_adam_async(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size
     float *im = img ? img : reinterpret_cast<float *>(k.ws + L.pix_img);
     float *T = reinterpret_cast<float *>(k.ws + L.pix_T);
     int *n = reinterpret_cast<int *>(k.ws + L.pix_n);
-    float *dl = reinterpret_cast<float *>(k.ws + L.pix_dl);
     if ((rc = do_preprocess(ctx, k))) return rc;
     if ((rc = do_bin_sort(ctx, k))) return rc;
-    if ((rc = do_render_fwd(ctx, k, im, T, n, target, loss_kind, dl))) return rc;
-    return do_render_bwd(ctx, k, dl, T, n, true, &fa);
+    return do_render_step(ctx, k, im, T, n, target, loss_kind, &fa);
 }
 
 }  // extern "C"

@@ -2,9 +2,10 @@
 //
 //   k_gauss_bwd  one CTA per 32 Gaussians of one model, lane = Gaussian, frames 16 at a time:
 //                first, per (frame, Gaussian), the 2-D gradients dL/d(u, v, conic, opacity,
-//                colour) from compositing -> dL/dG_b over the 14 channels (chain rule through
-//                conic inversion, J W Sigma W^T J^T, R diag(s^2) R^T, quaternion
-//                normalisation, exp and sigmoid) into shared memory; then the adjoint of Eq. 1:
+//                colour) from the compositing backward's sums -> dL/dG_b over the 14 channels
+//                (chain rule through conic inversion, J W Sigma W^T J^T, R diag(s^2) R^T,
+//                quaternion normalisation, exp and sigmoid) into shared memory; then the
+//                adjoint of Eq. 1:
 //                dG0[ch][i]    += sum_b dG_b[ch][i]
 //                ddG[k][a][i]  += sum_b psi_b[k] dG_b[ch_a][i]
 //                dpsi_b[k]     partial = sum_{a, i in chunk} dG_k[a][i] dG_b[ch_a][i]
@@ -28,12 +29,15 @@ struct Fwd {
     float A, B, C, det;
 };
 
-// Rt: [12] = TBN matrix row-major (columns T, B, N), then t (the identity and zero for unbound
-// models); the Gaussian is mapped from tangent space by x = R x_T + t, covariance R Sigma R^T.
+// BOUND: Rt [12] = TBN matrix row-major (columns T, B, N), then t (the identity and zero for an
+// unbound model of a batch that also has bound ones); the Gaussian is mapped from tangent space
+// by x = R x_T + t, covariance R Sigma R^T. !BOUND: no mapping (Rt is not read).
+template <bool BOUND>
 __device__ __forceinline__ void recompute(const float v[10], const float *V, int W, int H, const float *Rt, Fwd &f) {
     float xm[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) xm[c] = Rt[3 * c] * v[0] + Rt[3 * c + 1] * v[1] + Rt[3 * c + 2] * v[2] + Rt[9 + c];
+    for (int c = 0; c < 3; ++c)
+        xm[c] = BOUND ? Rt[3 * c] * v[0] + Rt[3 * c + 1] * v[1] + Rt[3 * c + 2] * v[2] + Rt[9 + c] : v[c];
 #pragma unroll
     for (int j = 0; j < 3; ++j) f.p[j] = V[4 * j] * xm[0] + V[4 * j + 1] * xm[1] + V[4 * j + 2] * xm[2] + V[4 * j + 3];
 #pragma unroll
@@ -61,7 +65,7 @@ __device__ __forceinline__ void recompute(const float v[10], const float *V, int
             for (int m = 0; m < 3; ++m) a += f.R[i][m] * f.s[m] * f.s[m] * f.R[j][m];
             Sg[i][j] = a;
         }
-    {
+    if (BOUND) {
         float P[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -113,17 +117,25 @@ __device__ __forceinline__ void recompute(const float v[10], const float *V, int
     f.det = f.A * f.C - f.B * f.B;
 }
 
-// dG[14]: gradient w.r.t. the blended channels of one (frame, Gaussian).
+// dG[14]: gradient w.r.t. the blended channels of one (frame, Gaussian). g2: the compositing
+// backward's sums over the pixels that blend the Gaussian, S = (S1, S2, S3, S4, S5, S0) of
+// g (dx, dy, dx^2, dx dy, dy^2, 1) with g = dL/dpower and (dx, dy) = pixel centre - mean, then
+// dL/d(r, g, b). As power = -(a dx^2 + c dy^2) / 2 - b dx dy and alpha = o e^power:
+// dL/du = a S1 + b S2, dL/dv = b S1 + c S2, dL/d(a, b, c) = (-S3 / 2, -S4, -S5 / 2) and
+// dL/do = S0 / o, with the conic (a, b, c) = Sigma'^-1 recomputed here.
+template <bool BOUND>
 __device__ __forceinline__ void chain(const float v[10], float op, const float *V, int W, int H,
                                       const float *Rt, const float g2[9], float dG[kNch]) {
     Fwd f;
-    recompute(v, V, W, H, Rt, f);
-    const float du = g2[0], dv = g2[1], dca = g2[2], dcb = g2[3], dcc = g2[4];
-    dG[10] = g2[5] * op * (1.f - op);
+    recompute<BOUND>(v, V, W, H, Rt, f);
+    const float A = f.A, B = f.B, C = f.C, D = f.det, iD = __frcp_rn(D), iD2 = iD * iD;
+    const float ca = C * iD, cb = -B * iD, cc = A * iD;
+    const float du = ca * g2[0] + cb * g2[1], dv = cb * g2[0] + cc * g2[1];
+    const float dca = -0.5f * g2[2], dcb = -g2[3], dcc = -0.5f * g2[4];
+    dG[10] = g2[5] * (1.f - op);  // dL/do times the sigmoid's o (1 - o)
     dG[11] = g2[6];
     dG[12] = g2[7];
     dG[13] = g2[8];
-    const float A = f.A, B = f.B, C = f.C, D = f.det, iD = __frcp_rn(D), iD2 = iD * iD;
     const float dA = dca * (-C * C * iD2) + dcb * (B * C * iD2) + dcc * (iD - A * C * iD2);
     const float dC = dca * (iD - A * C * iD2) + dcb * (A * B * iD2) + dcc * (-A * A * iD2);
     const float dB = dca * (2.f * B * C * iD2) + dcb * (-iD - 2.f * B * B * iD2) + dcc * (2.f * A * B * iD2);
@@ -154,7 +166,7 @@ __device__ __forceinline__ void chain(const float v[10], float op, const float *
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) dS[r][c] = tmp[r][0] * V[c] + tmp[r][1] * V[4 + c] + tmp[r][2] * V[8 + c];
-    {  // Sigma = R Sigma_T R^T: dSigma_T = R^T dSigma R
+    if (BOUND) {  // Sigma = R Sigma_T R^T: dSigma_T = R^T dSigma R
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -216,7 +228,7 @@ __device__ __forceinline__ void chain(const float v[10], float op, const float *
     for (int c = 0; c < 3; ++c) dxw[c] = V[c] * dp0 + V[4 + c] * dp1 + V[8 + c] * dp2;
 #pragma unroll
     for (int c = 0; c < 3; ++c)  // x = R x_T + t: dx_T = R^T dx
-        dG[c] = Rt[c] * dxw[0] + Rt[3 + c] * dxw[1] + Rt[6 + c] * dxw[2];
+        dG[c] = BOUND ? Rt[c] * dxw[0] + Rt[3 + c] * dxw[1] + Rt[6 + c] * dxw[2] : dxw[c];
 }
 
 // TBN matrix and barycentric point of Gaussian i in one frame (the same definitions as the
@@ -320,7 +332,9 @@ struct NoAdam {
 template <bool ADAM>
 using AdamArg = typename std::conditional<ADAM, FusedAdam, NoAdam>::type;
 
-template <bool ADAM>
+// BOUND: some model of the batch has a tangent-space binding (the chain rule then maps through
+// each bound Gaussian's TBN frame); otherwise that mapping is compiled out.
+template <bool ADAM, bool BOUND>
 __global__ void __launch_bounds__(kBwdThreads, 3)
 k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
     extern __shared__ float smem[];
@@ -407,9 +421,13 @@ k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
                 if (live[0] && c2[0].w != 0.f) {  // item u sits in slot 0 (a rolled loop keeps the code small)
                     const float v[10] = {c0[0].x, c0[0].y, c0[0].z, c0[0].w, c1[0].x, c1[0].y, c1[0].z, c1[0].w, c2[0].x, c2[0].y};
                     const float g2[9] = {ga[0].x, ga[0].y, ga[0].z, ga[0].w, gb[0].x, gb[0].y, gb[0].z, gb[0].w, gc[0].x};
-                    float Rt[12] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f};
-                    if (m.n_faces == 0 || tbn_fast(m, s_verts[fl], i0 + li, Rt))
-                        chain(v, c2[0].z, s_fp[fl], s_wh[fl][0], s_wh[fl][1], Rt, g2, dG);
+                    if (BOUND) {
+                        float Rt[12] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f};
+                        if (m.n_faces == 0 || tbn_fast(m, s_verts[fl], i0 + li, Rt))
+                            chain<true>(v, c2[0].z, s_fp[fl], s_wh[fl][0], s_wh[fl][1], Rt, g2, dG);
+                    } else {
+                        chain<false>(v, c2[0].z, s_fp[fl], s_wh[fl][0], s_wh[fl][1], nullptr, g2, dG);
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < kNch; ++q) s_dG[(fl * kNch + q) * kBwdChunk + li] = dG[q];
@@ -576,7 +594,7 @@ __global__ void __launch_bounds__(kDpsiThreads) k_dpsi_reduce(Ctx c) {
 }  // namespace
 
 namespace {
-template <bool ADAM>
+template <bool ADAM, bool BOUND>
 cudaError_t gauss_bwd_inst(const Ctx &c, int max_chunks, int max_k, int max_ka, const AdamArg<ADAM> &fa,
                            cudaStream_t s) {
     auto bytes = [](int k, int ka) { return (kFG2 * kNch * kBwdChunk + kFG2 * k + ka * kBwdChunk) * (int)sizeof(float); };
@@ -587,22 +605,26 @@ cudaError_t gauss_bwd_inst(const Ctx &c, int max_chunks, int max_k, int max_ka, 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (attr_device != dev) {
-        e = cudaFuncSetAttribute(k_gauss_bwd<ADAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_gauss_bwd<ADAM, BOUND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  bytes(RGBA_MAX_K, RGBA_MAX_K * 13));
         if (e != cudaSuccess) return e;
         attr_device = dev;
     }
     dim3 g2(max_chunks, c.M);
-    return launch_pdl(k_gauss_bwd<ADAM>, g2, dim3(kBwdThreads), (size_t)bytes(max_k, max_ka), s, c, max_k, fa);
+    return launch_pdl(k_gauss_bwd<ADAM, BOUND>, g2, dim3(kBwdThreads), (size_t)bytes(max_k, max_ka), s, c, max_k,
+                      fa);
 }
 }  // namespace
 
 cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_k, int max_ka, const FusedAdam *fa,
-                             cudaStream_t s) {
+                             bool any_bound, cudaStream_t s) {
     if (c.M == 0 || max_chunks == 0) return cudaSuccess;
-    if (fa) return gauss_bwd_inst<true>(c, max_chunks, max_k, max_ka, *fa, s);
+    if (fa)
+        return any_bound ? gauss_bwd_inst<true, true>(c, max_chunks, max_k, max_ka, *fa, s)
+                         : gauss_bwd_inst<true, false>(c, max_chunks, max_k, max_ka, *fa, s);
     const NoAdam none{};
-    return gauss_bwd_inst<false>(c, max_chunks, max_k, max_ka, none, s);
+    return any_bound ? gauss_bwd_inst<false, true>(c, max_chunks, max_k, max_ka, none, s)
+                     : gauss_bwd_inst<false, false>(c, max_chunks, max_k, max_ka, none, s);
 }
 
 cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s) {

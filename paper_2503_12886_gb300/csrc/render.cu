@@ -17,7 +17,7 @@
 //   stop, without blending, once T (1 - alpha) < 1e-4
 // The backward recomputes each alpha with the same instruction sequence as the forward, walks
 // the list backwards from the stored contributor count, and recovers T by division by
-// (1 - alpha). Per-Gaussian gradients are reduced across the warp (reduce-scatter) and reach
+// (1 - alpha). Per-Gaussian gradient sums are reduced across the warp (reduce-scatter) and reach
 // global memory as one atomic per Gaussian, pixel block and component.
 #include "rgba_internal.cuh"
 
@@ -183,11 +183,12 @@ __device__ __forceinline__ float warp_reduce4(const float v[4], int lane) {
 }
 
 // Writes one finished pixel (colour over the background, T, contributor count) and, with a
-// target, its loss term and dL/dpixel.
+// target, adds its loss term and returns dL/dpixel in g (also stored to dl_dimg unless that is
+// NULL: the fused training-step kernel keeps it in registers).
 __device__ __forceinline__ void finish_pixel(const Ctx &c, const FrameInfo &f, int b, int px, int py,
                                              const PixF &p, float *img, float *T_final, int *n_contrib,
                                              const float *target, int loss_kind, float *dl_dimg,
-                                             float &loss_acc) {
+                                             float &loss_acc, float g[3]) {
     const float *bg = c.fparams + (size_t)b * RGBA_FP_STRIDE + 17;
     const long long hw = (long long)f.W * f.H;
     const long long pix = (long long)py * f.W + px;
@@ -198,160 +199,113 @@ __device__ __forceinline__ void finish_pixel(const Ctx &c, const FrameInfo &f, i
     im[2 * hw] = o2;
     T_final[f.pix_base + pix] = p.T;
     n_contrib[f.pix_base + pix] = p.last;
+    g[0] = g[1] = g[2] = 0.0f;
     if (target) {
         const float *tg = target + f.pix_base * 3 + pix;
         const float scale = 1.0f / (3.0f * (float)hw * (float)c.loss_frames);
         const float d0 = o0 - tg[0], d1 = o1 - tg[hw], d2 = o2 - tg[2 * hw];
-        float *dl = dl_dimg + f.pix_base * 3 + pix;
         if (loss_kind == RGBA_LOSS_L1) {
             loss_acc += (fabsf(d0) + fabsf(d1) + fabsf(d2)) * scale;
-            dl[0] = d0 > 0.f ? scale : (d0 < 0.f ? -scale : 0.f);
-            dl[hw] = d1 > 0.f ? scale : (d1 < 0.f ? -scale : 0.f);
-            dl[2 * hw] = d2 > 0.f ? scale : (d2 < 0.f ? -scale : 0.f);
+            g[0] = d0 > 0.f ? scale : (d0 < 0.f ? -scale : 0.f);
+            g[1] = d1 > 0.f ? scale : (d1 < 0.f ? -scale : 0.f);
+            g[2] = d2 > 0.f ? scale : (d2 < 0.f ? -scale : 0.f);
         } else {
             loss_acc += 0.5f * (d0 * d0 + d1 * d1 + d2 * d2) * scale;
-            dl[0] = d0 * scale;
-            dl[hw] = d1 * scale;
-            dl[2 * hw] = d2 * scale;
+            g[0] = d0 * scale;
+            g[1] = d1 * scale;
+            g[2] = d2 * scale;
+        }
+        if (dl_dimg) {
+            float *dl = dl_dimg + f.pix_base * 3 + pix;
+            dl[0] = g[0];
+            dl[hw] = g[1];
+            dl[2 * hw] = g[2];
         }
     }
 }
 
-// Items: the pixel blocks of the non-empty tiles (work list order, heaviest tiles first), then
-// one item per empty tile, which the warp fills with the background eight pixels per lane.
-// ACC (colour initialisation, Eq. 3): every blended entry also adds its splatting weight w and
-// w times the pixel's colour in acc_target to the record's first four 2-D gradient slots
-// (one warp reduction and four atomics per entry and pixel block).
-// STATS (the counting instance): also count the visits that evaluate an entry and the
-// (pixel, entry) pairs that blend, into the compositing statistics of the counters.
-template <int TW, int BATCH, bool ACC, bool STATS = false>
-__global__ void __launch_bounds__(32 * kWarpsPerCta)
-k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *__restrict__ n_contrib,
-             const float *__restrict__ target, int loss_kind, float *__restrict__ dl_dimg,
-             const float *__restrict__ acc_target) {
-    constexpr int TH = kTilePix / TW, BH = 4, NBX = TW / 8, NB = NBX * (TH / BH), S = BATCH / 32;
-    __shared__ float4 s_a[kWarpsPerCta][BATCH];
-    __shared__ float2 s_q[kWarpsPerCta][BATCH];
-    __shared__ float4 s_c[kWarpsPerCta][BATCH];
-    __shared__ unsigned s_idx[kWarpsPerCta][ACC ? BATCH : 1];
-    __shared__ float s_red[kWarpsPerCta];
-    pdl_enter();
-    if (c.cnt->overflow) return;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float4 *wa = s_a[wid], *wc = s_c[wid];
-    float2 *wq = s_q[wid];
-    unsigned *widx = ACC ? s_idx[wid] : nullptr;
-    const unsigned n_work = c.cnt->n_work, n_blocks = n_work * NB;
-    const unsigned n_items = n_blocks + ((unsigned)c.T - n_work);
-    float loss_acc = 0.0f;
-    unsigned long long st_visits = 0;  // STATS: warp-uniform
-    unsigned st_blends = 0;            // STATS: this lane's
-    while (true) {
-        unsigned item = 0;
-        if (lane == 0) item = atomicAdd(&c.cnt->next_fwd, 1u);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= n_items) break;
-        if (item >= n_blocks) {  // an empty tile: background, T = 1, no contributors
-            const long long t = c.work[n_work + (item - n_blocks)];
-            const int b = find_frame(c, t);
-            const FrameInfo &f = c.frames[b];
-            const int lt = (int)(t - f.tile_base);
-            const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
+// One compositing warp's view of a (tile, pixel block) item: the frame, the tile's list, the
+// block's pixel-centre box and the warp's shared-memory slots.
+struct Walk {
+    unsigned st;        // first list entry of the tile
+    int len;            // list length
+    const float4 *rec;  // the frame's render records
+    float bx0, bx1, by0, by1;
+    float4 *wa, *wc;
+    float2 *wq;
+    unsigned *widx;     // Gaussian index per slot, or nullptr when no caller needs it
+};
+
+// An empty tile's item: the background, T = 1, no contributors, eight pixels per lane.
+template <int TW>
+__device__ __forceinline__ void empty_tile(const Ctx &c, long long t, float *img, float *T_final, int *n_contrib,
+                                           const float *target, int loss_kind, float *dl_dimg, float &loss_acc) {
+    constexpr int TH = kTilePix / TW;
+    const int lane = threadIdx.x & 31;
+    const int b = find_frame(c, t);
+    const FrameInfo &f = c.frames[b];
+    const int lt = (int)(t - f.tile_base);
+    const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
 #pragma unroll 1
-            for (int k = lane; k < kTilePix; k += 32) {
-                const int px = tx * TW + (k % TW), py = ty * TH + (k / TW);
-                if (px < f.W && py < f.H) {
-                    const PixF p{(float)px + 0.5f, (float)py + 0.5f, 1.f, 0.f, 0.f, 0.f, 0, true, true};
-                    finish_pixel(c, f, b, px, py, p, img, T_final, n_contrib, target, loss_kind, dl_dimg, loss_acc);
-                }
-            }
-            continue;
+    for (int k = lane; k < kTilePix; k += 32) {
+        const int px = tx * TW + (k % TW), py = ty * TH + (k / TW);
+        if (px < f.W && py < f.H) {
+            const PixF p{(float)px + 0.5f, (float)py + 0.5f, 1.f, 0.f, 0.f, 0.f, 0, true, true};
+            float g[3];
+            finish_pixel(c, f, b, px, py, p, img, T_final, n_contrib, target, loss_kind, dl_dimg, loss_acc, g);
         }
-        const unsigned w = item / NB, blk = item - w * NB;
-        const long long t = c.work[w];
-        const int b = find_frame(c, t);
-        const FrameInfo &f = c.frames[b];
-        const int lt = (int)(t - f.tile_base);
-        const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
-        const int bx = tx * TW + (int)(blk % NBX) * 8, by = ty * TH + (int)(blk / NBX) * BH;
-        const int px = bx + (lane & 7), py = by + (lane >> 3);
-        const float bx0 = (float)bx + 0.5f, bx1 = (float)bx + 7.5f, by0 = (float)by + 0.5f, by1 = (float)by + 3.5f;
-        PixF p{(float)px + 0.5f, (float)py + 0.5f, 1.f, 0.f, 0.f, 0.f, 0, px < f.W && py < f.H, false};
-        p.done = !p.inside;
-        float I0 = 0.f, I1 = 0.f, I2 = 0.f;  // ACC: the pixel's target colour
-        if (ACC && p.inside) {
-            const long long hw = (long long)f.W * f.H;
-            const float *tg = acc_target + f.pix_base * 3 + (long long)py * f.W + px;
-            I0 = tg[0];
-            I1 = tg[hw];
-            I2 = tg[2 * hw];
-        }
-        float *acc = c.grad2d + (size_t)f.rec_base * kG2Floats;
-        const unsigned st = c.tile_start[t];
-        const int len = (int)(c.tile_start[t + 1] - st);
-        const float4 *rec = c.records + (size_t)f.rec_base * 3;
-        Stage<S> g;
-        unsigned nidx[S];
-        load_idx<S>(c, 0, len, st, nidx);
-        load_rec<S>(rec, 0, len, nidx, g);
-        load_idx<S>(c, BATCH, len, st, nidx);
-        for (int lo = 0; lo < len; lo += BATCH) {
-            if (__all_sync(0xffffffffu, p.done)) break;
-            unsigned hit[S];
-            __syncwarp();  // the previous batch's slots are no longer read
-            commit<S>(g, lo, len, wa, wq, wc, widx, bx0, bx1, by0, by1, hit);
-            load_rec<S>(rec, lo + BATCH, len, nidx, g);
-            load_idx<S>(c, lo + 2 * BATCH, len, st, nidx);
-            __syncwarp();
-            const int pos0 = lo + 1;
+    }
+}
+
+// The forward walk of one pixel block: the tile's list staged BATCH = 32 S entries at a time
+// (each batch's loads one and two batches ahead), the hits of each batch composited front to
+// back, until every pixel of the block is done or the list ends. The last committed batch
+// stays in the warp's slots: its first list position in lo_last (-1 if none), its hit words in
+// hit[]. ACC: colour-initialisation accumulation into acc (see k_render_fwd).
+template <int S, bool ACC, bool STATS>
+__device__ __forceinline__ void fwd_walk(const Ctx &c, const Walk &w, PixF &p, float I0, float I1, float I2,
+                                         float *acc, unsigned hit[S], int &lo_last,
+                                         unsigned long long &st_visits, unsigned &st_blends) {
+    constexpr int BATCH = 32 * S;
+    const int lane = threadIdx.x & 31;
+    Stage<S> g;
+    unsigned nidx[S];
+    load_idx<S>(c, 0, w.len, w.st, nidx);
+    load_rec<S>(w.rec, 0, w.len, nidx, g);
+    load_idx<S>(c, BATCH, w.len, w.st, nidx);
+    lo_last = -1;
+    for (int lo = 0; lo < w.len; lo += BATCH) {
+        if (__all_sync(0xffffffffu, p.done)) break;
+        __syncwarp();  // the previous batch's slots are no longer read
+        commit<S>(g, lo, w.len, w.wa, w.wq, w.wc, w.widx, w.bx0, w.bx1, w.by0, w.by1, hit);
+        lo_last = lo;
+        load_rec<S>(w.rec, lo + BATCH, w.len, nidx, g);
+        load_idx<S>(c, lo + 2 * BATCH, w.len, w.st, nidx);
+        __syncwarp();
+        const int pos0 = lo + 1;
 #pragma unroll
-            for (int q = 0; q < S; ++q) {
-                unsigned hm = hit[q];
-                while (hm) {
-                    const int j = 32 * q + __ffs(hm) - 1;
-                    hm &= hm - 1;
-                    const float4 A = wa[j];
-                    const float2 Q = wq[j];
-                    const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
-                    const float power = power_of(dx, dy, A, Q);
-                    const bool live = !p.done && !skip(power, Q.y);
-                    if (!__any_sync(0xffffffffu, live)) continue;  // the colour is not even read
-                    const float w = composite(p, live, power, wc[j], pos0 + j);
-                    if (STATS) {
-                        ++st_visits;
-                        st_blends += w > 0.0f ? 1u : 0u;
-                    }
-                    if (ACC && __any_sync(0xffffffffu, w > 0.0f)) {
-                        const float v[4] = {w, w * I0, w * I1, w * I2};
-                        const float mine = warp_reduce4(v, lane);
-                        if ((lane & 7) == 0) atomicAdd(acc + (size_t)widx[j] * kG2Floats + (lane >> 3), mine);
-                    }
+        for (int q = 0; q < S; ++q) {
+            unsigned hm = hit[q];
+            while (hm) {
+                const int j = 32 * q + __ffs(hm) - 1;
+                hm &= hm - 1;
+                const float4 A = w.wa[j];
+                const float2 Q = w.wq[j];
+                const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
+                const float power = power_of(dx, dy, A, Q);
+                const bool live = !p.done && !skip(power, Q.y);
+                if (!__any_sync(0xffffffffu, live)) continue;  // the colour is not even read
+                const float wgt = composite(p, live, power, w.wc[j], pos0 + j);
+                if (STATS) {
+                    ++st_visits;
+                    st_blends += wgt > 0.0f ? 1u : 0u;
+                }
+                if (ACC && __any_sync(0xffffffffu, wgt > 0.0f)) {
+                    const float v[4] = {wgt, wgt * I0, wgt * I1, wgt * I2};
+                    const float mine = warp_reduce4(v, lane);
+                    if ((lane & 7) == 0) atomicAdd(acc + (size_t)w.widx[j] * kG2Floats + (lane >> 3), mine);
                 }
             }
-        }
-        if (p.inside)
-            finish_pixel(c, f, b, px, py, p, img, T_final, n_contrib, target, loss_kind, dl_dimg, loss_acc);
-    }
-    if (STATS) {
-        for (int o = 16; o > 0; o >>= 1) st_blends += __shfl_xor_sync(0xffffffffu, st_blends, o);
-        if (lane == 0) {
-            atomicAdd(&c.cnt->st_fwd_visits, st_visits);
-            atomicAdd(&c.cnt->st_fwd_blends, (unsigned long long)st_blends);
-        }
-    }
-    // the last warp out puts the work counter back to zero for the next launch
-    if (lane == 0 && atomicAdd(&c.cnt->done_fwd, 1u) == gridDim.x * kWarpsPerCta - 1) {
-        c.cnt->next_fwd = 0u;
-        c.cnt->done_fwd = 0u;
-    }
-    if (target) {
-        for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
-        if (lane == 0) s_red[wid] = loss_acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float sum = 0.f;
-            for (int i = 0; i < kWarpsPerCta; ++i) sum += s_red[i];
-            atomicAdd(&c.cnt->loss, (double)sum);
         }
     }
 }
@@ -367,12 +321,16 @@ struct PixB {
 // One list entry for one pixel, in reverse, once the caller has evaluated the entry's power at
 // the pixel: live = the pixel blended the entry (its position is within the pixel's contributor
 // count and the power passes the cutoff). Writes this pixel's share of the entry's gradient
-// dL/d(u, v, conic a, b, c, opacity, r, g, b) into v (zeros when not live) and, when live,
-// steps T and P back past the entry. Branch-free, like the forward step: a lane that is not
-// live keeps its state and computes with its power clamped to 0, so that no infinite
-// exponential times a zero factor puts a NaN into the warp's sums.
-__device__ __forceinline__ void accumulate(PixB &p, bool live, float dx, float dy, float power, const float4 &A,
-                                           const float2 &Q, const float4 &Cc, float v[9]) {
+// sums into v (zeros when not live) and, when live, steps T and P back past the entry. With
+// g = dL/dpower at the pixel and (dx, dy) = pixel centre - mean, the power's gradient with
+// respect to the mean, the conic and the opacity is linear in g (dx, dy, dx^2, dx dy, dy^2, 1):
+// v = (g dx, g dy, g dx^2, g dx dy, g dy^2, g, dL/dr, dL/dg, dL/db), and the projection
+// backward turns the block sums into dL/d(u, v, conic, opacity) with the splat's own conic and
+// opacity (five products per pixel instead of sixteen). Branch-free, like the forward step: a
+// lane that is not live keeps its state and computes with its power clamped to 0, so that no
+// infinite exponential times a zero factor puts a NaN into the warp's sums.
+__device__ __forceinline__ void accumulate(PixB &p, bool live, float dx, float dy, float power, const float4 &Cc,
+                                           float v[9]) {
     const float G = __expf(fminf(power, 0.0f));
     const float araw = __fmul_rn(Cc.x, G);
     const float alpha = fminf(kAlphaMax, araw);
@@ -391,15 +349,14 @@ __device__ __forceinline__ void accumulate(PixB &p, bool live, float dx, float d
     v[8] = wgt * p.g2;
     // the clamp alpha = 0.99 passes no gradient to the opacity, conic or mean
     const float dcl = (live && !(araw > kAlphaMax)) ? dalpha : 0.0f;
-    v[5] = dcl * G;
-    const float dpow = dcl * araw;
-    const float hx = -0.5f * dx, hy = -0.5f * dy;
-    v[2] = hx * dx * dpow;
-    v[3] = -dx * dy * dpow;
-    v[4] = hy * dy * dpow;
-    // conic a = -2 A.z, b = -A.w, c = -2 Q.x
-    v[0] = -dpow * (2.0f * A.z * dx + A.w * dy);
-    v[1] = -dpow * (2.0f * Q.x * dy + A.w * dx);
+    const float dpow = dcl * araw;  // dL/dpower: alpha = o e^power
+    const float ex = dpow * dx, ey = dpow * dy;
+    v[0] = ex;
+    v[1] = ey;
+    v[2] = ex * dx;
+    v[3] = ex * dy;
+    v[4] = ey * dy;
+    v[5] = dpow;
 }
 
 // Warp sum of v[0..8] as a reduce-scatter: three halving exchanges leave lane l with the partial
@@ -432,13 +389,199 @@ __device__ __forceinline__ void warp_reduce9(const float v[9], int lane, float &
     v8 = x;
 }
 
+// The reverse walk of one pixel block over list positions [0, top), top the block's largest
+// contributor count: batches of BATCH = 32 S entries aligned to multiples of BATCH, from the one
+// holding position top - 1 down to position 0 (each batch's loads one and two batches ahead),
+// the hits of each batch in reverse. If the top batch is already in the warp's slots (staged by
+// the forward walk of the same block: first position `have`, hit words in hit[]), it is not
+// staged again. Per hit the block's gradient is reduced across the warp and added to the
+// entry's 2-D gradient slots in g2 (one atomic per component).
+template <int S, bool STATS>
+__device__ __forceinline__ void bwd_walk(const Ctx &c, const Walk &w, PixB &p, float *g2, int top, int have,
+                                         unsigned hit[S], unsigned long long &st_visits, unsigned &st_pairs) {
+    constexpr int BATCH = 32 * S;
+    const int lane = threadIdx.x & 31;
+    if (top <= 0) return;
+    const int b_hi = ((top - 1) / BATCH) * BATCH;
+    Stage<S> g;
+    unsigned nidx[S];
+    if (b_hi != have) {
+        load_idx<S>(c, b_hi, w.len, w.st, nidx);
+        load_rec<S>(w.rec, b_hi, w.len, nidx, g);
+        __syncwarp();  // the slots may still be read by the forward walk's last visits
+        commit<S>(g, b_hi, w.len, w.wa, w.wq, w.wc, w.widx, w.bx0, w.bx1, w.by0, w.by1, hit);
+    }
+    load_idx<S>(c, b_hi - BATCH, w.len, w.st, nidx);
+    load_rec<S>(w.rec, b_hi - BATCH, w.len, nidx, g);
+    load_idx<S>(c, b_hi - 2 * BATCH, w.len, w.st, nidx);
+    __syncwarp();
+    for (int begin = b_hi; begin >= 0; begin -= BATCH) {
+        if (begin != b_hi) {
+            __syncwarp();  // the previous batch's slots are no longer read
+            commit<S>(g, begin, w.len, w.wa, w.wq, w.wc, w.widx, w.bx0, w.bx1, w.by0, w.by1, hit);
+            load_rec<S>(w.rec, begin - BATCH, w.len, nidx, g);
+            load_idx<S>(c, begin - 2 * BATCH, w.len, w.st, nidx);
+            __syncwarp();
+        }
+#pragma unroll
+        for (int q = S - 1; q >= 0; --q) {
+            // positions at or past top blended at no pixel of the block
+            const int room = top - begin - 32 * q;
+            unsigned hm = hit[q] & (room >= 32 ? 0xffffffffu : (room <= 0 ? 0u : (1u << room) - 1u));
+            while (hm) {
+                const int bit = 31 - __clz(hm);
+                hm &= ~(1u << bit);
+                const int j = 32 * q + bit;
+                const int pos = begin + j + 1;
+                const float4 A = w.wa[j];
+                const float2 Q = w.wq[j];
+                const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
+                const float power = power_of(dx, dy, A, Q);
+                const bool live = pos <= p.last && !skip(power, Q.y);
+                if (!__any_sync(0xffffffffu, live)) continue;  // the colour is not even read
+                if (STATS) {
+                    ++st_visits;
+                    st_pairs += live ? 1u : 0u;
+                }
+                float v[9];
+                accumulate(p, live, dx, dy, power, w.wc[j], v);
+                float mine, v8;
+                warp_reduce9(v, lane, mine, v8);
+                float *dst = g2 + (size_t)w.widx[j] * kG2Floats;
+                if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), mine);
+                if (lane == 0) atomicAdd(dst + 8, v8);
+            }
+        }
+    }
+}
+
+// A (tile, pixel block) item: its frame, the block's pixel (one per lane: column lane % 8 of
+// row lane / 8 of the 8 x 4 block) and the walk over the tile's list.
+template <int TW>
+__device__ __forceinline__ int block_item(const Ctx &c, unsigned item, int &px, int &py, Walk &w) {
+    constexpr int TH = kTilePix / TW, NBX = TW / 8, NB = NBX * (TH / 4);
+    const int lane = threadIdx.x & 31;
+    const unsigned wk = item / NB, blk = item - wk * NB;
+    const long long t = c.work[wk];
+    const int b = find_frame(c, t);
+    const FrameInfo &f = c.frames[b];
+    const int lt = (int)(t - f.tile_base);
+    const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
+    const int bx = tx * TW + (int)(blk % NBX) * 8, by = ty * TH + (int)(blk / NBX) * 4;
+    px = bx + (lane & 7);
+    py = by + (lane >> 3);
+    w.bx0 = (float)bx + 0.5f;
+    w.bx1 = (float)bx + 7.5f;
+    w.by0 = (float)by + 0.5f;
+    w.by1 = (float)by + 3.5f;
+    w.st = c.tile_start[t];
+    w.len = (int)(c.tile_start[t + 1] - w.st);
+    w.rec = c.records + (size_t)f.rec_base * 3;
+    return b;
+}
+
+// Sums a per-lane statistic over the warp; lane 0 adds it and the warp's visit count.
+__device__ __forceinline__ void flush_stats(unsigned long long *visits, unsigned long long *count,
+                                            unsigned long long st_visits, unsigned st_count) {
+    for (int o = 16; o > 0; o >>= 1) st_count += __shfl_xor_sync(0xffffffffu, st_count, o);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(visits, st_visits);
+        atomicAdd(count, (unsigned long long)st_count);
+    }
+}
+
+// The loss: warp sums, then one double atomic per CTA.
+__device__ __forceinline__ void flush_loss(const Ctx &c, float loss_acc, float *s_red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
+    if (lane == 0) s_red[wid] = loss_acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float sum = 0.f;
+        for (int i = 0; i < kWarpsPerCta; ++i) sum += s_red[i];
+        atomicAdd(&c.cnt->loss, (double)sum);
+    }
+}
+
+// Items: the pixel blocks of the non-empty tiles (work list order, heaviest tiles first), then
+// one item per empty tile, which the warp fills with the background eight pixels per lane.
+// ACC (colour initialisation, Eq. 3): every blended entry also adds its splatting weight w and
+// w times the pixel's colour in acc_target to the record's first four 2-D gradient slots
+// (one warp reduction and four atomics per entry and pixel block).
+// STATS (the counting instance): also count the visits that evaluate an entry and the
+// (pixel, entry) pairs that blend, into the compositing statistics of the counters.
+template <int TW, int BATCH, bool ACC, bool STATS = false>
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
+k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *__restrict__ n_contrib,
+             const float *__restrict__ target, int loss_kind, float *__restrict__ dl_dimg,
+             const float *__restrict__ acc_target) {
+    constexpr int TH = kTilePix / TW, NB = (TW / 8) * (TH / 4), S = BATCH / 32;
+    __shared__ float4 s_a[kWarpsPerCta][BATCH];
+    __shared__ float2 s_q[kWarpsPerCta][BATCH];
+    __shared__ float4 s_c[kWarpsPerCta][BATCH];
+    __shared__ unsigned s_idx[kWarpsPerCta][ACC ? BATCH : 1];
+    __shared__ float s_red[kWarpsPerCta];
+    pdl_enter();
+    if (c.cnt->overflow) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    Walk w;
+    w.wa = s_a[wid];
+    w.wc = s_c[wid];
+    w.wq = s_q[wid];
+    w.widx = ACC ? s_idx[wid] : nullptr;
+    const unsigned n_work = c.cnt->n_work, n_blocks = n_work * NB;
+    const unsigned n_items = n_blocks + ((unsigned)c.T - n_work);
+    float loss_acc = 0.0f;
+    unsigned long long st_visits = 0;  // STATS: warp-uniform
+    unsigned st_blends = 0;            // STATS: this lane's
+    while (true) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(&c.cnt->next_fwd, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        if (item >= n_blocks) {  // an empty tile: background, T = 1, no contributors
+            empty_tile<TW>(c, c.work[n_work + (item - n_blocks)], img, T_final, n_contrib, target, loss_kind,
+                           dl_dimg, loss_acc);
+            continue;
+        }
+        int px, py;
+        const int b = block_item<TW>(c, item, px, py, w);
+        const FrameInfo &f = c.frames[b];
+        PixF p{(float)px + 0.5f, (float)py + 0.5f, 1.f, 0.f, 0.f, 0.f, 0, px < f.W && py < f.H, false};
+        p.done = !p.inside;
+        float I0 = 0.f, I1 = 0.f, I2 = 0.f;  // ACC: the pixel's target colour
+        if (ACC && p.inside) {
+            const long long hw = (long long)f.W * f.H;
+            const float *tg = acc_target + f.pix_base * 3 + (long long)py * f.W + px;
+            I0 = tg[0];
+            I1 = tg[hw];
+            I2 = tg[2 * hw];
+        }
+        unsigned hit[S];
+        int lo_last;
+        fwd_walk<S, ACC, STATS>(c, w, p, I0, I1, I2, c.grad2d + (size_t)f.rec_base * kG2Floats, hit, lo_last,
+                                st_visits, st_blends);
+        if (p.inside) {
+            float g[3];
+            finish_pixel(c, f, b, px, py, p, img, T_final, n_contrib, target, loss_kind, dl_dimg, loss_acc, g);
+        }
+    }
+    if (STATS) flush_stats(&c.cnt->st_fwd_visits, &c.cnt->st_fwd_blends, st_visits, st_blends);
+    // the last warp out puts the work counter back to zero for the next launch
+    if (lane == 0 && atomicAdd(&c.cnt->done_fwd, 1u) == gridDim.x * kWarpsPerCta - 1) {
+        c.cnt->next_fwd = 0u;
+        c.cnt->done_fwd = 0u;
+    }
+    if (target) flush_loss(c, loss_acc, s_red);
+}
+
 // STATS (the counting instance): also count the visits that evaluate an entry and the
 // (pixel, entry) pairs that take a gradient, into the compositing statistics of the counters.
 template <int TW, int BATCH, bool STATS = false>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__ T_final,
              const int *__restrict__ n_contrib) {
-    constexpr int TH = kTilePix / TW, NBX = TW / 8, NB = NBX * (TH / 4), S = BATCH / 32;
+    constexpr int TH = kTilePix / TW, NB = (TW / 8) * (TH / 4), S = BATCH / 32;
     __shared__ float4 s_a[kWarpsPerCta][BATCH];
     __shared__ float2 s_q[kWarpsPerCta][BATCH];
     __shared__ float4 s_c[kWarpsPerCta][BATCH];
@@ -446,9 +589,11 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
     pdl_enter();
     if (c.cnt->overflow) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float4 *wa = s_a[wid], *wc = s_c[wid];
-    float2 *wq = s_q[wid];
-    unsigned *widx = s_idx[wid];
+    Walk w;
+    w.wa = s_a[wid];
+    w.wc = s_c[wid];
+    w.wq = s_q[wid];
+    w.widx = s_idx[wid];
     const unsigned n_items = c.cnt->n_work * NB;
     unsigned long long st_visits = 0;  // STATS: warp-uniform
     unsigned st_pairs = 0;             // STATS: this lane's
@@ -457,19 +602,9 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
         if (lane == 0) item = atomicAdd(&c.cnt->next_bwd, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        const unsigned w = item / NB, blk = item - w * NB;
-        const long long t = c.work[w];
-        const int b = find_frame(c, t);
+        int px, py;
+        const int b = block_item<TW>(c, item, px, py, w);
         const FrameInfo &f = c.frames[b];
-        const int lt = (int)(t - f.tile_base);
-        const int ty = lt / f.tiles_x, tx = lt - ty * f.tiles_x;
-        // the block: 8 x 4 pixels; lane l owns column l % 8 of row l / 8
-        const int bx = tx * TW + (int)(blk % NBX) * 8, by = ty * TH + (int)(blk / NBX) * 4;
-        const int px = bx + (lane & 7), py = by + (lane >> 3);
-        const float bx0 = (float)bx + 0.5f, bx1 = (float)bx + 7.5f, by0 = (float)by + 0.5f, by1 = (float)by + 3.5f;
-        const unsigned st = c.tile_start[t], list_len = c.tile_start[t + 1] - st;
-        const float4 *rec = c.records + (size_t)f.rec_base * 3;
-        float *g2 = c.grad2d + (size_t)f.rec_base * kG2Floats;
         const float *bgp = c.fparams + (size_t)b * RGBA_FP_STRIDE + 17;
         const long long hw = (long long)f.W * f.H;
         PixB p{(float)px + 0.5f, (float)py + 0.5f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
@@ -487,58 +622,11 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
         int m = p.last;
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         // n_contrib comes from the caller: entries past the list's end do not exist
-        const int top = min(m, (int)list_len);
-        // batches from the top: [top - BATCH, top), [top - 2 BATCH, top - BATCH), ...; the slots
-        // of a batch cut at 0 start at the batch's nominal start (negative positions are empty)
-        Stage<S> g;
-        unsigned nidx[S];
-        load_idx<S>(c, top - BATCH, top, st, nidx);
-        load_rec<S>(rec, top - BATCH, top, nidx, g);
-        load_idx<S>(c, top - 2 * BATCH, top - BATCH, st, nidx);
-        for (int end = top; end > 0; end -= BATCH) {
-            const int begin = end - BATCH;
-            unsigned hit[S];
-            __syncwarp();  // the previous batch's slots are no longer read
-            commit<S>(g, begin, end, wa, wq, wc, widx, bx0, bx1, by0, by1, hit);
-            load_rec<S>(rec, begin - BATCH, begin, nidx, g);
-            load_idx<S>(c, begin - 2 * BATCH, begin - BATCH, st, nidx);
-            __syncwarp();
-#pragma unroll
-            for (int q = S - 1; q >= 0; --q) {
-                unsigned hm = hit[q];
-                while (hm) {
-                    const int bit = 31 - __clz(hm);
-                    hm &= ~(1u << bit);
-                    const int j = 32 * q + bit;
-                    const int pos = begin + j + 1;
-                    const float4 A = wa[j];
-                    const float2 Q = wq[j];
-                    const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
-                    const float power = power_of(dx, dy, A, Q);
-                    const bool live = pos <= p.last && !skip(power, Q.y);
-                    if (!__any_sync(0xffffffffu, live)) continue;  // the colour is not even read
-                    if (STATS) {
-                        ++st_visits;
-                        st_pairs += live ? 1u : 0u;
-                    }
-                    float v[9];
-                    accumulate(p, live, dx, dy, power, A, Q, wc[j], v);
-                    float mine, v8;
-                    warp_reduce9(v, lane, mine, v8);
-                    float *dst = g2 + (size_t)widx[j] * kG2Floats;
-                    if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), mine);
-                    if (lane == 0) atomicAdd(dst + 8, v8);
-                }
-            }
-        }
+        unsigned hit[S];
+        bwd_walk<S, STATS>(c, w, p, c.grad2d + (size_t)f.rec_base * kG2Floats, min(m, w.len), -1, hit, st_visits,
+                           st_pairs);
     }
-    if (STATS) {
-        for (int o = 16; o > 0; o >>= 1) st_pairs += __shfl_xor_sync(0xffffffffu, st_pairs, o);
-        if (lane == 0) {
-            atomicAdd(&c.cnt->st_bwd_visits, st_visits);
-            atomicAdd(&c.cnt->st_bwd_pairs, (unsigned long long)st_pairs);
-        }
-    }
+    if (STATS) flush_stats(&c.cnt->st_bwd_visits, &c.cnt->st_bwd_pairs, st_visits, st_pairs);
     // the last warp out puts the work counter back to zero for the next launch
     if (lane == 0 && atomicAdd(&c.cnt->done_bwd, 1u) == gridDim.x * kWarpsPerCta - 1) {
         c.cnt->next_bwd = 0u;

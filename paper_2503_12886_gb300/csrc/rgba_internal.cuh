@@ -244,8 +244,9 @@ bool make_fused_adam(const ModelInfo *models, int n_models, const rgba_adam_cfg 
 // max_ka: the largest k * A over the models (rows of blendshapes a chunk stages). fa (may be
 // NULL): apply Adam to G0 and the blendshapes where their gradients are reduced, instead of
 // writing the gradients (every model must be rendered by 1..16 frames).
+// any_bound: some model has a tangent-space binding (else the instance without the TBN mapping).
 cudaError_t launch_gauss_bwd(const Ctx &c, int max_chunks, int max_k, int max_ka, const FusedAdam *fa,
-                             cudaStream_t s);
+                             bool any_bound, cudaStream_t s);
 cudaError_t launch_dpsi_reduce(const Ctx &c, int max_k, cudaStream_t s);
 cudaError_t launch_adam(const ModelInfo *models, int n_models, const rgba_adam_cfg &cfg,
                         const rgba_adam_state *st, int step, int *step_dev, int sms, cudaStream_t s);

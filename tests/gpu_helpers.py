@@ -49,6 +49,24 @@ def read_intermediates(r: Renderer, db: DeviceBatch) -> dict:
             "layout": lay}
 
 
+def grad2d_from_sums(sums: np.ndarray, rec: np.ndarray) -> np.ndarray:
+    """The 2-D gradients dL/d(u, v, conic a, b, c, opacity, r, g, b) of the records rec [n][12]
+    from the compositing backward's per-record sums [n][>=9] (the workspace's grad2d layout:
+    S1..S5, S0 of g (dx, dy, dx^2, dx dy, dy^2, 1), g = dL/dpower, then the colour gradients),
+    in FP64: power = -(a dx^2 + c dy^2) / 2 - b dx dy with dx = pixel - u, alpha = o e^power."""
+    S = np.asarray(sums, np.float64)
+    a, b, c, o = (np.asarray(rec[:, k], np.float64) for k in (2, 3, 4, 5))
+    out = np.zeros((S.shape[0], 9))
+    out[:, 0] = a * S[:, 0] + b * S[:, 1]
+    out[:, 1] = b * S[:, 0] + c * S[:, 1]
+    out[:, 2] = -0.5 * S[:, 2]
+    out[:, 3] = -S[:, 3]
+    out[:, 4] = -0.5 * S[:, 4]
+    out[:, 5] = np.divide(S[:, 5], o, out=np.zeros_like(o), where=o > 0)
+    out[:, 6:9] = S[:, 6:9]
+    return out
+
+
 def frame_tile_bases(batch: synth.Batch, tile=(16, 16)):
     TW, TH = tile
     out, t = [], 0

@@ -10,7 +10,7 @@ from paper_2503_12886_gb300 import synth
 from paper_2503_12886_gb300.rasterizer import DeviceBatch, Renderer
 
 from gpu_helpers import (GRAD_FLOOR, GRAD_RTOL, PIX_ATOL, backward_errors, compare_decisions,
-                         compare_images, oracle_fwd_bwd, read_intermediates)
+                         compare_images, grad2d_from_sums, oracle_fwd_bwd, read_intermediates)
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +53,8 @@ def test_batched_workload_full_size(renderer):
     dl = torch.from_numpy(rng.standard_normal(3 * db.total_pix).astype(np.float32) * 1e-6).cuda()
     renderer.backward(db, dl, T, n)
     torch.cuda.synchronize()
-    g2_gpu = read_intermediates(renderer, db)["grad2d"]
+    inter = read_intermediates(renderer, db)
+    g2_gpu = grad2d_from_sums(inter["grad2d"], inter["records"])
     dl_views = [v.cpu().numpy().astype(np.float64) for v in db.image_views(dl)]
     checked = 0
     for b in (0, 7, 15):
@@ -73,7 +74,7 @@ def test_batched_workload_full_size(renderer):
         inside = (r[:, 0] >= x0) & (r[:, 2] <= x1) & (r[:, 1] >= y0) & (r[:, 3] <= y1) & (r[:, 2] > r[:, 0])
         idx = np.nonzero(inside)[0]
         assert len(idx) > 100
-        got = g2_gpu[db.rec_offsets[b] + idx, :9].astype(np.float64)
+        got = g2_gpu[db.rec_offsets[b] + idx]
         ref = g2[idx]
         scale = np.abs(ref).max(0, keepdims=True)
         err = np.abs(got - ref) / (GRAD_RTOL * np.abs(ref) + GRAD_FLOOR * scale + 1e-30)

@@ -287,3 +287,4 @@ def test_more_than_sixteen_frames_per_avatar(renderer, case):
     torch.cuda.synchronize()
     errs = backward_errors(batch, db, per_model, dpsi, dgbs, gb)
     assert max(errs.values()) <= 1.0, errs
+
