@@ -326,10 +326,14 @@ int rgba_profile_read(rgba_ctx_t ctx, rgba_profile *out);
  * accounting: how many list entries the kernels evaluated and how many of those blend.
  * Synchronous; out: host. */
 typedef struct {
-    int64_t fwd_visits;  /* (list entry, 8x4 pixel block) visits at which the forward evaluated the
-                            entry (its box meets the block and some pixel passes the cutoffs) */
+    int64_t fwd_staged;  /* list entries the forward's pixel-block warps staged */
+    int64_t fwd_hits;    /* (list entry, 8x4 pixel block) pairs whose alpha box meets the block */
+    int64_t fwd_visits;  /* hits at which some pixel of the block passes the cutoffs (the entry
+                            is then composited at the block) */
     int64_t fwd_blends;  /* (pixel, entry) pairs the forward blended */
-    int64_t bwd_visits;  /* the same visits of the backward's reverse walk */
+    int64_t bwd_staged;  /* the same counts for the backward's reverse walk */
+    int64_t bwd_hits;
+    int64_t bwd_visits;
     int64_t bwd_pairs;   /* (pixel, entry) pairs the backward took a gradient of (those that
                             blended: equal to fwd_blends after one forward and one backward) */
 } rgba_render_stats;

@@ -79,8 +79,9 @@ class RgbaAdamState(C.Structure):
 
 
 class RgbaRenderStats(C.Structure):
-    _fields_ = [("fwd_visits", C.c_int64), ("fwd_blends", C.c_int64), ("bwd_visits", C.c_int64),
-                ("bwd_pairs", C.c_int64)]
+    _fields_ = [("fwd_staged", C.c_int64), ("fwd_hits", C.c_int64), ("fwd_visits", C.c_int64),
+                ("fwd_blends", C.c_int64), ("bwd_staged", C.c_int64), ("bwd_hits", C.c_int64),
+                ("bwd_visits", C.c_int64), ("bwd_pairs", C.c_int64)]
 
 
 class RgbaProfile(C.Structure):

@@ -853,10 +853,14 @@ int rgba_debug_render_stats(rgba_ctx_t ctx, const rgba_batch *batch, const void 
     cudaError_t e = cudaMemcpyAsync(&h, k.ws + k.p.L.counters, sizeof(h), cudaMemcpyDeviceToHost, k.s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(k.s);
     if (e != cudaSuccess) return cuda_fail(e, "read counters");
-    out->fwd_visits = (int64_t)h.st_fwd_visits;
-    out->fwd_blends = (int64_t)h.st_fwd_blends;
-    out->bwd_visits = (int64_t)h.st_bwd_visits;
-    out->bwd_pairs = (int64_t)h.st_bwd_pairs;
+    out->fwd_staged = (int64_t)h.st_fwd[0];
+    out->fwd_hits = (int64_t)h.st_fwd[1];
+    out->fwd_visits = (int64_t)h.st_fwd[2];
+    out->fwd_blends = (int64_t)h.st_fwd[3];
+    out->bwd_staged = (int64_t)h.st_bwd[0];
+    out->bwd_hits = (int64_t)h.st_bwd[1];
+    out->bwd_visits = (int64_t)h.st_bwd[2];
+    out->bwd_pairs = (int64_t)h.st_bwd[3];
     return RGBA_OK;
 }
 

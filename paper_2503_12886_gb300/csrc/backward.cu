@@ -316,8 +316,9 @@ __device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// 3 CTAs per SM (80 registers, a few spills to L1) beat 2 CTAs without spills: the kernel
-// waits on memory and needs the warps.
+// 2 CTAs per SM: without the TBN mapping (unbound batches) the chain rule fits without spills
+// at up to 128 registers, and that beat 3 CTAs at 80 registers with spills (0.120 vs 0.127 ms
+// on the batched training workload).
 // ADAM: the fused Adam update of rgba_step_adam_async; every model is rendered by at most kFG2
 // frames, so the reductions below are complete after one group. Their results are parked in
 // shared memory (G0's in s_g0, the blendshapes' in the slots of the staged rows, whose values
@@ -335,7 +336,7 @@ using AdamArg = typename std::conditional<ADAM, FusedAdam, NoAdam>::type;
 // BOUND: some model of the batch has a tangent-space binding (the chain rule then maps through
 // each bound Gaussian's TBN frame); otherwise that mapping is compiled out.
 template <bool ADAM, bool BOUND>
-__global__ void __launch_bounds__(kBwdThreads, 3)
+__global__ void __launch_bounds__(kBwdThreads, 2)
 k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
     extern __shared__ float smem[];
     float *s_dG = smem;                                   // [16][14][32]

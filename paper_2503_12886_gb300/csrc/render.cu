@@ -257,6 +257,14 @@ __device__ __forceinline__ void empty_tile(const Ctx &c, long long t, float *img
     }
 }
 
+// Compositing statistics of one warp (counting instances only): entries staged, box hits,
+// visits that evaluated an entry (a hit with some pixel past the cutoffs; warp-uniform), and the
+// (pixel, entry) pairs that blend or take a gradient (this lane's).
+struct WalkStats {
+    unsigned long long staged, hits, visits;
+    unsigned lanes;
+};
+
 // The forward walk of one pixel block: the tile's list staged BATCH = 32 S entries at a time
 // (each batch's loads one and two batches ahead), the hits of each batch composited front to
 // back, until every pixel of the block is done or the list ends. The last committed batch
@@ -264,8 +272,7 @@ __device__ __forceinline__ void empty_tile(const Ctx &c, long long t, float *img
 // hit[]. ACC: colour-initialisation accumulation into acc (see k_render_fwd).
 template <int S, bool ACC, bool STATS>
 __device__ __forceinline__ void fwd_walk(const Ctx &c, const Walk &w, PixF &p, float I0, float I1, float I2,
-                                         float *acc, unsigned hit[S], int &lo_last,
-                                         unsigned long long &st_visits, unsigned &st_blends) {
+                                         float *acc, unsigned hit[S], int &lo_last, WalkStats &st) {
     constexpr int BATCH = 32 * S;
     const int lane = threadIdx.x & 31;
     Stage<S> g;
@@ -279,6 +286,7 @@ __device__ __forceinline__ void fwd_walk(const Ctx &c, const Walk &w, PixF &p, f
         __syncwarp();  // the previous batch's slots are no longer read
         commit<S>(g, lo, w.len, w.wa, w.wq, w.wc, w.widx, w.bx0, w.bx1, w.by0, w.by1, hit);
         lo_last = lo;
+        if (STATS) st.staged += min(BATCH, w.len - lo);
         load_rec<S>(w.rec, lo + BATCH, w.len, nidx, g);
         load_idx<S>(c, lo + 2 * BATCH, w.len, w.st, nidx);
         __syncwarp();
@@ -294,11 +302,12 @@ __device__ __forceinline__ void fwd_walk(const Ctx &c, const Walk &w, PixF &p, f
                 const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
                 const float power = power_of(dx, dy, A, Q);
                 const bool live = !p.done && !skip(power, Q.y);
+                if (STATS) ++st.hits;
                 if (!__any_sync(0xffffffffu, live)) continue;  // the colour is not even read
                 const float wgt = composite(p, live, power, w.wc[j], pos0 + j);
                 if (STATS) {
-                    ++st_visits;
-                    st_blends += wgt > 0.0f ? 1u : 0u;
+                    ++st.visits;
+                    st.lanes += wgt > 0.0f ? 1u : 0u;
                 }
                 if (ACC && __any_sync(0xffffffffu, wgt > 0.0f)) {
                     const float v[4] = {wgt, wgt * I0, wgt * I1, wgt * I2};
@@ -398,7 +407,7 @@ __device__ __forceinline__ void warp_reduce9(const float v[9], int lane, float &
 // entry's 2-D gradient slots in g2 (one atomic per component).
 template <int S, bool STATS>
 __device__ __forceinline__ void bwd_walk(const Ctx &c, const Walk &w, PixB &p, float *g2, int top, int have,
-                                         unsigned hit[S], unsigned long long &st_visits, unsigned &st_pairs) {
+                                         unsigned hit[S], WalkStats &st) {
     constexpr int BATCH = 32 * S;
     const int lane = threadIdx.x & 31;
     if (top <= 0) return;
@@ -410,6 +419,7 @@ __device__ __forceinline__ void bwd_walk(const Ctx &c, const Walk &w, PixB &p, f
         load_rec<S>(w.rec, b_hi, w.len, nidx, g);
         __syncwarp();  // the slots may still be read by the forward walk's last visits
         commit<S>(g, b_hi, w.len, w.wa, w.wq, w.wc, w.widx, w.bx0, w.bx1, w.by0, w.by1, hit);
+        if (STATS) st.staged += min(BATCH, w.len - b_hi);
     }
     load_idx<S>(c, b_hi - BATCH, w.len, w.st, nidx);
     load_rec<S>(w.rec, b_hi - BATCH, w.len, nidx, g);
@@ -419,6 +429,7 @@ __device__ __forceinline__ void bwd_walk(const Ctx &c, const Walk &w, PixB &p, f
         if (begin != b_hi) {
             __syncwarp();  // the previous batch's slots are no longer read
             commit<S>(g, begin, w.len, w.wa, w.wq, w.wc, w.widx, w.bx0, w.bx1, w.by0, w.by1, hit);
+            if (STATS) st.staged += BATCH;
             load_rec<S>(w.rec, begin - BATCH, w.len, nidx, g);
             load_idx<S>(c, begin - 2 * BATCH, w.len, w.st, nidx);
             __syncwarp();
@@ -438,10 +449,11 @@ __device__ __forceinline__ void bwd_walk(const Ctx &c, const Walk &w, PixB &p, f
                 const float dx = __fsub_rn(p.pxc, A.x), dy = __fsub_rn(p.pyc, A.y);
                 const float power = power_of(dx, dy, A, Q);
                 const bool live = pos <= p.last && !skip(power, Q.y);
+                if (STATS) ++st.hits;
                 if (!__any_sync(0xffffffffu, live)) continue;  // the colour is not even read
                 if (STATS) {
-                    ++st_visits;
-                    st_pairs += live ? 1u : 0u;
+                    ++st.visits;
+                    st.lanes += live ? 1u : 0u;
                 }
                 float v[9];
                 accumulate(p, live, dx, dy, power, w.wc[j], v);
@@ -480,13 +492,15 @@ __device__ __forceinline__ int block_item(const Ctx &c, unsigned item, int &px, 
     return b;
 }
 
-// Sums a per-lane statistic over the warp; lane 0 adds it and the warp's visit count.
-__device__ __forceinline__ void flush_stats(unsigned long long *visits, unsigned long long *count,
-                                            unsigned long long st_visits, unsigned st_count) {
-    for (int o = 16; o > 0; o >>= 1) st_count += __shfl_xor_sync(0xffffffffu, st_count, o);
+// Adds a warp's statistics to the counters (dst: staged, hits, visits, pairs), the per-lane
+// pair count summed over the warp first.
+__device__ __forceinline__ void flush_stats(unsigned long long *dst, WalkStats st) {
+    for (int o = 16; o > 0; o >>= 1) st.lanes += __shfl_xor_sync(0xffffffffu, st.lanes, o);
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(visits, st_visits);
-        atomicAdd(count, (unsigned long long)st_count);
+        atomicAdd(dst + 0, st.staged);
+        atomicAdd(dst + 1, st.hits);
+        atomicAdd(dst + 2, st.visits);
+        atomicAdd(dst + 3, (unsigned long long)st.lanes);
     }
 }
 
@@ -532,8 +546,7 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
     const unsigned n_work = c.cnt->n_work, n_blocks = n_work * NB;
     const unsigned n_items = n_blocks + ((unsigned)c.T - n_work);
     float loss_acc = 0.0f;
-    unsigned long long st_visits = 0;  // STATS: warp-uniform
-    unsigned st_blends = 0;            // STATS: this lane's
+    WalkStats st{0ull, 0ull, 0ull, 0u};  // STATS
     while (true) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(&c.cnt->next_fwd, 1u);
@@ -559,14 +572,13 @@ k_render_fwd(Ctx c, float *__restrict__ img, float *__restrict__ T_final, int *_
         }
         unsigned hit[S];
         int lo_last;
-        fwd_walk<S, ACC, STATS>(c, w, p, I0, I1, I2, c.grad2d + (size_t)f.rec_base * kG2Floats, hit, lo_last,
-                                st_visits, st_blends);
+        fwd_walk<S, ACC, STATS>(c, w, p, I0, I1, I2, c.grad2d + (size_t)f.rec_base * kG2Floats, hit, lo_last, st);
         if (p.inside) {
             float g[3];
             finish_pixel(c, f, b, px, py, p, img, T_final, n_contrib, target, loss_kind, dl_dimg, loss_acc, g);
         }
     }
-    if (STATS) flush_stats(&c.cnt->st_fwd_visits, &c.cnt->st_fwd_blends, st_visits, st_blends);
+    if (STATS) flush_stats(c.cnt->st_fwd, st);
     // the last warp out puts the work counter back to zero for the next launch
     if (lane == 0 && atomicAdd(&c.cnt->done_fwd, 1u) == gridDim.x * kWarpsPerCta - 1) {
         c.cnt->next_fwd = 0u;
@@ -595,8 +607,7 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
     w.wq = s_q[wid];
     w.widx = s_idx[wid];
     const unsigned n_items = c.cnt->n_work * NB;
-    unsigned long long st_visits = 0;  // STATS: warp-uniform
-    unsigned st_pairs = 0;             // STATS: this lane's
+    WalkStats st{0ull, 0ull, 0ull, 0u};  // STATS
     while (true) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(&c.cnt->next_bwd, 1u);
@@ -623,10 +634,9 @@ k_render_bwd(Ctx c, const float *__restrict__ dl_dimg, const float *__restrict__
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         // n_contrib comes from the caller: entries past the list's end do not exist
         unsigned hit[S];
-        bwd_walk<S, STATS>(c, w, p, c.grad2d + (size_t)f.rec_base * kG2Floats, min(m, w.len), -1, hit, st_visits,
-                           st_pairs);
+        bwd_walk<S, STATS>(c, w, p, c.grad2d + (size_t)f.rec_base * kG2Floats, min(m, w.len), -1, hit, st);
     }
-    if (STATS) flush_stats(&c.cnt->st_bwd_visits, &c.cnt->st_bwd_pairs, st_visits, st_pairs);
+    if (STATS) flush_stats(c.cnt->st_bwd, st);
     // the last warp out puts the work counter back to zero for the next launch
     if (lane == 0 && atomicAdd(&c.cnt->done_bwd, 1u) == gridDim.x * kWarpsPerCta - 1) {
         c.cnt->next_bwd = 0u;

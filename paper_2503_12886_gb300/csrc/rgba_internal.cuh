@@ -84,10 +84,10 @@ struct Counters {
     unsigned done_bwd;    // every launch starts from zero without a memset
     // compositing statistics, counted only by the counting instances of the compositing kernels
     // (rgba_profile_enable(ctx, 2)); zeroed with the rest at the start of every preprocess
-    unsigned long long st_fwd_visits;  // (entry, pixel block) visits the forward evaluated
-    unsigned long long st_fwd_blends;  // (pixel, entry) pairs the forward blended
-    unsigned long long st_bwd_visits;  // (entry, pixel block) visits the backward evaluated
-    unsigned long long st_bwd_pairs;   // (pixel, entry) pairs the backward took a gradient of
+    // per direction: list entries staged, box hits, (entry, pixel block) visits that evaluated
+    // the entry, (pixel, entry) pairs that blended (forward) or took a gradient (backward)
+    unsigned long long st_fwd[4];
+    unsigned long long st_bwd[4];
 };
 static_assert(sizeof(Counters) <= 256, "counters fit in one 256-byte block");
 

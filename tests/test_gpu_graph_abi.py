@@ -135,12 +135,13 @@ def test_render_stats_count_blends_without_changing_results(renderer):
                      db.grad_psi.clone(), n, st))
     api.rgba_profile_enable(renderer.ctx, 0)
     (i0, l0, g0, d0, p0, n0, s0), (i2, l2, g2, d2, p2, n2, s2) = outs
-    assert s0 == {"fwd_visits": 0, "fwd_blends": 0, "bwd_visits": 0, "bwd_pairs": 0}
+    assert all(v == 0 for v in s0.values())
     assert torch.equal(i0, i2) and torch.equal(n0, n2)
     assert abs(l0 - l2) <= 1e-6 * l0  # fp32 per-CTA loss partials are added by atomics, in any order
     # the compositing backward's atomics may sum in another order: equal up to that
     for a, b in ((g0, g2), (d0, d2), (p0, p2)):
         assert float((a - b).abs().max()) <= 1e-5 * float(a.abs().max())
     assert s2["fwd_blends"] == s2["bwd_pairs"] > 0
-    assert s2["fwd_visits"] > 0 and s2["bwd_visits"] > 0
+    assert 0 < s2["fwd_visits"] <= s2["fwd_hits"] <= s2["fwd_staged"]
+    assert 0 < s2["bwd_visits"] <= s2["bwd_hits"] <= s2["bwd_staged"]
     assert int((n2 > 0).sum()) <= s2["fwd_blends"] <= int(n2.to(torch.int64).sum())
