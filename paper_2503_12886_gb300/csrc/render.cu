@@ -164,6 +164,14 @@ __device__ __forceinline__ void commit(const Stage<S> &g, int lo, int hi, float4
     }
 }
 
+// A fire-and-forget global float add by the lanes where p holds, written as one predicated
+// instruction: a branch around the atomic made the compiler reconverge the warp at every visit
+// (0.53 -> 0.48 ms for the compositing backward of the batched training workload).
+__device__ __forceinline__ void red_add_if(bool p, float *addr, float v) {
+    asm volatile("{ .reg .pred q; setp.ne.b32 q, %2, 0; @q red.global.add.f32 [%0], %1; }"
+                 :: "l"(addr), "f"(v), "r"((int)p) : "memory");
+}
+
 // Warp sum of v[0..3] as a reduce-scatter: lane l ends with the total of value (l >> 3) & 3.
 __device__ __forceinline__ float warp_reduce4(const float v[4], int lane) {
     const unsigned F = 0xffffffffu;
@@ -312,7 +320,7 @@ __device__ __forceinline__ void fwd_walk(const Ctx &c, const Walk &w, PixF &p, f
                 if (ACC && __any_sync(0xffffffffu, wgt > 0.0f)) {
                     const float v[4] = {wgt, wgt * I0, wgt * I1, wgt * I2};
                     const float mine = warp_reduce4(v, lane);
-                    if ((lane & 7) == 0) atomicAdd(acc + (size_t)w.widx[j] * kG2Floats + (lane >> 3), mine);
+                    red_add_if((lane & 7) == 0, acc + (size_t)w.widx[j] * kG2Floats + (lane >> 3), mine);
                 }
             }
         }
@@ -460,8 +468,8 @@ __device__ __forceinline__ void bwd_walk(const Ctx &c, const Walk &w, PixB &p, f
                 float mine, v8;
                 warp_reduce9(v, lane, mine, v8);
                 float *dst = g2 + (size_t)w.widx[j] * kG2Floats;
-                if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), mine);
-                if (lane == 0) atomicAdd(dst + 8, v8);
+                red_add_if((lane & 3) == 0, dst + (lane >> 2), mine);
+                red_add_if(lane == 0, dst + 8, v8);
             }
         }
     }
