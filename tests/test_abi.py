@@ -71,6 +71,7 @@ def test_workspace_size_grows_with_capacity(api):
                         setattr(ms[0], "faces", 0x5000), setattr(ms[0], "face_uv", 0x6000),
                         setattr(ms[0], "face_of", 0x7000), setattr(ms[0], "bary", 0x8000)), "verts"),
     (lambda b, ms, fs: setattr(ms[0], "n_faces", -1), "tangent-space binding"),
+    (lambda b, ms, fs: setattr(b, "loss_frames", -1), "loss_frames"),
 ])
 def test_invalid_batches_rejected_on_host(api, mutate, msg):
     b, ms, fs = _batch(api)
@@ -79,6 +80,13 @@ def test_invalid_batches_rejected_on_host(api, mutate, msg):
         api.rgba_workspace_size(b, 100)
     assert e.value.code == api.RGBA_ERR_INVALID_ARG
     assert msg in str(e.value)
+
+
+def test_loss_frames_of_a_shard_accepted(api):
+    """A data-parallel rank's batch averages its loss over the global batch: loss_frames at or
+    above the batch's own frame count is valid and changes no buffer size."""
+    b, _, _ = _batch(api, loss_frames=16)
+    assert api.rgba_workspace_size(b, 100) == api.rgba_workspace_size(_batch(api)[0], 100)
 
 
 def test_complete_binding_accepted(api):
