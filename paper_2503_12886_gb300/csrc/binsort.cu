@@ -217,12 +217,17 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(Ctx c) {
         const uint4 *rp = reinterpret_cast<const uint4 *>(c.ranks + r * kRankSlots);
         const uint4 r0 = rp[0], r1 = rp[1];
         const unsigned rk[kRankSlots] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        const unsigned *ts = c.tile_start + f.tile_base + (long long)rc.y * f.tiles_x + rc.x;
+        int ox = 0, off = 0;  // slot q is tile (rc.x + ox, rc.y + q / w), off its offset from ts
 #pragma unroll
         for (int q = 0; q < kRankSlots; ++q) {
             if (q < area) {
-                const int dy = q / w;
-                const long long gt = f.tile_base + (long long)(rc.y + dy) * f.tiles_x + rc.x + (q - dy * w);
-                c.keys[c.tile_start[gt] + rk[q]] = key;
+                c.keys[ts[off] + rk[q]] = key;
+                ++off;
+                if (++ox == w) {
+                    ox = 0;
+                    off += f.tiles_x - w;
+                }
             }
         }
         return;

@@ -281,11 +281,13 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const ModelInfo &
         float rad = ceilf(fmul(3.0f, fsqrt(lam)));
         float u = fadd(fmul(fx, fdiv(p[0], p[2])), V[14]);
         float vv = fadd(fmul(fy, fdiv(p[1], p[2])), V[15]);
-        const float ftw = (float)c.tw, fth = (float)c.th;
-        float x0 = floorf(fdiv(fsub(u, rad), ftw));
-        float x1 = floorf(fdiv(fadd(fadd(u, rad), fsub(ftw, 1.0f)), ftw));
-        float y0 = floorf(fdiv(fsub(vv, rad), fth));
-        float y1 = floorf(fdiv(fadd(fadd(vv, rad), fsub(fth, 1.0f)), fth));
+        // the tile sides are powers of two (16 x 16 or 8 x 32), so each division by a side is
+        // the product with its exact reciprocal: the same correctly rounded quotient
+        const float ftw = (float)c.tw, fth = (float)c.th, rtw = 1.0f / ftw, rth = 1.0f / fth;
+        float x0 = floorf(fmul(fsub(u, rad), rtw));
+        float x1 = floorf(fmul(fadd(fadd(u, rad), fsub(ftw, 1.0f)), rtw));
+        float y0 = floorf(fmul(fsub(vv, rad), rth));
+        float y1 = floorf(fmul(fadd(fadd(vv, rad), fsub(fth, 1.0f)), rth));
         x0 = fminf((float)f.tiles_x, fmaxf(0.0f, x0));
         x1 = fminf((float)f.tiles_x, fmaxf(0.0f, x1));
         y0 = fminf((float)f.tiles_y, fmaxf(0.0f, y0));
@@ -301,14 +303,19 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const ModelInfo &
         // tiles keep the slot each count returns, so the scatter needs no atomics
         const int rw = ix1 - ix0, area = rw * (iy1 - iy0);
         if (area <= kRankSlots) {
-            unsigned *tc = c.tile_count + f.tile_base;
+            unsigned *tc = c.tile_count + f.tile_base + iy0 * f.tiles_x + ix0;
             unsigned rk[kRankSlots];
+            int ox = 0, off = 0;  // slot q is tile (ix0 + ox, iy0 + q / rw), off its offset from tc
 #pragma unroll
             for (int q = 0; q < kRankSlots; ++q) {
                 rk[q] = 0u;
                 if (q < area) {
-                    const int dy = q / rw;
-                    rk[q] = atomicAdd(tc + (iy0 + dy) * f.tiles_x + ix0 + (q - dy * rw), 1u);
+                    rk[q] = atomicAdd(tc + off, 1u);
+                    ++off;
+                    if (++ox == rw) {
+                        ox = 0;
+                        off += f.tiles_x - rw;
+                    }
                 }
             }
             uint4 *rp = reinterpret_cast<uint4 *>(c.ranks + r * kRankSlots);
@@ -331,6 +338,8 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const ModelInfo &
 }
 
 constexpr int kPreThreads = 128;  // standalone blend
+// the row stride of the staged weights: max_k rounded up to a multiple of 4
+__host__ __device__ constexpr int psi_stride(int max_k) { return (max_k + 3) & ~3; }
 constexpr int kPreG = 32;         // Gaussians per CTA
 constexpr int kPreSlots = 8;      // frame slots per Gaussian
 constexpr int kPreFB = 2;         // frames per thread per round (register block)
@@ -370,8 +379,9 @@ k_preprocess(Ctx c, int max_k) {
     const unsigned mask = MASK ? MASK : m.mask;
     const int K = m.k, A = MASK ? popcount_c(MASK) : m.A, rows = kNch + K * A;
     float *s_rows = reinterpret_cast<float *>(smem4);      // [rows][kPreG]: G0 then blendshapes
-    float *s_psi = s_rows + (size_t)rows * kPreG;          // [16][max_k]
-    float *s_fp = s_psi + kPreRound * max_k;               // [16][20]
+    const int kp = psi_stride(max_k);                      // 16-byte rows of weights
+    float *s_psi = s_rows + (size_t)rows * kPreG;          // [16][kp]
+    float *s_fp = s_psi + kPreRound * kp;                  // [16][20]
     const int tid = threadIdx.x;
     const int cols = min(kPreG, m.n_pad - i0);
     {  // 16-byte asynchronous copies of the chunk's rows by every thread, then one wait
@@ -395,7 +405,7 @@ k_preprocess(Ctx c, int max_k) {
         for (int e = tid; e < nr * K; e += kPreBlock) {
             const int fl = e / K, kk = e - fl * K;
             const int b = c.mframes[m.frame_off + round + fl];
-            s_psi[fl * max_k + kk] = c.psi[(size_t)b * c.k_stride + kk];
+            s_psi[fl * kp + kk] = c.psi[(size_t)b * c.k_stride + kk];
         }
         for (int e = tid; e < nr * RGBA_FP_STRIDE; e += kPreBlock) {
             const int fl = e / RGBA_FP_STRIDE, q = e - fl * RGBA_FP_STRIDE;
@@ -428,10 +438,7 @@ k_preprocess(Ctx c, int max_k) {
 #pragma unroll
                 for (int q = 0; q < kPreFB; ++q) v[q][ch] = x;
             }
-            for (int kk = 0; kk < K; ++kk) {
-                float ps[kPreFB];
-#pragma unroll
-                for (int q = 0; q < kPreFB; ++q) ps[q] = s_psi[(f0 + q) * max_k + kk];
+            auto term = [&](int kk, const float ps[kPreFB]) {
                 const float *d = s_rows + (size_t)(kNch + kk * A) * kPreG + g;
                 int a = 0;
 #pragma unroll
@@ -443,6 +450,31 @@ k_preprocess(Ctx c, int max_k) {
                         ++a;
                     }
                 }
+            };
+            int kk = 0;
+            for (; kk + 4 <= K; kk += 4) {  // the weights four at a time (one 16-byte load per frame)
+                float4 w4[kPreFB];
+#pragma unroll
+                for (int q = 0; q < kPreFB; ++q) w4[q] = *reinterpret_cast<const float4 *>(s_psi + (f0 + q) * kp + kk);
+                float ps[kPreFB];
+#pragma unroll
+                for (int q = 0; q < kPreFB; ++q) ps[q] = w4[q].x;
+                term(kk, ps);
+#pragma unroll
+                for (int q = 0; q < kPreFB; ++q) ps[q] = w4[q].y;
+                term(kk + 1, ps);
+#pragma unroll
+                for (int q = 0; q < kPreFB; ++q) ps[q] = w4[q].z;
+                term(kk + 2, ps);
+#pragma unroll
+                for (int q = 0; q < kPreFB; ++q) ps[q] = w4[q].w;
+                term(kk + 3, ps);
+            }
+            for (; kk < K; ++kk) {
+                float ps[kPreFB];
+#pragma unroll
+                for (int q = 0; q < kPreFB; ++q) ps[q] = s_psi[(f0 + q) * kp + kk];
+                term(kk, ps);
             }
             // one frame at a time through v[0] (a rolled loop keeps the code small)
 #pragma unroll 1
@@ -540,7 +572,7 @@ cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t
 }
 
 int preprocess_smem(int max_k, int max_rows) {
-    return (max_rows * kPreG + kPreRound * max_k + kPreRound * RGBA_FP_STRIDE) * (int)sizeof(float);
+    return (max_rows * kPreG + kPreRound * psi_stride(max_k) + kPreRound * RGBA_FP_STRIDE) * (int)sizeof(float);
 }
 
 namespace {
