@@ -384,22 +384,21 @@ k_preprocess(Ctx c, int max_k) {
     float *s_fp = s_psi + kPreRound * kp;                  // [16][20]
     const int tid = threadIdx.x;
     const int cols = min(kPreG, m.n_pad - i0);
-    {  // 16-byte asynchronous copies of the chunk's rows by every thread, then one wait
+    {  // 16-byte asynchronous copies of the chunk's rows by every thread; the first round's
+       // frame tables below are gathered while they are in flight, then one wait
         const int per_row = cols >> 2;  // n_pad and i0 are multiples of 4
         for (int e = tid; e < rows * per_row; e += kPreBlock) {
             const int rr = e / per_row, q = e - rr * per_row;
             const float *src = (rr < kNch ? m.g0 + (size_t)rr * m.n_pad : m.dg + (size_t)(rr - kNch) * m.n_pad) + i0 + 4 * q;
             cp_async16(s_rows + (size_t)rr * kPreG + 4 * q, src);
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
     }
     const int g = tid % kPreG, slot = tid / kPreG;
     const int i = i0 + g;
     const bool valid = i < m.n;
     // opacity is the same for every frame unless it is blended
     const bool op_blended = (mask >> 10) & 1u;
-    const float op0 = sigmoid_spec(s_rows[10 * kPreG + g]);
+    float op0 = 0.0f;
     for (int round = 0; round < m.nb; round += kPreRound) {
         const int nr = min(kPreRound, m.nb - round);
         for (int e = tid; e < nr * K; e += kPreBlock) {
@@ -426,7 +425,9 @@ k_preprocess(Ctx c, int max_k) {
             fc.verts = f.verts;
             s_fc[tid] = fc;
         }
+        if (round == 0) asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
+        if (round == 0) op0 = sigmoid_spec(s_rows[10 * kPreG + g]);
         const int f0 = slot * kPreFB;
         if (valid && f0 < nr) {
             // Eq. 1 for kPreFB frames: v = g0, then v = fma(psi_k, dG_k, v) for k ascending in

@@ -111,6 +111,21 @@ def tangent_batch(mask=synth.MASK_MEAN_SCALE_COLOR, seed=81):
     return synth.make_batch([m], fr, seed, jitter_deg=20, random_bg=True)
 
 
+def odd_k_batch():
+    """Blendshape counts that are not multiples of four (7 and 3, one channel mask: the compiled
+    instance; the blend takes the weights four at a time and the rest one by one)."""
+    ms = [synth.make_model(83, 2500, 7), synth.make_model(84, 1800, 3)]
+    fr = [synth.Frame(0, 96, 96), synth.Frame(1, 80, 112), synth.Frame(0, 64, 64)]
+    return synth.make_batch(ms, fr, seed=83, jitter_deg=12, random_bg=True)
+
+
+def odd_k_mixed_batch():
+    """K = 5 and K = 1 with different channel masks (the run-time-mask instance)."""
+    ms = [synth.make_model(85, 2200, 5, mask=synth.MASK_PAPER), synth.make_model(86, 2000, 1, mask=MASK_MEAN_COLOR)]
+    fr = [synth.Frame(0, 96, 80), synth.Frame(1, 96, 96)]
+    return synth.make_batch(ms, fr, seed=85, jitter_deg=12, random_bg=True)
+
+
 CASES = {
     "single_128": (lambda: synth.workload_single(), (16, 16), 64),
     "gradcheck_64": (lambda: synth.workload_gradcheck(), (16, 16), 256),
@@ -125,6 +140,8 @@ CASES = {
     "dense_lists": (dense_batch, (16, 16), 64),
     "tangent": (tangent_batch, (16, 16), 64),
     "tangent_paper_mask": (lambda: tangent_batch(synth.MASK_PAPER, 82), (8, 32), 128),
+    "odd_k": (odd_k_batch, (16, 16), 64),
+    "odd_k_mixed": (odd_k_mixed_batch, (8, 32), 64),
 }
 
 
