@@ -241,6 +241,13 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter(Ctx c) {
         }
 }
 
+// Asynchronous 8-byte copy global -> shared (both addresses 8-byte aligned), completed by
+// cp.async.wait_all.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+                 :: "r"(static_cast<unsigned>(__cvta_generic_to_shared(dst))), "l"(src) : "memory");
+}
+
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadixCap = 8192;                  // keys a segment may have for the shared-memory radix sort
@@ -437,37 +444,57 @@ __device__ unsigned long long *bucket_sort(unsigned long long *a, unsigned long 
 // on the depth bits only, which leaves runs of equal depth in list order, and a tie pass orders
 // each such run by index (insertion sort by the run's first thread). A bucket longer than
 // kBucketRun or a run longer than kTieRun sends the segment to a full-key sort: radix passes on
-// the index bits, then on the depth bits. The next work item is claimed while the current one
-// is sorted.
+// the index bits, then on the depth bits.
+// The sort is bound by round trips to memory, so none of them waits on another: thread 0 claims
+// work items three ahead and, one stage per item, loads the claimed item's tile id and then its
+// list bounds while the CTA sorts the current segment; a segment that fits in shared memory
+// arrives there by asynchronous copies, all in flight at once.
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
     extern __shared__ unsigned long long s_keys[];  // [kRadixCap] x 2, counts, ranks
     unsigned *s_cnt = reinterpret_cast<unsigned *>(s_keys + 2 * kRadixCap);
     unsigned short *s_rank = reinterpret_cast<unsigned short *>(s_cnt + kSortWarps * 256 + kSortWarps);
-    __shared__ unsigned s_w, s_dmin, s_dmax, s_imax, s_long;
+    __shared__ unsigned s_cur, s_st, s_L, s_dmin, s_dmax, s_imax, s_long;
     pdl_enter();
     if (c.cnt->overflow) return;
     const unsigned n_work = c.cnt->n_work;
+    // thread 0's pipeline: w1 / t1 the next item and its tile, w2 the item after it
+    unsigned w1 = 0, t1 = 0, w2 = 0;
     if (threadIdx.x == 0) {
-        s_w = atomicAdd(&c.cnt->next_sort, 1u);
+        const unsigned w0 = atomicAdd(&c.cnt->next_sort, 1u);
+        w1 = atomicAdd(&c.cnt->next_sort, 1u);
+        w2 = atomicAdd(&c.cnt->next_sort, 1u);
+        const unsigned t0 = w0 < n_work ? c.work[w0] : 0u;
+        t1 = w1 < n_work ? c.work[w1] : 0u;
+        s_cur = w0 < n_work ? 1u : 0u;
+        s_st = w0 < n_work ? c.tile_start[t0] : 0u;
+        s_L = w0 < n_work ? c.tile_start[t0 + 1] - s_st : 0u;
         s_dmin = 0xffffffffu;
         s_dmax = 0u;
         s_imax = 0u;
         s_long = 0u;
     }
     __syncthreads();
-    while (true) {
-        const unsigned w = s_w;
-        if (w >= n_work) break;
-        unsigned nxt = 0;
-        if (threadIdx.x == 0) nxt = atomicAdd(&c.cnt->next_sort, 1u);
-        const unsigned t = c.work[w];
-        const unsigned st = c.tile_start[t], L = c.tile_start[t + 1] - st;
+    while (s_cur) {
+        const unsigned st = s_st, L = s_L;
+        unsigned nst = 0, nend = 0, t2 = 0, w3 = 0;
+        if (threadIdx.x == 0) {  // consumed at the end of this segment and at the next one
+            if (w1 < n_work) {
+                nst = c.tile_start[t1];
+                nend = c.tile_start[t1 + 1];
+            }
+            t2 = w2 < n_work ? c.work[w2] : 0u;
+            w3 = atomicAdd(&c.cnt->next_sort, 1u);
+        }
         const unsigned long long *g = c.keys + st;
         const bool in_smem = L <= (unsigned)kRadixCap;
         unsigned dmin = 0xffffffffu, dmax = 0u, imax = 0u;
+        if (in_smem) {
+            for (unsigned e = threadIdx.x; e < L; e += blockDim.x) cp_async8(s_keys + e, g + e);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncthreads();
+        }
         for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
-            const unsigned long long k = g[e];
-            if (in_smem) s_keys[e] = k;  // read once; compressed in place below
+            const unsigned long long k = in_smem ? s_keys[e] : g[e];
             const unsigned d = (unsigned)(k >> 32), i = (unsigned)k;
             dmin = min(dmin, d);
             dmax = max(dmax, d);
@@ -535,7 +562,12 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
         for (unsigned e = threadIdx.x; e < L; e += blockDim.x) c.sorted[st + e] = (unsigned)res[e];
         __syncthreads();
         if (threadIdx.x == 0) {
-            s_w = nxt;
+            s_cur = w1 < n_work ? 1u : 0u;
+            s_st = nst;
+            s_L = nend - nst;
+            w1 = w2;
+            t1 = t2;
+            w2 = w3;
             s_dmin = 0xffffffffu;
             s_dmax = 0u;
             s_imax = 0u;
