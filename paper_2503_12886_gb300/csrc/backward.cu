@@ -9,8 +9,11 @@
 //                dG0[ch][i]    += sum_b dG_b[ch][i]
 //                ddG[k][a][i]  += sum_b psi_b[k] dG_b[ch_a][i]
 //                dpsi_b[k]     partial = sum_{a, i in chunk} dG_k[a][i] dG_b[ch_a][i]
-// The reduction over frames happens in registers in a fixed order, so dG0 and ddG are
-// deterministic; dpsi partials go to a [frame][k][chunk] buffer that a second kernel sums.
+//                the last two as TF32 tensor-core products at FP32 accuracy (three products
+//                of split operands).
+// Every sum runs in a fixed order (dG0 in registers, the products tile by tile, the warps'
+// dpsi sums in warp order), so the results are deterministic; dpsi partials go to a
+// [frame][k][chunk] buffer that a second kernel sums.
 #include <type_traits>
 
 #include "rgba_internal.cuh"
@@ -273,10 +276,8 @@ __device__ __forceinline__ bool tbn_fast(const ModelInfo &m, const float *__rest
 // memory asynchronously at the start. Meanwhile the chain rule per (frame, Gaussian) turns the
 // 2-D gradients into dL/dG_b over the 14 channels, straight into shared memory (each item
 // reads only its cache and 2-D gradients: the cache carries the opacity and whether the
-// Gaussian was kept); then the adjoint of Eq. 1 reduces them over the frames. A warp takes two adjacent
-// blendshapes k, k+1 at a time with the 16 frames' weights psi_b[k], psi_b[k+1] in registers,
-// so each dG_b value read from shared memory feeds four FMAs; its dpsi partials (16 frames x 2
-// blendshapes per lane) are summed over the warp by a shuffle reduce-scatter.
+// Gaussian was kept); then the adjoint of Eq. 1 reduces them over the frames: dG0 by plain
+// sums, ddG and the dpsi partials as tensor-core products (below).
 // Asynchronous 16-byte copy global -> shared (both addresses 16-byte aligned), completed by
 // cp.async.wait_all.
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -286,34 +287,41 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 
 constexpr int kFG2 = 16;
 constexpr int kWarps = kBwdThreads / 32;
+// Shared-memory strides in floats: a frame's 14 x 32 blended-channel gradients, and a staged
+// blendshape row of 32 Gaussians, each padded by 4 so that the tensor-core fragment loads,
+// which step over frames or blendshapes, fall in different banks (stride = 4 mod 32).
+constexpr int kDGF = kNch * kBwdChunk + 4;
+constexpr int kDgRow = kBwdChunk + 4;
 
-// Sum of v[j] over the 32 lanes for j = 0..15, by recursive halving: after the call lane l
-// holds the total of j = l >> 1 in v[0] (lanes 2j and 2j+1 both hold it).
-__device__ __forceinline__ float warp_reduce_scatter16(float v[16], int lane) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {  // xor 16: keep the half selected by bit 4
-        const bool hi = lane & 16;
-        const float send = hi ? v[j] : v[j + 8], keep = hi ? v[j + 8] : v[j];
-        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {  // xor 8: bit 3
-        const bool hi = lane & 8;
-        const float send = hi ? v[j] : v[j + 4], keep = hi ? v[j + 4] : v[j];
-        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {  // xor 4: bit 2
-        const bool hi = lane & 4;
-        const float send = hi ? v[j] : v[j + 2], keep = hi ? v[j + 2] : v[j];
-        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    {  // xor 2: bit 1
-        const bool hi = lane & 2;
-        const float send = hi ? v[0] : v[1], keep = hi ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+// The adjoint of Eq. 1 is two small dense products per chunk and group of frames (ddG: the
+// K x 16 weights times the 16 x (A 32) blended-channel gradients; dpsi: the 16 x (A 32)
+// gradients times the (A 32) x K blendshape rows), done on the tensor cores as
+// m16n8k8 TF32 matrix multiply-accumulates with FP32 accumulators. Each FP32 operand x is split
+// into x_hi = tf32(x) and x_lo = tf32(x - x_hi), and a b is accumulated as
+// a_lo b_hi + a_hi b_lo + a_hi b_hi (the a_lo b_lo term is below FP32 rounding), which keeps
+// the products at FP32 accuracy. Fragment layout (m16n8k8, A row-major, B column-major), with
+// g = lane / 4 and t = lane % 4: A elements (g, t), (g + 8, t), (g, t + 4), (g + 8, t + 4);
+// B elements (t, g), (t + 4, g); C elements (g, 2t), (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1).
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+    const float r = x - __uint_as_float(hi);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
+__device__ __forceinline__ void mma_tf32(float d[4], const unsigned a[4], const unsigned b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// d += a b at FP32 accuracy from split operands (small terms first)
+__device__ __forceinline__ void mma_3xtf32(float d[4], const unsigned ah[4], const unsigned al[4],
+                                           const unsigned bh[2], const unsigned bl[2]) {
+    mma_tf32(d, al, bh);
+    mma_tf32(d, ah, bl);
+    mma_tf32(d, ah, bh);
 }
 
 // 2 CTAs per SM: without the TBN mapping (unbound batches) the chain rule fits without spills
@@ -339,15 +347,17 @@ template <bool ADAM, bool BOUND>
 __global__ void __launch_bounds__(kBwdThreads, 2)
 k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
     extern __shared__ float smem[];
-    float *s_dG = smem;                                   // [16][14][32]
-    float *s_psi = s_dG + kFG2 * kNch * kBwdChunk;        // [16][max_k]
-    float *s_dgc = s_psi + kFG2 * max_k;                  // [k][A][32]: the chunk's blendshapes
+    float *s_dG = smem;                                   // [16][kDGF]: [14][32] per frame
+    float *s_psi = s_dG + kFG2 * kDGF;                    // [16][max_k]
+    float *s_dgc = s_psi + kFG2 * max_k;                  // [k][A][kDgRow]: the chunk's blendshapes
     __shared__ __align__(16) float s_g0[ADAM ? kNch * kBwdChunk : 1];  // ADAM: the G0 gradients
     __shared__ long long s_rec[kFG2];
     __shared__ int s_wh[kFG2][2];
     __shared__ const float *s_verts[kFG2];
     pdl_enter();
     __shared__ float s_fp[kFG2][RGBA_FP_STRIDE];
+    __shared__ int s_ch[kNch];               // the model's blended channels, by slot
+    __shared__ __align__(16) float s_red[kWarps * kFG2 * 32];  // dpsi: each warp's sums, 32 blendshapes
     const ModelInfo &m = c.models[blockIdx.y];
     const int chunk = blockIdx.x;
     const int i0 = chunk * kBwdChunk;
@@ -367,9 +377,10 @@ k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
         const int per_row = min(kBwdChunk, m.n_pad - i0) >> 2;  // n_pad, i0 multiples of 4
         for (int e = threadIdx.x; e < K * A * per_row; e += kBwdThreads) {
             const int rr = e / per_row, q = e - rr * per_row;
-            cp_async16(s_dgc + rr * kBwdChunk + 4 * q, m.dg + (size_t)rr * m.n_pad + i0 + 4 * q);
+            cp_async16(s_dgc + rr * kDgRow + 4 * q, m.dg + (size_t)rr * m.n_pad + i0 + 4 * q);
         }
     }
+    if (threadIdx.x < A) s_ch[threadIdx.x] = m.chans[threadIdx.x];
     for (int g0 = 0; g0 < m.nb; g0 += kFG2) {
         const int ng = min(kFG2, m.nb - g0);
         if (threadIdx.x < ng) {
@@ -431,7 +442,7 @@ k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < kNch; ++q) s_dG[(fl * kNch + q) * kBwdChunk + li] = dG[q];
+                for (int q = 0; q < kNch; ++q) s_dG[fl * kDGF + q * kBwdChunk + li] = dG[q];
                 if (c.grad_blended && fl < ng && i0 + li < m.n_pad) {  // rgba_render_bwd's optional output
                     float *o = c.grad_blended + s_rec[fl] * kNch + i0 + li;
 #pragma unroll
@@ -455,7 +466,7 @@ k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
         if ((ADAM ? am.p0 != nullptr : m.gg0 != nullptr) && in_pad) {
             for (int ch = warp; ch < kNch; ch += kWarps) {
                 float a = 0.f;
-                for (int fl = 0; fl < ng; ++fl) a += s_dG[(fl * kNch + ch) * kBwdChunk + lane];
+                for (int fl = 0; fl < ng; ++fl) a += s_dG[fl * kDGF + ch * kBwdChunk + lane];
                 const size_t o = (size_t)ch * m.n_pad + i;
                 if (ADAM) {  // parked for the update below, exactly as the separate update reads it
                     s_g0[ch * kBwdChunk + lane] = 0.f + a;
@@ -464,54 +475,101 @@ k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
                 }
             }
         }
-        // ddG[k][a][i] = sum_b psi_b[k] dG_b[ch_a][i];  dpsi_b[k] partial = sum_a,i dG_k[a][i] dG_b[ch_a][i]
-        for (int kk = 2 * warp; kk < K; kk += 2 * kWarps) {
-            const bool two = kk + 1 < K;
-            float p0[kFG2], p1[kFG2], s0[kFG2], s1[kFG2];
+        const int grp = lane >> 2, tig = lane & 3;
+        // dpsi_b[k] partial = sum over a, i of dG_k[a][i] dG_b[ch_a][i]: D (frames x k) =
+        // A (frames x columns) B (columns x k), a column being (channel slot a, Gaussian i) and
+        // 8 columns one k-step; the warps split the k-steps, their sums meet in s_red
+        if (c.grad_psi) {
+            const int KS = A * (kBwdChunk / 8);
+            for (int kb = 0; kb < K; kb += 32) {
+                float acc[4][4];
 #pragma unroll
-            for (int fl = 0; fl < kFG2; ++fl) {
-                p0[fl] = s_psi[fl * max_k + kk];
-                p1[fl] = two ? s_psi[fl * max_k + kk + 1] : 0.f;
-                s0[fl] = 0.f;
-                s1[fl] = 0.f;
-            }
-            for (int a = 0; a < A; ++a) {
-                const int ch = m.chans[a];
-                const size_t off0 = ((size_t)kk * A + a) * m.n_pad + i;
-                const size_t off1 = off0 + (size_t)A * m.n_pad;
-                // padding columns hold whatever the caller left there: zero them
-                const float dg0 = valid ? s_dgc[(kk * A + a) * kBwdChunk + lane] : 0.f;
-                const float dg1 = (valid && two) ? s_dgc[((kk + 1) * A + a) * kBwdChunk + lane] : 0.f;
-                float acc0 = 0.f, acc1 = 0.f;
+                for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+                for (int ks = warp; ks < KS; ks += kWarps) {
+                    const int sa = ks / (kBwdChunk / 8), ib = (ks % (kBwdChunk / 8)) * 8;
+                    const float *dg = s_dG + s_ch[sa] * kBwdChunk + ib;  // + frame * kDGF
+                    unsigned ah[4], al[4];
+                    split_tf32(dg[grp * kDGF + tig], ah[0], al[0]);
+                    split_tf32(dg[(grp + 8) * kDGF + tig], ah[1], al[1]);
+                    split_tf32(dg[grp * kDGF + tig + 4], ah[2], al[2]);
+                    split_tf32(dg[(grp + 8) * kDGF + tig + 4], ah[3], al[3]);
+                    // padding columns hold whatever the caller left there: zero them
+                    const bool v0 = i0 + ib + tig < m.n, v1 = i0 + ib + tig + 4 < m.n;
 #pragma unroll
-                for (int fl = 0; fl < kFG2; ++fl) {
-                    const float d = s_dG[(fl * kNch + ch) * kBwdChunk + lane];
-                    acc0 = fmaf(p0[fl], d, acc0);
-                    acc1 = fmaf(p1[fl], d, acc1);
-                    s0[fl] = fmaf(dg0, d, s0[fl]);
-                    s1[fl] = fmaf(dg1, d, s1[fl]);
-                }
-                if (ADAM) {
-                    // this lane was the staged value's only reader: the slot now parks the gradient
-                    s_dgc[(kk * A + a) * kBwdChunk + lane] = 0.f + acc0;
-                    if (two) s_dgc[((kk + 1) * A + a) * kBwdChunk + lane] = 0.f + acc1;
-                } else if (m.gdg && in_pad) {
-                    float *o = m.gdg + off0;
-                    *o = (g0 == 0 ? 0.f : *o) + acc0;
-                    if (two) {
-                        o = m.gdg + off1;
-                        *o = (g0 == 0 ? 0.f : *o) + acc1;
+                    for (int j = 0; j < 4; ++j) {
+                        const int kk = kb + j * 8 + grp;
+                        const float *bs = s_dgc + ((size_t)kk * A + sa) * kDgRow + ib + tig;
+                        unsigned bh[2], bl[2];
+                        split_tf32(kk < K && v0 ? bs[0] : 0.f, bh[0], bl[0]);
+                        split_tf32(kk < K && v1 ? bs[4] : 0.f, bh[1], bl[1]);
+                        mma_3xtf32(acc[j], ah, al, bh, bl);
                     }
                 }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {  // this warp's sums, then the warps' in a fixed order
+                    float *r = s_red + warp * (kFG2 * 32) + grp * 32 + j * 8 + 2 * tig;
+                    *reinterpret_cast<float2 *>(r) = make_float2(acc[j][0], acc[j][1]);
+                    *reinterpret_cast<float2 *>(r + 8 * 32) = make_float2(acc[j][2], acc[j][3]);
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < kFG2 * 32; e += kBwdThreads) {
+                    const int fl = e >> 5, kk = kb + (e & 31);
+                    float t = 0.f;
+#pragma unroll
+                    for (int w = 0; w < kWarps; ++w) t += s_red[w * (kFG2 * 32) + e];
+                    if (fl < ng && kk < K)
+                        c.dpsi_part[m.dpsi_off + ((long long)(g0 + fl) * K + kk) * m.n_chunks + chunk] = t;
+                }
+                __syncthreads();
             }
-            if (c.grad_psi) {
-                const float t0 = warp_reduce_scatter16(s0, lane);
-                const float t1 = warp_reduce_scatter16(s1, lane);
-                const int fl = lane >> 1;
-                if ((lane & 1) == 0 && fl < ng) {
-                    float *dp = c.dpsi_part + m.dpsi_off + ((long long)(g0 + fl) * K + kk) * m.n_chunks + chunk;
-                    dp[0] = t0;
-                    if (two) dp[m.n_chunks] = t1;
+        }
+        // ddG[k][a][i] = sum_b psi_b[k] dG_b[ch_a][i]: D (k x columns) = A (k x frames)
+        // B (frames x columns), two k-steps of 8 frames; the warps split the 8-column tiles
+        if (ADAM ? true : m.gdg != nullptr) {
+            const int NT = A * (kBwdChunk / 8);
+            for (int mb = 0; mb < K; mb += 16) {
+                const int k0 = mb + grp, k1 = k0 + 8;
+                unsigned ah[2][4], al[2][4];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int f0 = q * 8 + tig, f1 = f0 + 4;
+                    split_tf32(k0 < K ? s_psi[f0 * max_k + k0] : 0.f, ah[q][0], al[q][0]);
+                    split_tf32(k1 < K ? s_psi[f0 * max_k + k1] : 0.f, ah[q][1], al[q][1]);
+                    split_tf32(k0 < K ? s_psi[f1 * max_k + k0] : 0.f, ah[q][2], al[q][2]);
+                    split_tf32(k1 < K ? s_psi[f1 * max_k + k1] : 0.f, ah[q][3], al[q][3]);
+                }
+                for (int nt = warp; nt < NT; nt += kWarps) {
+                    const int sa = nt / (kBwdChunk / 8), ib = (nt % (kBwdChunk / 8)) * 8;
+                    const float *dg = s_dG + s_ch[sa] * kBwdChunk + ib + grp;
+                    float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        unsigned bh[2], bl[2];
+                        split_tf32(dg[(q * 8 + tig) * kDGF], bh[0], bl[0]);
+                        split_tf32(dg[(q * 8 + tig + 4) * kDGF], bh[1], bl[1]);
+                        mma_3xtf32(d, ah[q], al[q], bh, bl);
+                    }
+                    const int i = ib + 2 * tig;  // columns i, i + 1 of rows k0 and k1
+                    if (ADAM) {
+                        // s_dgc is no longer read (dpsi is done): its slots park the gradients
+                        if (k0 < K) {
+                            s_dgc[((size_t)k0 * A + sa) * kDgRow + i] = 0.f + d[0];
+                            s_dgc[((size_t)k0 * A + sa) * kDgRow + i + 1] = 0.f + d[1];
+                        }
+                        if (k1 < K) {
+                            s_dgc[((size_t)k1 * A + sa) * kDgRow + i] = 0.f + d[2];
+                            s_dgc[((size_t)k1 * A + sa) * kDgRow + i + 1] = 0.f + d[3];
+                        }
+                    } else if (i0 + i < m.n_pad) {  // n_pad - i0 is a multiple of 4: i + 1 too
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int kk = h ? k1 : k0;
+                            if (kk >= K) continue;
+                            float2 *o = reinterpret_cast<float2 *>(m.gdg + ((size_t)kk * A + sa) * m.n_pad + i0 + i);
+                            const float2 old = g0 == 0 ? make_float2(0.f, 0.f) : *o;
+                            *o = make_float2(old.x + d[2 * h], old.y + d[2 * h + 1]);
+                        }
+                    }
                 }
             }
         }
@@ -547,7 +605,7 @@ k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
                 const bool base = row < rows0;
                 const int rr = base ? row : row - rows0;
                 const size_t off = (size_t)rr * m.n_pad + i0 + 4 * c4;
-                const float4 g = *reinterpret_cast<const float4 *>((base ? s_g0 : s_dgc) + rr * kBwdChunk + 4 * c4);
+                const float4 g = *reinterpret_cast<const float4 *>((base ? s_g0 + rr * kBwdChunk : s_dgc + rr * kDgRow) + 4 * c4);
                 const float lr = base ? am.lr0[rr] : am.lrd[rr % A];
                 float p4[4] = {pp[u].x, pp[u].y, pp[u].z, pp[u].w}, m4[4] = {mm[u].x, mm[u].y, mm[u].z, mm[u].w},
                       v4[4] = {vv[u].x, vv[u].y, vv[u].z, vv[u].w};
@@ -598,7 +656,7 @@ namespace {
 template <bool ADAM, bool BOUND>
 cudaError_t gauss_bwd_inst(const Ctx &c, int max_chunks, int max_k, int max_ka, const AdamArg<ADAM> &fa,
                            cudaStream_t s) {
-    auto bytes = [](int k, int ka) { return (kFG2 * kNch * kBwdChunk + kFG2 * k + ka * kBwdChunk) * (int)sizeof(float); };
+    auto bytes = [](int k, int ka) { return (kFG2 * kDGF + kFG2 * k + ka * kDgRow) * (int)sizeof(float); };
     // set once, at the largest size any batch can ask for, so no attribute call happens while
     // a stream is being captured
     static int attr_device = -1;
