@@ -43,9 +43,10 @@ __global__ void k_adam(AdamChunk ch, float b1, float b2, float eps, float ibc1, 
     const long long rows0 = kNch, rowsd = (long long)M.k * M.A;
     const long long q4 = M.n_pad / 4;                  // float4s per row
     const long long total = (rows0 + rowsd) * q4;
+    const bool narrow = total + (long long)gridDim.x * blockDim.x < 0xffffffffLL;  // 32-bit division
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const long long row = e / q4;
+        const long long row = narrow ? (long long)((unsigned)e / (unsigned)q4) : e / q4;
         if (row < rows0) {
             if (!M.p0) continue;
             float4 *p = reinterpret_cast<float4 *>(M.p0) + e;
@@ -60,7 +61,7 @@ __global__ void k_adam(AdamChunk ch, float b1, float b2, float eps, float ibc1, 
         } else {
             if (!M.pd) continue;
             const long long ed = e - rows0 * q4;
-            const int a = (int)((row - rows0) % M.A);
+            const int a = (int)((unsigned)(row - rows0) % (unsigned)M.A);
             float4 *p = reinterpret_cast<float4 *>(M.pd) + ed;
             float4 *m = reinterpret_cast<float4 *>(M.md) + ed;
             float4 *v = reinterpret_cast<float4 *>(M.vd) + ed;
