@@ -164,7 +164,7 @@ int make_plan(const rgba_batch *b, Plan &p) {
     L.models = take(sizeof(ModelInfo) * (size_t)M);
     L.frames = take(sizeof(FrameInfo) * (size_t)B);
     L.mframes = take(sizeof(int) * (size_t)B);
-    L.tile_count = take(4 * (size_t)T * (1 + kSubCounters));
+    L.tile_count = take((size_t)tc_bytes(T));
     L.tile_start = take(4 * (size_t)(T + 1));
     L.cursor = take(4 * (size_t)T * kSubCounters);
     L.work = take(4 * (size_t)T);
@@ -218,6 +218,7 @@ Ctx make_ctx(const Layout &L, unsigned char *ws, const rgba_batch *b) {
     c.grad_psi = b->grad_psi;
     c.cnt = reinterpret_cast<Counters *>(ws + L.counters);
     c.tile_count = reinterpret_cast<unsigned *>(ws + L.tile_count);
+    c.tc_mask = (unsigned)(tc_pow2(L.T) - 1);
     c.tile_start = reinterpret_cast<unsigned *>(ws + L.tile_start);
     c.cursor = reinterpret_cast<unsigned *>(ws + L.cursor);
     c.work = reinterpret_cast<unsigned *>(ws + L.work);
@@ -320,7 +321,7 @@ int memset_async(void *p, size_t bytes, cudaStream_t s, const char *what) {
 
 int do_preprocess(rgba_ctx_t ctx, Call &k) {
     int rc;
-    const size_t count_bytes = 4 * (size_t)k.p.L.T * (1 + kSubCounters);
+    const size_t count_bytes = (size_t)tc_bytes(k.p.L.T);
     {  // tables, counters and tile counts in one launch when the tables fit its parameters
         const Layout &L = k.p.L;
         PrologueArgs a{};

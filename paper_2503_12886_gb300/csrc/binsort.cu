@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(kScanTile) k_scan_blocks(Ctx c) {
     const long long t = (long long)blockIdx.x * kScanTile + threadIdx.x;
     unsigned v = 0;
     if (t < c.T) {
-        const unsigned *sub = c.tile_count + c.T + t * kSubCounters;
-        v = c.tile_count[t];
+        const unsigned *sub = c.tile_count + tc_sub_base(c.tc_mask) + t * kSubCounters;
+        v = c.tile_count[tc_word(c.tc_mask, t)];
 #pragma unroll
         for (int q = 0; q < kSubCounters; ++q) {
             c.cursor[t * kSubCounters + q] = v;

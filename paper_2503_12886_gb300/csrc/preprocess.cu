@@ -303,14 +303,14 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const ModelInfo &
         // tiles keep the slot each count returns, so the scatter needs no atomics
         const int rw = ix1 - ix0, area = rw * (iy1 - iy0);
         if (area <= kRankSlots) {
-            unsigned *tc = c.tile_count + f.tile_base + iy0 * f.tiles_x + ix0;
+            const long long t0 = (long long)f.tile_base + iy0 * f.tiles_x + ix0;
             unsigned rk[kRankSlots];
-            int ox = 0, off = 0;  // slot q is tile (ix0 + ox, iy0 + q / rw), off its offset from tc
+            int ox = 0, off = 0;  // slot q is tile (ix0 + ox, iy0 + q / rw), off its offset from t0
 #pragma unroll
             for (int q = 0; q < kRankSlots; ++q) {
                 rk[q] = 0u;
                 if (q < area) {
-                    rk[q] = atomicAdd(tc + off, 1u);
+                    rk[q] = atomicAdd(c.tile_count + tc_word(c.tc_mask, t0 + off), 1u);
                     ++off;
                     if (++ox == rw) {
                         ox = 0;
@@ -322,7 +322,8 @@ __device__ __forceinline__ void decide_and_write(const Ctx &c, const ModelInfo &
             rp[0] = make_uint4(rk[0], rk[1], rk[2], rk[3]);
             rp[1] = make_uint4(rk[4], rk[5], rk[6], rk[7]);
         } else {  // spread over kSubCounters counters per tile, chosen by the Gaussian index
-            unsigned *tb = c.tile_count + c.T + (size_t)f.tile_base * kSubCounters + (r & (kSubCounters - 1));
+            unsigned *tb = c.tile_count + tc_sub_base(c.tc_mask) + (size_t)f.tile_base * kSubCounters +
+                           (r & (kSubCounters - 1));
             for (int ty = iy0; ty < iy1; ++ty)
                 for (int tx = ix0; tx < ix1; ++tx) atomicAdd(tb + (size_t)(ty * f.tiles_x + tx) * kSubCounters, 1u);
         }
