@@ -366,7 +366,7 @@ int rgba_color_init(rgba_ctx_t ctx, const rgba_batch *batch, void *ws, size_t ws
  *    Gaussian records) does not fit the block returns RGBA_ERR_INVALID_ARG before anything is
  *    enqueued. The block holds the full rgba_step layout, so roughly 208 bytes per Gaussian
  *    record (a frame's record count is its model's n_pad; 20 of them are the one pair per record
- *    that must fit) + 32 bytes per pixel + 80 bytes per tile must fit in 64 MiB: one 512x512
+ *    that must fit) + 32 bytes per pixel + 110-140 bytes per tile must fit in 64 MiB: one 512x512
  *    frame of a 100,000-Gaussian avatar (about 29 MB) or two of them fit, three do not; 16
  *    frames of 512x512 of a 60,000-Gaussian avatar need about 335 MB and are rejected. More
  *    pairs than fit in what is left return RGBA_ERR_CAPACITY with out->pairs_needed set (the
