@@ -982,7 +982,9 @@ def run_serve(local_rank, seconds):
     avatars = synth.serving_avatars()
     trace = synth.serving_requests(duration_s=seconds)
     srv = Server(avatars, local_rank, hbm_budget=40e9, max_frames=32, slots=3, max_res=1024)
-    warm = requests_from_trace(synth.serving_requests(seed=77, duration_s=0.2), avatars, 77)
+    # one second of other arrivals first: every kernel instance and slot shape the trace can
+    # use has run before the measured second starts
+    warm = requests_from_trace(synth.serving_requests(seed=77, duration_s=1.0), avatars, 77)
     srv.run(warm, realtime=True)
     st = srv.run(requests_from_trace(trace, avatars), realtime=True)
     pf = srv.run_per_frame(requests_from_trace(trace, avatars), realtime=True)
