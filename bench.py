@@ -338,6 +338,35 @@ def run_ours(args, rank, world, local_rank):
                 # runs the same collectives
                 return
 
+    done_ev = [torch.cuda.Event() for _ in dbs]
+
+    def run_steps(steps):
+        """`steps` steps with each step's one host synchronisation (its loss, pair count and
+        overflow flag) taken while the next step runs, so the GPU never waits for the host
+        between steps; a step that overflowed grows the workspace and, on one rank, is
+        replayed (with the step after it, which ran with the old workspace)."""
+        pending = None
+        for i in range(steps):
+            j = i % len(cap["graphs"])
+            replay(j)
+            done_ev[j].record(s)
+            if pending is not None:
+                done_ev[pending].synchronize()
+                if overflowed(pending):
+                    s.synchronize()
+                    for jj in ((pending, j) if world == 1 else (pending,)):
+                        while overflowed(jj):
+                            regrow(jj)
+                            if world > 1:
+                                break
+                            replay(jj)
+                            s.synchronize()
+            pending = j
+        if pending is not None:
+            done_ev[pending].synchronize()
+            if overflowed(pending):
+                step(pending)
+
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     with torch.cuda.stream(s):
@@ -356,8 +385,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        for i in range(args.steps):
-            step(i)
+        run_steps(args.steps)
         e1.record(s)
         torch.cuda.synchronize()
     ck = clocks.stop()
