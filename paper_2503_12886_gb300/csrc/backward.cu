@@ -299,8 +299,9 @@ constexpr int kDgRow = kBwdChunk + 4;
 // m16n8k8 TF32 matrix multiply-accumulates with FP32 accumulators. Each FP32 operand x is split
 // into x_hi = tf32(x) and x_lo = tf32(x - x_hi), and a b is accumulated as
 // a_lo b_hi + a_hi b_lo + a_hi b_hi (the a_lo b_lo term is below FP32 rounding), which keeps
-// the products at FP32 accuracy. Fragment layout (m16n8k8, A row-major, B column-major), with
-// g = lane / 4 and t = lane % 4: A elements (g, t), (g + 8, t), (g, t + 4), (g + 8, t + 4);
+// the products at FP32 accuracy (the split-operand scheme of Ootomo and Yokota, "Recovering
+// single precision accuracy from Tensor Cores", 2022). Fragment layout (m16n8k8, A row-major,
+// B column-major), with g = lane / 4 and t = lane % 4: A elements (g, t), (g + 8, t), (g, t + 4), (g + 8, t + 4);
 // B elements (t, g), (t + 4, g); C elements (g, 2t), (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1).
 __device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));

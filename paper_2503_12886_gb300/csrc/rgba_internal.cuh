@@ -43,8 +43,8 @@ constexpr int kSubCounters = 8;  // per-tile counters for larger rectangles (by 
 // the tiles a face covers. Stored side by side, those counters share a few L2 slices, whose
 // atomic units then set the preprocess's pace (it varied by 30 % with the counters' offset). So
 // each tile's ranked count has its own 32-byte sector, at a slot given by an odd multiplier
-// modulo a power of two (a bijection that scatters neighbouring tiles), and the sub-counters
-// follow the slots.
+// modulo a power of two (Knuth's multiplicative hashing with the golden-ratio constant: a
+// bijection that scatters neighbouring tiles), and the sub-counters follow the slots.
 constexpr int kTcWords = 8;
 __host__ __device__ inline long long tc_pow2(long long T) {
     long long p = 1;
