@@ -126,6 +126,14 @@ def odd_k_mixed_batch():
     return synth.make_batch(ms, fr, seed=85, jitter_deg=12, random_bg=True)
 
 
+def many_tiles_batch():
+    """17 frames of 512x512 at 16x16 tiles: 17,408 tiles over 17 scan CTAs, a batch with more
+    tiles than the 16-frame workload, every tile list and pixel compared."""
+    m = synth.make_model(87, 3000, 8)
+    return synth.make_batch([m], [synth.Frame(0, 512, 512) for _ in range(17)], seed=87, jitter_deg=15,
+                            random_bg=True)
+
+
 CASES = {
     "single_128": (lambda: synth.workload_single(), (16, 16), 64),
     "gradcheck_64": (lambda: synth.workload_gradcheck(), (16, 16), 256),
@@ -142,6 +150,7 @@ CASES = {
     "tangent_paper_mask": (lambda: tangent_batch(synth.MASK_PAPER, 82), (8, 32), 128),
     "odd_k": (odd_k_batch, (16, 16), 64),
     "odd_k_mixed": (odd_k_mixed_batch, (8, 32), 64),
+    "many_tiles": (many_tiles_batch, (16, 16), 64),
 }
 
 
