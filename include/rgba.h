@@ -56,7 +56,7 @@ typedef enum {
     RGBA_ERR_CUDA = 3,         /* a CUDA runtime call failed; see rgba_last_error() */
     RGBA_ERR_TIMEOUT = 4,      /* a bounded device wait gave up; the results are invalid (reserved:
                                   no kernel of this library waits on another's progress) */
-    RGBA_ERR_UNSUPPORTED = 5   /* valid request outside what this build supports */
+    RGBA_ERR_UNSUPPORTED = 5   /* valid request outside what the library supports */
 } rgba_status;
 
 #define RGBA_NCH 14
