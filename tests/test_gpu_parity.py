@@ -126,6 +126,19 @@ def odd_k_mixed_batch():
     return synth.make_batch(ms, fr, seed=85, jitter_deg=12, random_bg=True)
 
 
+def closeup_batch():
+    """The camera 0.25 m and 0.22 m from the avatar's centre: the near plane (0.2 m) culls part
+    of the avatar, the rest spans more than the field of view, so the Jacobian's 1.3 x
+    half-fov clamp is active for many Gaussians (the decision spec's clamp and the backward's
+    blocked gradient on clamped coordinates), and the splats are large."""
+    m = synth.make_model(88, 4000, 8)
+    b = synth.make_batch([m], [synth.Frame(0, 128, 128), synth.Frame(0, 96, 128)], seed=88, jitter_deg=10,
+                         random_bg=True)
+    b.fparams[0, 11] = 0.25
+    b.fparams[1, 11] = 0.22
+    return b
+
+
 def many_tiles_batch():
     """17 frames of 512x512 at 16x16 tiles: 17,408 tiles over 17 scan CTAs, a batch with more
     tiles than the 16-frame workload, every tile list and pixel compared."""
@@ -151,6 +164,7 @@ CASES = {
     "odd_k": (odd_k_batch, (16, 16), 64),
     "odd_k_mixed": (odd_k_mixed_batch, (8, 32), 64),
     "many_tiles": (many_tiles_batch, (16, 16), 64),
+    "closeup": (closeup_batch, (16, 16), 64),
 }
 
 
