@@ -381,18 +381,18 @@ static_assert((1 << kBucketBits) + kSortWarps <= kSortWarps * 256 + kSortWarps, 
 // buckets), so the count costs little and is the same for every key of a bucket. A bucket
 // longer than kBucketRun sets *s_long and the keys are returned grouped by bucket for the
 // caller's fallback. Returns the buffer holding the result.
-__device__ unsigned long long *bucket_sort(unsigned long long *a, unsigned long long *b, int L, int db,
-                                           unsigned *s_hist /* >= 2^kBucketBits + kSortWarps */,
+__device__ unsigned long long *bucket_sort(unsigned long long *a, unsigned long long *b, int L, unsigned d0, int db,
+                                           unsigned *s_hist /* >= 2^kBucketBits + kSortWarps, zeroed */,
                                            unsigned short *s_rank, unsigned *s_long) {
     constexpr int NB = 1 << kBucketBits, PER = NB / kSortThreads;
     static_assert(NB % kSortThreads == 0, "whole buckets per thread");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int shift = 32 + max(0, db - kBucketBits);
+    const int bshift = max(0, db - kBucketBits);
+    // the bucket of a key: the top kBucketBits bits of its depth above the segment's minimum
+    auto bucket = [&](unsigned long long k) { return ((unsigned)(k >> 32) - d0) >> bshift; };
     unsigned *wsum = s_hist + NB;
-    for (int i = tid; i < NB; i += kSortThreads) s_hist[i] = 0u;
-    __syncthreads();
     for (int e = tid; e < L; e += kSortThreads)
-        s_rank[e] = (unsigned short)atomicAdd(&s_hist[(unsigned)(a[e] >> shift)], 1u);
+        s_rank[e] = (unsigned short)atomicAdd(&s_hist[bucket(a[e])], 1u);
     __syncthreads();
     {  // exclusive scan of the bucket counts; thread t owns buckets [t PER, (t+1) PER)
         unsigned v[PER], run = 0;
@@ -418,12 +418,12 @@ __device__ unsigned long long *bucket_sort(unsigned long long *a, unsigned long 
     __syncthreads();
     for (int e = tid; e < L; e += kSortThreads) {
         const unsigned long long k = a[e];
-        b[s_hist[(unsigned)(k >> shift)] + s_rank[e]] = k;
+        b[s_hist[bucket(k)] + s_rank[e]] = k;
     }
     __syncthreads();
     for (int p = tid; p < L; p += kSortThreads) {
         const unsigned long long k = b[p];
-        const unsigned bk = (unsigned)(k >> shift);
+        const unsigned bk = bucket(k);
         const int lo = (int)s_hist[bk], hi = bk + 1 < (unsigned)NB ? (int)s_hist[bk + 1] : L;
         if (hi - lo > kBucketRun) {
             *s_long = 1u;
@@ -490,6 +490,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
         unsigned dmin = 0xffffffffu, dmax = 0u, imax = 0u;
         if (in_smem) {
             for (unsigned e = threadIdx.x; e < L; e += blockDim.x) cp_async8(s_keys + e, g + e);
+            for (int i = threadIdx.x; i < (1 << kBucketBits); i += blockDim.x) s_cnt[i] = 0u;  // bucket counts
             asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
         }
@@ -516,21 +517,27 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
         const int db = 32 - __clz(s_dmax - d0);  // bits of the depth spread
         unsigned long long *a = in_smem ? s_keys : c.keys2 + st;
         unsigned long long *bb = in_smem ? s_keys + kRadixCap : c.keys + st;
-        for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
-            const unsigned long long k = in_smem ? a[e] : g[e];
-            a[e] = ((unsigned long long)((unsigned)(k >> 32) - d0) << 32) | (unsigned)k;
-        }
-        __syncthreads();
+        // the radix passes take keys compressed to (depth - d0) << 32 | index (the order is the
+        // same); the bucket sort reads the keys as they are
+        auto compress = [&](unsigned long long *dst, const unsigned long long *src) {
+            for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
+                const unsigned long long k = src[e];
+                dst[e] = ((unsigned long long)((unsigned)(k >> 32) - d0) << 32) | (unsigned)k;
+            }
+            __syncthreads();
+        };
         unsigned long long *res;
         if (in_smem) {
-            res = bucket_sort(a, bb, (int)L, db, s_cnt, s_rank, &s_long);
+            res = bucket_sort(a, bb, (int)L, d0, db, s_cnt, s_rank, &s_long);
             if (s_long) {  // a bucket too crowded for the fix-up: the full key by radix passes
+                compress(res, res);
                 unsigned long long *other = res == a ? bb : a;
                 res = radix_sort<true>(res, other, (int)L, 0, ib, s_cnt, s_rank);
                 other = res == a ? bb : a;
                 res = radix_sort<true>(res, other, (int)L, 32, 32 + db, s_cnt, s_rank);
             }
         } else {
+            compress(a, g);
             res = radix_sort<false>(a, bb, (int)L, 32, 32 + db, s_cnt, nullptr);
             // ties: a run keeps its depth under any reordering, so run starts found by other
             // threads do not change while a run is being ordered
