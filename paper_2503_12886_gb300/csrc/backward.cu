@@ -376,9 +376,14 @@ k_gauss_bwd(Ctx c, int max_k, AdamArg<ADAM> fa) {
     const FusedAdamModel &am = fa.m[ADAM ? blockIdx.y : 0];
     {  // the chunk's blendshape rows travel to shared memory while the chain rule runs
         const int per_row = min(kBwdChunk, m.n_pad - i0) >> 2;  // n_pad, i0 multiples of 4
-        for (int e = threadIdx.x; e < K * A * per_row; e += kBwdThreads) {
-            const int rr = e / per_row, q = e - rr * per_row;
+        auto copy = [&](int rr, int q) {
             cp_async16(s_dgc + rr * kDgRow + 4 * q, m.dg + (size_t)rr * m.n_pad + i0 + 4 * q);
+        };
+        if (per_row == kBwdChunk / 4) {  // a full chunk: thread t copies quad t % 8 of every 32nd row
+            for (int rr = threadIdx.x / (kBwdChunk / 4); rr < K * A; rr += kBwdThreads / (kBwdChunk / 4))
+                copy(rr, threadIdx.x % (kBwdChunk / 4));
+        } else {
+            for (int e = threadIdx.x; e < K * A * per_row; e += kBwdThreads) copy(e / per_row, e % per_row);
         }
     }
     if (threadIdx.x < A) s_ch[threadIdx.x] = m.chans[threadIdx.x];

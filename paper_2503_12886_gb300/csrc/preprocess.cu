@@ -388,10 +388,14 @@ k_preprocess(Ctx c, int max_k) {
     {  // 16-byte asynchronous copies of the chunk's rows by every thread; the first round's
        // frame tables below are gathered while they are in flight, then one wait
         const int per_row = cols >> 2;  // n_pad and i0 are multiples of 4
-        for (int e = tid; e < rows * per_row; e += kPreBlock) {
-            const int rr = e / per_row, q = e - rr * per_row;
+        auto copy = [&](int rr, int q) {
             const float *src = (rr < kNch ? m.g0 + (size_t)rr * m.n_pad : m.dg + (size_t)(rr - kNch) * m.n_pad) + i0 + 4 * q;
             cp_async16(s_rows + (size_t)rr * kPreG + 4 * q, src);
+        };
+        if (per_row == kPreG / 4) {  // a full chunk: thread t copies quad t % 8 of every 32nd row
+            for (int rr = tid / (kPreG / 4); rr < rows; rr += kPreBlock / (kPreG / 4)) copy(rr, tid % (kPreG / 4));
+        } else {
+            for (int e = tid; e < rows * per_row; e += kPreBlock) copy(e / per_row, e % per_row);
         }
     }
     const int g = tid % kPreG, slot = tid / kPreG;
