@@ -1,5 +1,5 @@
 """Edge cases of the CUDA path through the C ABI: empty batches, empty models, everything
-culled, tiny and ragged images, the largest frame and K, pair-buffer overflow with retry, and
+culled, the near-plane boundary, tiny and ragged images, the largest frame and K, pair-buffer overflow with retry, and
 tangent-space bindings with degenerate triangles or out-of-range indices."""
 import math
 
@@ -70,6 +70,31 @@ def test_everything_culled(renderer):
     assert out.pairs == 0
     assert float(db.models[0].grad_g0.abs().max()) == 0.0
     assert float(db.grad_psi.abs().max()) == 0.0
+
+
+def test_near_plane_boundary_matches_the_oracle(renderer):
+    """Gaussians exactly at, just in front of, just behind and well behind the near distance
+    (camera depths 0.25, 0.2501, 0.24, 0.5 against near = 0.25, exact in binary32): the kernel
+    culls the same ones as the oracle, bit for bit."""
+    n = 4
+    g0 = np.zeros((14, n), np.float32)
+    g0[2] = [-0.75, -0.7499, -0.76, -0.5]
+    g0[0] = [-0.01, 0.01, 0.0, 0.02]
+    g0[3] = 1.0
+    g0[7:10] = math.log(0.01)
+    g0[10] = 1.0
+    g0[11:14] = 0.5
+    m = synth.Model(n=n, k=1, mask=synth.MASK_MEAN_SCALE_COLOR, g0=g0, dg=np.zeros((1, 9, n), np.float32))
+    fp = synth.camera_params(64, 64, bg=(0.1, 0.2, 0.3))
+    fp[16] = 0.25
+    batch = synth.Batch(models=[m], frames=[synth.Frame(0, 64, 64)], psi=np.zeros((1, 1), np.float32),
+                        fparams=fp[None, :], k_stride=1)
+    r, db, img, T, nc = run_gpu_forward(batch, renderer=renderer)
+    ores = oracle.forward(batch, do_render=False)
+    compare_decisions(batch, ores, read_intermediates(r, db), db)
+    rect = ores[0].rect
+    kept = (rect[:, 2] > rect[:, 0]) & (rect[:, 3] > rect[:, 1])
+    assert kept.tolist() == [False, True, False, True]
 
 
 @pytest.mark.parametrize("W,H,tile", [(1, 1, (16, 16)), (17, 1, (16, 16)), (1, 33, (8, 32)),

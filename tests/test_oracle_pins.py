@@ -137,6 +137,20 @@ def closed_form_image(W, H, mean_px, cov2, o, color, bg, rect, TW=16, TH=16):
     return img
 
 
+@pytest.mark.parametrize("z,near,kept", [(-0.75, 0.25, False), (-0.75, 0.2499, True),
+                                         (-0.7499, 0.25, True), (-0.76, 0.25, False)])
+def test_near_plane_culls_at_and_behind_it(z, near, kept):
+    """The near-plane reading: a Gaussian whose camera depth p_z = z + 1 m (the default camera)
+    is at or in front of the near distance is culled, one just past it is kept (0.75 and 0.25
+    are exact in binary32, so p_z == near holds exactly in the first case)."""
+    m = one_gaussian_model((0.0, 0.0, z), (1.0, 0.0, 0.0, 0.0), np.log((0.01, 0.01, 0.01)), 1.0,
+                           (0.5, 0.5, 0.5))
+    batch = single_frame_batch(m, 64, 64)
+    batch.fparams[0, 16] = near
+    rect = oracle.forward(batch, do_render=False)[0].rect[0]
+    assert ((rect[2] > rect[0]) and (rect[3] > rect[1])) == kept
+
+
 @pytest.mark.parametrize("case", ["isotropic_axis", "rotated_axis", "offaxis_general"])
 def test_single_gaussian_closed_form(case):
     from scipy.spatial.transform import Rotation
