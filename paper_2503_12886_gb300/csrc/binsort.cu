@@ -274,6 +274,8 @@ __device__ __forceinline__ unsigned digit_peers(unsigned act, unsigned d) {
 // last pass is fully sorted. With kCacheRanks each key's rank within its warp's run of equal
 // digits is kept from the counting sweep (s_rank, L entries) and the scatter sweep only adds the
 // digit base; without it the scatter sweep ranks again. Returns the buffer holding the result.
+constexpr int kRounds = 4;  // rounds of 32 keys whose loads the radix sweeps issue together
+
 template <bool kCacheRanks>
 __device__ unsigned long long *radix_sort(unsigned long long *a, unsigned long long *b, int L,
                                           int shift0, int shift_end,
@@ -290,20 +292,33 @@ __device__ unsigned long long *radix_sort(unsigned long long *a, unsigned long l
     for (int shift = shift0; shift < shift_end; shift += 8) {
         for (int d = lane; d < 256; d += 32) cnt[d] = 0;
         __syncwarp();
-        for (int base = lo; base < hi; base += 32) {
-            const int e = base + lane;
-            const bool ok = e < hi;
-            const unsigned act = __ballot_sync(0xffffffffu, ok);
-            unsigned d = 0, peers = 0, before = 0;
-            if (ok) {
-                d = (unsigned)(a[e] >> shift) & 255u;
-                peers = digit_peers(act, d);
-                before = cnt[d];
-                if (kCacheRanks) s_rank[e] = (unsigned short)(before + __popc(peers & lt_mask));
+        // rounds of 32 keys, the keys of kRounds rounds loaded at once (in global memory each
+        // round would otherwise wait for its own load)
+        for (int base0 = lo; base0 < hi; base0 += kRounds * 32) {
+            unsigned long long kk[kRounds];
+#pragma unroll
+            for (int u = 0; u < kRounds; ++u) {
+                const int e = base0 + 32 * u + lane;
+                kk[u] = e < hi ? a[e] : 0ull;
             }
-            __syncwarp();
-            if (ok && (peers & lt_mask) == 0) cnt[d] = before + __popc(peers);
-            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < kRounds; ++u) {
+                const int base = base0 + 32 * u;
+                if (base >= hi) break;  // warp-uniform
+                const int e = base + lane;
+                const bool ok = e < hi;
+                const unsigned act = __ballot_sync(0xffffffffu, ok);
+                unsigned d = 0, peers = 0, before = 0;
+                if (ok) {
+                    d = (unsigned)(kk[u] >> shift) & 255u;
+                    peers = digit_peers(act, d);
+                    before = cnt[d];
+                    if (kCacheRanks) s_rank[e] = (unsigned short)(before + __popc(peers & lt_mask));
+                }
+                __syncwarp();
+                if (ok && (peers & lt_mask) == 0) cnt[d] = before + __popc(peers);
+                __syncwarp();
+            }
         }
         __syncthreads();
         // the scatter base of (digit d, warp w) is the count of all (digit, warp) pairs before it
@@ -338,24 +353,34 @@ __device__ unsigned long long *radix_sort(unsigned long long *a, unsigned long l
                 b[cnt[(unsigned)(k >> shift) & 255u] + s_rank[e]] = k;
             }
         } else {
-            for (int base = lo; base < hi; base += 32) {
-                const int e = base + lane;
-                const bool ok = e < hi;
-                const unsigned act = __ballot_sync(0xffffffffu, ok);
-                unsigned d = 0, peers = 0, pos = 0;
-                unsigned long long k = 0;
-                if (ok) {
-                    k = a[e];
-                    d = (unsigned)(k >> shift) & 255u;
-                    peers = digit_peers(act, d);
-                    pos = cnt[d] + __popc(peers & lt_mask);
+            for (int base0 = lo; base0 < hi; base0 += kRounds * 32) {
+                unsigned long long kk[kRounds];
+#pragma unroll
+                for (int u = 0; u < kRounds; ++u) {
+                    const int e = base0 + 32 * u + lane;
+                    kk[u] = e < hi ? a[e] : 0ull;
                 }
-                __syncwarp();
-                if (ok) {
-                    b[pos] = k;
-                    if ((peers & lt_mask) == 0) cnt[d] += __popc(peers);
+#pragma unroll
+                for (int u = 0; u < kRounds; ++u) {
+                    const int base = base0 + 32 * u;
+                    if (base >= hi) break;  // warp-uniform
+                    const int e = base + lane;
+                    const bool ok = e < hi;
+                    const unsigned act = __ballot_sync(0xffffffffu, ok);
+                    unsigned d = 0, peers = 0, pos = 0;
+                    const unsigned long long k = kk[u];
+                    if (ok) {
+                        d = (unsigned)(k >> shift) & 255u;
+                        peers = digit_peers(act, d);
+                        pos = cnt[d] + __popc(peers & lt_mask);
+                    }
+                    __syncwarp();
+                    if (ok) {
+                        b[pos] = k;
+                        if ((peers & lt_mask) == 0) cnt[d] += __popc(peers);
+                    }
+                    __syncwarp();
                 }
-                __syncwarp();
             }
         }
         __syncthreads();
