@@ -1,6 +1,8 @@
 """Parity at the full workload sizes, in the launch configuration the bench times: all tile
 decisions and lists bit-exact, pixels and per-Gaussian 2-D gradients on sampled tile blocks
-(the oracle renders only those tiles), and sampled frames of the uneven 64-frame batch."""
+(the oracle renders only those tiles), sampled frames of the uneven 64-frame batch, and the
+final gradients (dG0, ddG, dpsi) of the batched, tangent-space and uneven workloads with every
+pixel of every frame."""
 import numpy as np
 import pytest
 import torch
@@ -165,3 +167,89 @@ def test_tangent_workload_full_size(renderer):
         s = compare_images(sub, o, _view_batch(db, b), img, T, n, tiles_only=[pix])
         assert s["max_err"] <= 1e-4 and s["n_mismatch"] == 0, (b, s)
         assert s["flagged"] <= 0.005 * s["pixels"]
+
+
+def test_tangent_workload_gradients_full_size(renderer):
+    """The tangent-space training workload at its full size (N=60,000 bound to a 9,024-triangle
+    head mesh with an expression per frame, K=32, B=16 at 512x512; Alg. 1 in the preprocess and
+    its derivative in the Gaussian backward): every pixel of every frame, then dG0, ddG, dpsi and
+    each frame's gradient with respect to its blended Gaussians against the oracle, from the same
+    L1 dL/dimg (zero at the pixels the oracle flags as ambiguous)."""
+    batch = synth.workload_tangent()
+    targets = synth.make_targets(batch, 97)
+    ores, L, dls, per_model, dpsi, g2s, dgbs = oracle_fwd_bwd(batch, targets, "l1",
+                                                               drop_flagged=True, with_blended=True)
+    db = DeviceBatch(batch, "cuda:0", tile=(16, 16), smem_batch=64)
+    img, T, n = renderer.forward(db)
+    torch.cuda.synchronize()
+    st = compare_images(batch, ores, db, img, T, n)
+    assert st["max_err"] <= PIX_ATOL and st["n_mismatch"] == 0, st
+    assert st["flagged"] <= 0.001 * st["pixels"], st
+    dl = db.pack_images([d.astype(np.float32) for d in dls])
+    gb = torch.full((db.total_rec * 14,), float("nan"), device="cuda:0")
+    renderer.backward(db, dl, T, n, grad_blended=gb)
+    torch.cuda.synchronize()
+    errs = backward_errors(batch, db, per_model, dpsi, dgbs, gb)
+    assert max(errs.values()) <= 1.0, errs
+
+
+def test_uneven_workload_full_size(renderer):
+    """The uneven batch at its full size (8 avatars, N 20k..100k, K 16/24/32, 64 frames at
+    256/512/1024 px, one launch per stage, the bench's 16x16 tiles and 64-entry staging): every
+    frame's decisions and lists bit-exact, every pixel, then every avatar's dG0 and ddG and every
+    frame's dpsi against the oracle. Both backward passes take the same dL/dimg: the L1 gradient
+    of the CUDA image, zero at the pixels the oracle flags as ambiguous. The oracle runs one
+    spawned worker per avatar."""
+    import multiprocessing as mp
+    import os
+
+    import oracle_pool
+    from gpu_helpers import AMBIG_EPS, AMBIG_EPS_T, frame_tile_bases, grad_error
+
+    batch = synth.workload_uneven()
+    B = len(batch.frames)
+    db = DeviceBatch(batch, "cuda:0", tile=(16, 16), smem_batch=64)
+    img, T, n = renderer.forward(db)
+    torch.cuda.synchronize()
+    inter = read_intermediates(renderer, db)
+    targets = synth.make_targets(batch, 96)
+    imgs, Ts, ns = db.image_views(img), db.pix_views(T), db.pix_views(n)
+    bases = frame_tile_bases(batch)
+    payload = {a: [] for a in range(len(batch.models))}
+    for b, fr in enumerate(batch.frames):
+        m = batch.models[fr.model]
+        rb = db.rec_offsets[b]
+        nt = ((fr.width + 15) // 16) * ((fr.height + 15) // 16)
+        ts = inter["tile_start"][bases[b]: bases[b] + nt + 1].astype(np.int64)
+        gi = imgs[b].cpu().numpy()
+        # L1 over the batch: mean per frame, mean over the frames
+        dl = (np.sign(gi.astype(np.float64) - targets[b]) / (3.0 * fr.width * fr.height * B)).astype(np.float32)
+        payload[fr.model].append({
+            "b": b, "img": gi, "T": Ts[b].cpu().numpy(), "n": ns[b].cpu().numpy(),
+            "rect": inter["rects"][rb: rb + m.n].astype(np.int32), "rec": inter["records"][rb: rb + m.n],
+            "tile_start": ts - ts[0], "lst": inter["sorted"][ts[0]: ts[-1]].astype(np.int64), "dl": dl})
+    jobs = [(a, payload[a], AMBIG_EPS, AMBIG_EPS_T, PIX_ATOL) for a in payload]
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        res = pool.map(oracle_pool.uneven_avatar, jobs)
+    dls = [None] * B
+    flagged = pixels = 0
+    for r in res:
+        flagged += r["stats"]["flagged"]
+        pixels += r["stats"]["pixels"]
+        for j, b in enumerate(r["idx"]):
+            f = payload[r["a"]][j]
+            dls[b] = np.where(r["flags"][j][None], np.float32(0), f["dl"])
+    assert flagged <= 0.001 * pixels, (flagged, pixels)
+    renderer.backward(db, db.pack_images(dls), T, n)
+    torch.cuda.synchronize()
+    errs = {}
+    dpsi = np.zeros_like(db.grad_psi.cpu().numpy(), dtype=np.float64)
+    for r in res:
+        m = db.models[r["a"]]
+        errs[f"g0[{r['a']}]"] = grad_error(m.grad_g0.cpu().numpy()[:, :m.n], r["g0"][:, :m.n])
+        errs[f"dg[{r['a']}]"] = grad_error(m.grad_dg.cpu().numpy()[..., :m.n].reshape(-1, m.n),
+                                           r["dg"][..., :m.n].reshape(-1, m.n))
+        assert np.all(m.grad_g0.cpu().numpy()[:, m.n:] == 0)
+        dpsi[r["idx"], :r["dpsi"].shape[1]] = r["dpsi"]
+    errs["psi"] = grad_error(db.grad_psi.cpu().numpy(), dpsi, axis_rows=False)
+    assert max(errs.values()) <= 1.0, errs
