@@ -251,6 +251,7 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadixCap = 8192;                  // keys a segment may have for the shared-memory radix sort
+constexpr int kMidCap = 2 * kRadixCap;           // keys a segment may have for the position bucket sort
 constexpr int kDigitParts = kSortThreads / 256;  // threads sharing one digit's column of warp counts
 static_assert(kSortThreads % 256 == 0 && 32 % kDigitParts == 0, "whole digits per warp");
 
@@ -462,22 +463,85 @@ __device__ unsigned long long *bucket_sort(unsigned long long *a, unsigned long 
     return *s_long ? b : a;  // b still holds every key for the fallback
 }
 
+// Sort of kRadixCap < L <= kMidCap keys held in shared memory as they are (a, filling the key
+// area of both buffers of bucket_sort) by the same one-pass bucketing, but moving 2-byte
+// positions instead of 8-byte keys so that twice as many keys fit: a shared-memory atomic per
+// key gives its bucket and its slot, a scan the bucket starts, each key's position goes to its
+// bucket's run in s_pos, and every key counts the smaller keys of its bucket (read through the
+// positions) and writes its Gaussian index straight to its rank in the tile's list `out`.
+// Returns false when some bucket is longer than kBucketRun (its keys are then not written; the
+// caller sorts the whole segment again another way).
+__device__ bool bucket_sort_pos(const unsigned long long *a, int L, unsigned d0, int db,
+                                unsigned *s_hist /* >= 2^kBucketBits + kSortWarps, zeroed */,
+                                unsigned short *s_rank, unsigned short *s_pos, unsigned *s_long,
+                                unsigned *__restrict__ out) {
+    constexpr int NB = 1 << kBucketBits, PER = NB / kSortThreads;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bshift = max(0, db - kBucketBits);
+    auto bucket = [&](unsigned long long k) { return ((unsigned)(k >> 32) - d0) >> bshift; };
+    unsigned *wsum = s_hist + NB;
+    for (int e = tid; e < L; e += kSortThreads)
+        s_rank[e] = (unsigned short)atomicAdd(&s_hist[bucket(a[e])], 1u);
+    __syncthreads();
+    {  // exclusive scan of the bucket counts; thread t owns buckets [t PER, (t+1) PER)
+        unsigned v[PER], run = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            v[q] = run;
+            run += s_hist[tid * PER + q];
+        }
+        unsigned x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        unsigned off = x - run;
+#pragma unroll
+        for (int q = 0; q < kSortWarps; ++q) off += q < warp ? wsum[q] : 0u;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) s_hist[tid * PER + q] = off + v[q];
+    }
+    __syncthreads();
+    for (int e = tid; e < L; e += kSortThreads) s_pos[s_hist[bucket(a[e])] + s_rank[e]] = (unsigned short)e;
+    __syncthreads();
+    for (int p = tid; p < L; p += kSortThreads) {
+        const unsigned long long k = a[s_pos[p]];
+        const unsigned bk = bucket(k);
+        const int lo = (int)s_hist[bk], hi = bk + 1 < (unsigned)NB ? (int)s_hist[bk + 1] : L;
+        if (hi - lo > kBucketRun) {
+            *s_long = 1u;
+            continue;
+        }
+        int rank = 0;
+        for (int q = lo; q < hi; ++q) rank += a[s_pos[q]] < k;
+        out[lo + rank] = (unsigned)k;
+    }
+    __syncthreads();
+    return *s_long == 0u;
+}
+
 // Persistent: CTAs take (frame, tile) segments from the LPT-ordered work list. A key is
 // (depth, Gaussian index); it is compressed to (depth - min depth) << 32 | index. A segment of
 // up to kRadixCap keys is sorted in shared memory by bucket_sort (one bucket pass, then each
-// bucket by the full key). A longer one is radix-sorted in place in global memory (mostly L2)
-// on the depth bits only, which leaves runs of equal depth in list order, and a tie pass orders
-// each such run by index (insertion sort by the run's first thread). A bucket longer than
-// kBucketRun or a run longer than kTieRun sends the segment to a full-key sort: radix passes on
-// the index bits, then on the depth bits.
+// bucket by the full key), one of up to kMidCap keys by bucket_sort_pos (the same with 2-byte
+// positions in place of moved keys). A longer one is radix-sorted in place in global memory
+// (mostly L2) on the depth bits only, which leaves runs of equal depth in list order, and a tie
+// pass orders each such run by index (insertion sort by the run's first thread). A bucket longer
+// than kBucketRun or a run longer than kTieRun sends the segment to a full-key sort: radix passes
+// on the index bits, then on the depth bits (a segment of bucket_sort_pos goes to the global-memory
+// sort).
 // The sort is bound by round trips to memory, so none of them waits on another: thread 0 claims
 // work items three ahead and, one stage per item, loads the claimed item's tile id and then its
 // list bounds while the CTA sorts the current segment; a segment that fits in shared memory
 // arrives there by asynchronous copies, all in flight at once.
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
-    extern __shared__ unsigned long long s_keys[];  // [kRadixCap] x 2, counts, ranks
+    extern __shared__ unsigned long long s_keys[];  // [kRadixCap] x 2 (or [kMidCap]), counts, ranks, positions
     unsigned *s_cnt = reinterpret_cast<unsigned *>(s_keys + 2 * kRadixCap);
     unsigned short *s_rank = reinterpret_cast<unsigned short *>(s_cnt + kSortWarps * 256 + kSortWarps);
+    unsigned short *s_pos = s_rank + kMidCap;
     __shared__ unsigned s_cur, s_st, s_L, s_dmin, s_dmax, s_imax, s_long;
     pdl_enter();
     if (c.cnt->overflow) return;
@@ -512,15 +576,16 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
         }
         const unsigned long long *g = c.keys + st;
         const bool in_smem = L <= (unsigned)kRadixCap;
+        const bool mid = !in_smem && L <= (unsigned)kMidCap;  // the position bucket sort
         unsigned dmin = 0xffffffffu, dmax = 0u, imax = 0u;
-        if (in_smem) {
+        if (in_smem || mid) {
             for (unsigned e = threadIdx.x; e < L; e += blockDim.x) cp_async8(s_keys + e, g + e);
             for (int i = threadIdx.x; i < (1 << kBucketBits); i += blockDim.x) s_cnt[i] = 0u;  // bucket counts
             asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
         }
         for (unsigned e = threadIdx.x; e < L; e += blockDim.x) {
-            const unsigned long long k = in_smem ? s_keys[e] : g[e];
+            const unsigned long long k = in_smem || mid ? s_keys[e] : g[e];
             const unsigned d = (unsigned)(k >> 32), i = (unsigned)k;
             dmin = min(dmin, d);
             dmax = max(dmax, d);
@@ -551,8 +616,18 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
             }
             __syncthreads();
         };
-        unsigned long long *res;
-        if (in_smem) {
+        unsigned long long *res = nullptr;  // stays null when the keys' indices are already written
+        bool done = false;
+        if (mid) {
+            done = bucket_sort_pos(s_keys, (int)L, d0, db, s_cnt, s_rank, s_pos, &s_long, c.sorted + st);
+            __syncthreads();  // every thread has read the flag before it is cleared
+            if (!done) {      // a crowded bucket: sort the segment in global memory below
+                if (threadIdx.x == 0) s_long = 0u;
+                __syncthreads();
+            }
+        }
+        if (done) {
+        } else if (in_smem) {
             res = bucket_sort(a, bb, (int)L, d0, db, s_cnt, s_rank, &s_long);
             if (s_long) {  // a bucket too crowded for the fix-up: the full key by radix passes
                 compress(res, res);
@@ -591,7 +666,8 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
                 res = radix_sort<false>(res, other, (int)L, 32, 32 + db, s_cnt, nullptr);
             }
         }
-        for (unsigned e = threadIdx.x; e < L; e += blockDim.x) c.sorted[st + e] = (unsigned)res[e];
+        if (res)
+            for (unsigned e = threadIdx.x; e < L; e += blockDim.x) c.sorted[st + e] = (unsigned)res[e];
         __syncthreads();
         if (threadIdx.x == 0) {
             s_cur = w1 < n_work ? 1u : 0u;
@@ -638,7 +714,7 @@ cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s) {
 cudaError_t launch_tile_sort(const Ctx &c, int sms, cudaStream_t s) {
     static int attr_device = -1, per_sm = 1;
     const int smem = 2 * kRadixCap * (int)sizeof(unsigned long long) + (kSortWarps * 256 + kSortWarps) * 4 +
-                     kRadixCap * (int)sizeof(unsigned short);
+                     2 * kMidCap * (int)sizeof(unsigned short);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
