@@ -251,7 +251,12 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadixCap = 8192;                  // keys a segment may have for the shared-memory radix sort
-constexpr int kMidCap = 2 * kRadixCap;           // keys a segment may have for the position bucket sort
+constexpr int kMidCap = 3 * kRadixCap / 2;       // keys a segment may have for the position bucket sort
+// the position sort's keys, ranks and positions fill the key area and rank array of the
+// shared-memory sort exactly, so the kernel needs no more shared memory than that one: a larger
+// footprint kept the next kernel's CTAs from starting on the SMs early and cost 0.12 ms per
+// training step in the captured graph
+static_assert(kMidCap * (8 + 2 + 2) <= kRadixCap * (2 * 8 + 2), "position sort fits the key area and rank array");
 constexpr int kDigitParts = kSortThreads / 256;  // threads sharing one digit's column of warp counts
 static_assert(kSortThreads % 256 == 0 && 32 % kDigitParts == 0, "whole digits per warp");
 
@@ -463,9 +468,9 @@ __device__ unsigned long long *bucket_sort(unsigned long long *a, unsigned long 
     return *s_long ? b : a;  // b still holds every key for the fallback
 }
 
-// Sort of kRadixCap < L <= kMidCap keys held in shared memory as they are (a, filling the key
-// area of both buffers of bucket_sort) by the same one-pass bucketing, but moving 2-byte
-// positions instead of 8-byte keys so that twice as many keys fit: a shared-memory atomic per
+// Sort of kRadixCap < L <= kMidCap keys held in shared memory as they are (a) by the same
+// one-pass bucketing, but moving 2-byte positions instead of 8-byte keys so that half as many
+// keys again fit in the same shared memory: a shared-memory atomic per
 // key gives its bucket and its slot, a scan the bucket starts, each key's position goes to its
 // bucket's run in s_pos, and every key counts the smaller keys of its bucket (read through the
 // positions) and writes its Gaussian index straight to its rank in the tile's list `out`.
@@ -538,10 +543,13 @@ __device__ bool bucket_sort_pos(const unsigned long long *a, int L, unsigned d0,
 // list bounds while the CTA sorts the current segment; a segment that fits in shared memory
 // arrives there by asynchronous copies, all in flight at once.
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
-    extern __shared__ unsigned long long s_keys[];  // [kRadixCap] x 2 (or [kMidCap]), counts, ranks, positions
-    unsigned *s_cnt = reinterpret_cast<unsigned *>(s_keys + 2 * kRadixCap);
-    unsigned short *s_rank = reinterpret_cast<unsigned short *>(s_cnt + kSortWarps * 256 + kSortWarps);
-    unsigned short *s_pos = s_rank + kMidCap;
+    // [kRadixCap] x 2 keys, [kRadixCap] ranks, counts; the position sort uses the keys and ranks
+    // area as [kMidCap] keys, [kMidCap] ranks, [kMidCap] positions
+    extern __shared__ unsigned long long s_keys[];
+    unsigned short *s_rank = reinterpret_cast<unsigned short *>(s_keys + 2 * kRadixCap);
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(s_rank + kRadixCap);
+    unsigned short *s_rank_mid = reinterpret_cast<unsigned short *>(s_keys + kMidCap);
+    unsigned short *s_pos_mid = s_rank_mid + kMidCap;
     __shared__ unsigned s_cur, s_st, s_L, s_dmin, s_dmax, s_imax, s_long;
     pdl_enter();
     if (c.cnt->overflow) return;
@@ -619,7 +627,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(Ctx c) {
         unsigned long long *res = nullptr;  // stays null when the keys' indices are already written
         bool done = false;
         if (mid) {
-            done = bucket_sort_pos(s_keys, (int)L, d0, db, s_cnt, s_rank, s_pos, &s_long, c.sorted + st);
+            done = bucket_sort_pos(s_keys, (int)L, d0, db, s_cnt, s_rank_mid, s_pos_mid, &s_long, c.sorted + st);
             __syncthreads();  // every thread has read the flag before it is cleared
             if (!done) {      // a crowded bucket: sort the segment in global memory below
                 if (threadIdx.x == 0) s_long = 0u;
@@ -713,8 +721,8 @@ cudaError_t launch_scatter(const Ctx &c, int max_n, cudaStream_t s) {
 
 cudaError_t launch_tile_sort(const Ctx &c, int sms, cudaStream_t s) {
     static int attr_device = -1, per_sm = 1;
-    const int smem = 2 * kRadixCap * (int)sizeof(unsigned long long) + (kSortWarps * 256 + kSortWarps) * 4 +
-                     2 * kMidCap * (int)sizeof(unsigned short);
+    const int smem = 2 * kRadixCap * (int)sizeof(unsigned long long) + kRadixCap * (int)sizeof(unsigned short) +
+                     (kSortWarps * 256 + kSortWarps) * 4;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
