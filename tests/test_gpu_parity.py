@@ -70,6 +70,25 @@ def dense_batch():
     return synth.make_batch([m], [synth.Frame(0, 64, 64)], seed=93)
 
 
+def mid_lists_batch():
+    """11,000 Gaussians around one tile corner: four tile lists of 8,238 to 10,405 keys, past the
+    shared-memory bucket sort's 8,192 and within the position bucket sort's 12,288 (depth
+    buckets of at most 16 keys)."""
+    m = synth.make_model(93, 11_000, 4, radii=(0.05, 0.05, 0.05), log_scale_mu=math.log(6e-3))
+    return synth.make_batch([m], [synth.Frame(0, 64, 64)], seed=93)
+
+
+def mid_lists_crowded_batch():
+    """The same four list lengths, with a cluster of 300 Gaussians at nearly one depth (steps of
+    about two ulps) in them: about 250 keys fall into one depth bucket, more than the position
+    sort's rank placement takes, so those lists go to the global-memory sort after it."""
+    m = synth.make_model(94, 11_000, 4, radii=(0.05, 0.05, 0.05), log_scale_mu=math.log(6e-3), sd_dmean=0.0)
+    g0 = m.g0.copy()
+    g0[0:2, :300] = 0.0
+    g0[2, :300] = 0.02 + 2.4e-7 * np.arange(300)
+    return synth.make_batch([dataclasses.replace(m, g0=g0)], [synth.Frame(0, 64, 64)], seed=94)
+
+
 def cluster_batch():
     """A tight cluster of 300 Gaussians at nearly one depth (steps of about two ulps) among 1,700
     spread ones: the cluster's tile lists put ~150 distinct keys into each of one or two of the
@@ -159,6 +178,8 @@ CASES = {
     "all_channels_k64": (all_channels_batch, (16, 16), 64),
     "mixed_masks": (mixed_masks_batch, (8, 32), 128),
     "dense_lists": (dense_batch, (16, 16), 64),
+    "mid_lists": (mid_lists_batch, (16, 16), 64),
+    "mid_lists_crowded": (mid_lists_crowded_batch, (16, 16), 64),
     "tangent": (tangent_batch, (16, 16), 64),
     "tangent_paper_mask": (lambda: tangent_batch(synth.MASK_PAPER, 82), (8, 32), 128),
     "odd_k": (odd_k_batch, (16, 16), 64),
