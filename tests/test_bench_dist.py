@@ -47,3 +47,25 @@ def test_reference_arm_ranks_other_than_zero_do_nothing(capsys):
         warmup, steps, gpus = 1, 1, 2
     bench.run_reference(A, rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_zero(capsys):
+    """The reference arm as the driver launches it (rank 0 of one): the oracle times frames of
+    the batched workload on the host cores and prints one JSON line with the contract's keys,
+    the reference arm's own e2e (no host-device copies) and its CPU-baseline record."""
+    import json
+
+    import bench
+
+    class A:
+        warmup, steps, gpus = 1, 2, 1
+    bench.run_reference(A, rank=0, world=1)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "img/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2 and d["n_gpus"] == 1
+    assert d["config"]["workload"] == bench.WORKLOAD
+    assert d["e2e"] == {"value": d["value"], "unit": "img/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
